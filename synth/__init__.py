@@ -1,0 +1,152 @@
+"""Seeded synthetic density matrices shaped like the paper's workloads.
+
+This module only builds inputs.  It holds none of the estimators'
+arithmetic (no entropy, no polynomial, no trace estimate, no power
+method): both the CUDA path's tests and the CPU oracle draw their
+matrices from here, and nothing else is shared between them.
+
+Input model (Section 1.1, eqs. R and R1): a real density matrix is
+R = Psi diag(p) Psi^T with orthonormal columns psi_i, p_i > 0 and
+sum p_i = 1.  The paper draws its dense matrices from QETLAB's
+RandomDensityMatrix (Section 6), which is not available here; Haar-like
+orthonormal Psi from the QR factorisation of a seeded Gaussian matrix
+stands in for it.  The banded matrices follow the paper's tridiagonal
+Poisson example (Section 6, eq. poisson_matrix) and its wider,
+diagonally dominant generalisation.
+
+Banded storage (DIA, symmetric): ``vals[d, i] = R[i, i + d]`` for
+d = 0 .. D-1 and i < n - d; entries with i >= n - d are zero padding.
+The lower triangle is implied by symmetry.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "spectrum_exponential",
+    "spectrum_powerlaw_floor",
+    "spectrum_poisson",
+    "haar_orthogonal",
+    "dense_density",
+    "dense_exp",
+    "dense_powerlaw",
+    "band_diag_dominant",
+    "band_poisson",
+    "dia_to_dense",
+    "WORKLOADS",
+]
+
+
+def spectrum_exponential(n: int, tau: float) -> np.ndarray:
+    """p_i proportional to exp(-i/tau), i = 1..n, normalised to unit sum."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    p = np.exp(-i / tau)
+    return p / p.sum()
+
+
+def spectrum_powerlaw_floor(n: int, k: int, alpha: float, floor: float) -> np.ndarray:
+    """p_i proportional to i^-alpha for i <= k, a constant floor for i > k,
+    then renormalised to unit sum (the floor is applied before scaling)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    p = np.where(i <= k, i ** (-alpha), 0.0)
+    p = p / p.sum()
+    p = np.where(i <= k, p, floor)
+    return p / p.sum()
+
+
+def spectrum_poisson(n: int) -> np.ndarray:
+    """Eigenvalues of tridiag(-1, 2, -1) / (2n), eq. trig_eigs of Section 6:
+    lambda_i = (4 / 2n) sin^2(i pi / (2n + 2)), i = 1..n (ascending)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return (4.0 / (2.0 * n)) * np.sin(i * np.pi / (2.0 * n + 2.0)) ** 2
+
+
+def haar_orthogonal(n: int, seed: int) -> np.ndarray:
+    """Q of the QR factorisation of a seeded n x n N(0,1) matrix (FP64)."""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(a)
+    # sign fix so that Q is Haar distributed (the diagonal of r made positive)
+    q *= np.sign(np.diag(r))[None, :]
+    return q
+
+
+def dense_density(psi: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """R = Psi diag(p) Psi^T, symmetrised, row-major FP64 (eq. R1)."""
+    r = (psi * p[None, :]) @ psi.T
+    r = 0.5 * (r + r.T)
+    return np.ascontiguousarray(r)
+
+
+def dense_exp(n: int = 512, tau: float = 50.0, seed: int = 1):
+    """Dense density matrix with p_i ~ exp(-i/tau); returns (R, p, Psi)."""
+    psi = haar_orthogonal(n, seed)
+    p = spectrum_exponential(n, tau)
+    return dense_density(psi, p), p, psi
+
+
+def dense_powerlaw(n: int = 8192, k: int = 2048, alpha: float = 1.5,
+                   floor: float = 1e-9, seed: int = 2):
+    """Dense density matrix with p_i ~ i^-alpha on the top k states and a
+    floor on the rest; returns (R, p, Psi)."""
+    psi = haar_orthogonal(n, seed)
+    p = spectrum_powerlaw_floor(n, k, alpha, floor)
+    return dense_density(psi, p), p, psi
+
+
+def band_diag_dominant(n: int, half_bw: int = 16, offdiag_scale: float = 0.02,
+                       seed: int = 3, dtype=np.float32) -> np.ndarray:
+    """Symmetric banded density matrix in DIA storage, shape (half_bw+1, n).
+
+    Off-diagonals are U(-1, 1) * offdiag_scale, the diagonal is
+    1 + sum_j |R_ij| over the row's off-diagonal entries (strict diagonal
+    dominance, so R is SPD), and the whole matrix is divided by its trace.
+    """
+    rng = np.random.default_rng(seed)
+    D = half_bw + 1
+    vals = np.zeros((D, n), dtype=np.float64)
+    rowabs = np.zeros(n, dtype=np.float64)
+    for d in range(1, D):
+        v = rng.uniform(-1.0, 1.0, n - d) * offdiag_scale
+        vals[d, : n - d] = v
+        a = np.abs(v)
+        rowabs[: n - d] += a   # row i holds R[i, i+d]
+        rowabs[d:] += a        # row i+d holds R[i+d, i]
+    vals[0] = 1.0 + rowabs
+    vals /= vals[0].sum()
+    return np.ascontiguousarray(vals.astype(dtype))
+
+
+def band_poisson(n: int, dtype=np.float64) -> np.ndarray:
+    """tridiag(-1, 2, -1) / (2n) in DIA storage, shape (2, n) (Section 6)."""
+    vals = np.zeros((2, n), dtype=np.float64)
+    vals[0] = 2.0
+    vals[1, : n - 1] = -1.0
+    vals /= 2.0 * n
+    return np.ascontiguousarray(vals.astype(dtype))
+
+
+def dia_to_dense(vals: np.ndarray) -> np.ndarray:
+    """Expand symmetric DIA storage to a dense FP64 matrix (small n only)."""
+    D, n = vals.shape
+    r = np.zeros((n, n), dtype=np.float64)
+    v = vals.astype(np.float64)
+    r[np.arange(n), np.arange(n)] = v[0]
+    for d in range(1, D):
+        idx = np.arange(n - d)
+        r[idx, idx + d] = v[d, : n - d]
+        r[idx + d, idx] = v[d, : n - d]
+    return r
+
+
+# Named workloads: (what it is, sizes).  The estimator parameters sit
+# beside the matrix recipe so that tests and the bench use one definition.
+WORKLOADS = {
+    "dense_exp_n512": dict(kind="dense", n=512, spectrum="exp", tau=50.0, seed=1,
+                           m=20, s=50, probe="rademacher", power_iters=30),
+    "dense_powerlaw_n8192": dict(kind="dense", n=8192, spectrum="powerlaw", k=2048,
+                                 alpha=1.5, floor=1e-9, seed=2, m=40, s=128,
+                                 probe="gaussian", power_iters=30),
+    "band33_n1e7": dict(kind="band", n=10_000_000, half_bw=16, offdiag_scale=0.02,
+                        seed=3, m=30, s=64, probe="rademacher", power_iters=30),
+}
