@@ -1,0 +1,409 @@
+"""Throughput of the randomized von Neumann entropy estimators on GB300.
+
+Default workload (one step = one density matrix through the whole hot path):
+dense n = 8192 density matrix R = Psi diag(p) Psi^T (Psi from the QR of a
+seeded Gaussian matrix, p_i ~ i^-1.5 on the top 2048 states and a 1e-9 floor
+on the rest, unit trace, FP64 in HBM).  Per step: bf16 hi/lo split of R,
+30 power-method products (Algorithm alg:power) -> u, then the Chebyshev
+(Algorithm 1b, m = 40) and Taylor (Algorithm 1a, m = 40) recurrences on
+s = 128 Gaussian probes sharing every pass over R (41 tensor-core steps),
+FP64 combine, and the estimates copied back to the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|bf16x3|f64]
+                    [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7]
+                    [--impl reference]
+
+Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def peak_value(d, *keys):
+    for k in keys:
+        v = d.get(k)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("value", "median", "mean"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return None
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def make_workload(name):
+    w = dict(synth.WORKLOADS[name])
+    if w["kind"] == "dense":
+        if w["spectrum"] == "powerlaw":
+            R, p, _ = synth.dense_powerlaw(w["n"], w["k"], w["alpha"], w["floor"], w["seed"])
+        else:
+            R, p, _ = synth.dense_exp(w["n"], w["tau"], w["seed"])
+        return w, R, p
+    vals = synth.band_diag_dominant(w["n"], w["half_bw"], w["offdiag_scale"], w["seed"],
+                                    dtype=np.float32)
+    return w, vals, None
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}",
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# --------------------------------------------------------------------------
+
+def oracle_sample_time(w, R, s_sample):
+    """Time the oracle on the full matrix with s_sample of the s probes:
+    power method + both recurrences.  Returns (seconds extrapolated to the
+    full s, description, threads)."""
+    import oracle as O
+    from oracle import rng
+
+    n, m, s = w["n"], w["m"], w["s"]
+    if w["kind"] == "band":
+        Rop = O.Dia(R)
+    else:
+        Rop = R
+    t0 = time.perf_counter()
+    lam, _ = O.power_method(Rop, rng.power_start(n, 1, w["seed"]), w["power_iters"])
+    t1 = time.perf_counter()
+    u = O.interval_u(lam, 1.0)
+    G = rng.probes(n, s, w["seed"], w["probe"])[:, :s_sample]
+    O.chebyshev_moments(Rop, G, u, m)
+    if w["kind"] == "dense":
+        O.taylor_terms(Rop, G, u, m)
+    t2 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * (s / s_sample)
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count() or 1
+    est = "Chebyshev + Taylor" if w["kind"] == "dense" else "Chebyshev"
+    desc = (f"oracle (NumPy FP64) on the full n={n} matrix: {w['power_iters']} power-method "
+            f"products + {est} recurrences, m={m}, on {s_sample} of the s={s} probes, "
+            f"time scaled by s/{s_sample} for the recurrence part")
+    return full, desc, threads
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1801_01072_gb300 as vne
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w, Rh, p = make_workload(args.workload)
+    dense = w["kind"] == "dense"
+    n, m, s = w["n"], w["m"], w["s"]
+    prec = args.precision if dense else "f32"
+    Rd = torch.as_tensor(Rh).to(dev)
+    layout = "dense" if dense else "dia"
+    seed = w["seed"] + 1000 * rank  # each rank: an independent estimate
+
+    def step(R):
+        if dense:
+            return vne.entropy_both(R, m, s, seed=seed, probe=w["probe"], precision=prec,
+                                    power_iters=w["power_iters"], layout=layout)
+        return vne.entropy_chebyshev(R, m, s, seed=seed, probe=w["probe"], precision=prec,
+                                     power_iters=w["power_iters"], layout=layout)
+
+    h = vne._handle(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        out = step(Rd)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    h.profile(True)
+    n_launch0 = h.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step(Rd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    n_launch = h.launch_count() - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    kind = 0 if (dense and prec in ("bf16", "bf16x3")) else (1 if dense else 2)
+    k_ms, k_n = h.profile_read(kind)
+    h.profile(False)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # ---- end to end: host-resident R, copies inside the call ----
+    Rpin = torch.as_tensor(Rh).pin_memory()
+    step(Rpin)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    e2e_steps = max(3, args.steps // 4)
+    for _ in range(e2e_steps):
+        step(Rpin)
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ev2.elapsed_time(ev3) / e2e_steps
+    e2e_wall = (time.perf_counter() - e0) / e2e_steps * 1e3
+    e2e_ms = max(e2e_ms, e2e_wall)
+
+    # ---- accuracy of this precision against the FP64 path on the GPU ----
+    rel_err = None
+    if rank == 0 and dense and prec != "f64" and not args.skip_f64_check:
+        ref = vne.entropy_both(Rd, m, s, seed=seed, probe=w["probe"], precision="f64",
+                               u=out.u)
+        rel_err = {
+            "chebyshev": abs(out.H_chebyshev - ref.H_chebyshev) / abs(ref.H_chebyshev),
+            "taylor": abs(out.H_taylor - ref.H_taylor) / abs(ref.H_taylor),
+        }
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    step_ms = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+    pk, pk_src = peaks()
+    if dense and prec in ("bf16", "bf16x3", "f64", "f32"):
+        # algorithmic flops per launch: 2 n^2 per probe column per step
+        cols = 2 * s * m + s  # Chebyshev: m steps x s cols; Taylor: (m+1) steps x s cols
+        flops = 2.0 * n * n * cols * args.steps
+        achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+        if prec in ("bf16", "bf16x3"):
+            peak = peak_value(pk, "bf16_tflops_sustained", "bf16_tflops")
+            bound, unit = "tensor", "TFLOP/s"
+        else:
+            peak, bound, unit = None, "alu", "TFLOP/s"
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+                "kernel": "k_tc_step" if kind == 0 else "k_simt_step",
+                "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
+                "peak_source": pk_src + (" bf16 sustained" if peak else "")}
+    else:
+        bytes_step = (3 * 4 * n * s + w["half_bw"] * 0 + (w["half_bw"] + 1) * 4 * n) * m
+        achieved = bytes_step * args.steps / (k_ms / 1e3) / 1e9 if k_ms > 0 else None
+        peak = peak_value(pk, "hbm_gbs")
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if (achieved and peak) else None, "traffic": None,
+                "kernel": "k_dia_step", "launches": k_n,
+                "avg_launch_us": k_ms / max(k_n, 1) * 1e3, "peak_source": pk_src + " hbm"}
+
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        s_sample = args.cpu_probes
+        t_full, desc, threads = oracle_sample_time(w, Rh, s_sample)
+        cpu = {"value": 1.0 / t_full, "unit": "entropies/s", "cores": threads, "kind": "oracle",
+               "sample": desc}
+
+    clocks = clk.summary()
+    line = {
+        "metric": "entropies/s (density matrices through power method + Chebyshev m=40 + "
+                  "Taylor m=40, s=128) at <=1e-3 rel. error vs the FP64 path on the same GPU"
+                  if dense else "entropies/s (banded Chebyshev m=30, s=64)",
+        "value": value,
+        "unit": "entropies/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "bf16x3": "bf16x3", "f64": "f64", "f32": "f32"}[prec],
+        "data": "synthetic (seeded density matrices, no dataset)",
+        "config": {"workload": args.workload, "n": n, "m": m, "s": s, "probe": w["probe"],
+                   "power_iters": w["power_iters"], "precision": prec,
+                   "estimators": "chebyshev+taylor" if dense else "chebyshev",
+                   "input": "R FP64 resident in HBM" if dense else "band FP32 resident in HBM",
+                   "l2": "inputs larger than L2 (R is %.0f MB)" % (Rh.nbytes / 1e6),
+                   "parallelism": f"independent matrices, {world} GPU(s)"},
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
+                "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": 200 * 8},
+        "gpu_launches": int(n_launch),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "rel_err_vs_f64": rel_err,
+        "estimates": {"H_chebyshev": getattr(out, "H_chebyshev", getattr(out, "H", None)),
+                      "H_taylor": getattr(out, "H_taylor", None), "u": out.u,
+                      "H_exact": float(-(p[p > 0] * np.log(p[p > 0])).sum()) if p is not None
+                      else None},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, Rh, p = make_workload(args.workload)
+    s_sample = args.ref_probes
+    times = []
+    for i in range(args.warmup + args.steps):
+        t, desc, threads = oracle_sample_time(w, Rh, s_sample)
+        if i >= args.warmup:
+            times.append(t)
+    tot = sum(times)
+    value = len(times) / tot
+    line = {
+        "impl": "reference",
+        "metric": "entropies/s (density matrices through power method + Chebyshev m=40 + "
+                  "Taylor m=40, s=128) at <=1e-3 rel. error vs the FP64 path on the same GPU"
+                  if w["kind"] == "dense" else "entropies/s (banded Chebyshev m=30, s=64)",
+        "value": value,
+        "unit": "entropies/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tot / len(times) * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded density matrices, no dataset)",
+        "config": {"workload": args.workload, "n": w["n"], "m": w["m"], "s": w["s"],
+                   "probe": w["probe"], "power_iters": w["power_iters"]},
+        "cpu_baseline": {"value": value, "unit": "entropies/s", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "entropies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dense_powerlaw_n8192", choices=list(synth.WORKLOADS))
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "f64", "f32"])
+    ap.add_argument("--cpu-probes", type=int, default=16)
+    ap.add_argument("--ref-probes", type=int, default=4)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-f64-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * vne.h -- C ABI of the GB300 (sm_103a) randomized von Neumann entropy library.
+ *
+ * The library estimates H(R) = -tr(R ln R) of a real symmetric positive
+ * (semi)definite density matrix R with unit trace (Section 1.1, eqs. earlyR,
+ * R, R1, VN of Kontopoulou et al., "Randomized linear algebra approaches to
+ * estimate the von Neumann entropy of density matrices", arXiv:1801.01072) by
+ *   - Algorithm 1a (Section 2): Taylor series of ln(u^-1 R) with a Gaussian /
+ *     Rademacher trace estimator (Lemma thm:trace),
+ *   - Algorithm 1b (Section 3): Chebyshev expansion f_m of h(x) = x ln x on
+ *     [0, u] (Lemma lem:prior) with the same trace estimator,
+ * where u = min{1, c * p1~} comes from the power method of Appendix A
+ * (Algorithm alg:power).  Every arithmetic step runs in CUDA kernels of this
+ * library; the host code only validates, sequences launches and copies the
+ * final scalars back.
+ *
+ * Conventions for every call below
+ *   - Ownership: the caller owns R, the probes and every output buffer.  The
+ *     handle owns a device workspace that grows on demand (cudaMalloc) and is
+ *     released by vne_destroy.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  All work is enqueued on it; calls that return host
+ *     outputs synchronise that stream before returning.
+ *   - Errors: every call returns a vne_status and never aborts or throws.
+ *     VNE_ERR_CUDA keeps the CUDA error code, readable by vne_last_cuda_error.
+ *     A handle is not thread safe: use one handle per host thread.
+ *   - Memory: matrix data is DEVICE memory unless vne_matrix.memory is
+ *     VNE_MEM_HOST, in which case the call copies it to the device itself
+ *     (pinned host memory gives the fastest copy).
+ */
+#ifndef VNE_H
+#define VNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vne_status {
+    VNE_OK = 0,
+    VNE_ERR_INVALID_ARG = 1,    /* NULL pointer, n < 1, m < 1, s < 1, bad enum, ld < n ... */
+    VNE_ERR_NOT_UNIT_TRACE = 2, /* check_trace set and |tr R - 1| > 1e-6 (Section 1.1)     */
+    VNE_ERR_BAD_INTERVAL = 3,   /* u <= 0, u > 1 or non-finite (Algorithms 1a/1b, step 3) */
+    VNE_ERR_OOM = 4,            /* workspace allocation failed                             */
+    VNE_ERR_CUDA = 5,           /* a CUDA runtime call failed; see vne_last_cuda_error     */
+    VNE_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up                      */
+    VNE_ERR_NONFINITE = 7,      /* a moment or the estimate is NaN / Inf                   */
+    VNE_ERR_UNSUPPORTED = 8     /* valid but not implemented combination                   */
+} vne_status;
+
+/* vne_matrix.layout */
+enum { VNE_DENSE = 0, VNE_DIA = 1 };
+/* vne_matrix.dtype: storage type of the matrix entries */
+enum { VNE_F64 = 0, VNE_F32 = 1 };
+/* vne_params.precision: arithmetic of the R.Y products of the recurrence
+ *   F64     : FP64 operands, FP64 accumulation (dense and banded)
+ *   F32     : FP32 operands, FP32 accumulation (dense and banded)
+ *   BF16    : R and Y rounded to bf16, FP32 accumulation on the tensor cores
+ *   BF16X3  : R = R_hi + R_lo, Y = Y_hi + Y_lo in bf16, products
+ *             R_hi Y_hi + R_hi Y_lo + R_lo Y_hi accumulated in FP32 (dense only)
+ * The three-term update keeps an FP32 (or FP64) master copy of Y; moments,
+ * coefficients and the final combination are always FP64. */
+enum { VNE_PREC_F64 = 0, VNE_PREC_F32 = 1, VNE_PREC_BF16 = 2, VNE_PREC_BF16X3 = 3 };
+/* vne_params.probe: law of the trace-estimator probe vectors g_j */
+enum { VNE_RADEMACHER = 0, VNE_GAUSSIAN = 1 };
+/* vne_matrix.memory */
+enum { VNE_MEM_DEVICE = 0, VNE_MEM_HOST = 1 };
+/* vne_suggest_m.method */
+enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1 };
+
+/* The density matrix R (eq. R1).
+ *   n        : order of R (n >= 1).
+ *   layout   : VNE_DENSE -- row-major, entry (i, k) at data[i*ld + k], ld >= n.
+ *                           Only symmetric R is meaningful; the full square is read.
+ *              VNE_DIA   -- symmetric banded: n_diags stored diagonals with offsets
+ *                           0..n_diags-1, entry R[i, i+d] at data[d*ld + i] for
+ *                           i < n-d (the rest of each row is ignored); the lower
+ *                           triangle is implied by symmetry.  ld >= n.
+ *   dtype    : VNE_F64 or VNE_F32.
+ *   data     : pointer to the entries (device, or host if memory == VNE_MEM_HOST).
+ *   memory   : VNE_MEM_DEVICE or VNE_MEM_HOST. */
+typedef struct vne_matrix {
+    int64_t n;
+    int32_t layout;
+    int32_t dtype;
+    const void* data;
+    int64_t ld;
+    int32_t n_diags;
+    int32_t memory;
+} vne_matrix;
+
+/* Estimator parameters (Algorithms 1a / 1b and alg:power).
+ *   m            : polynomial degree (Chebyshev) / number of Taylor terms, m >= 1.
+ *   s            : number of probe vectors, s >= 1.
+ *   probe        : VNE_RADEMACHER or VNE_GAUSSIAN.
+ *   precision    : VNE_PREC_*.
+ *   seed         : seeds the SplitMix64 counter generator of the probes (entry
+ *                  (i, j) of the n x s probe block uses counter j*n + i; Gaussian
+ *                  entries use counters 2e, 2e+1 and Box-Muller) and of the
+ *                  power method's start vectors (seed ^ 0x5851F42D4C957F2D).
+ *   power_iters  : t of Algorithm alg:power (t >= 1).
+ *   power_trials : q of Algorithm alg:power (q >= 1).
+ *   u_scale      : c in u = min{1, c * p1~}; the algorithms print c = 6, the
+ *                  experiments of Section 6 use c = 1 and c = 6.  0 means 1.
+ *   u_override   : > 0 skips the power method and uses this u.
+ *   check_trace  : nonzero: reject R with |tr R - 1| > 1e-6 (VNE_ERR_NOT_UNIT_TRACE). */
+typedef struct vne_params {
+    int32_t m;
+    int32_t s;
+    int32_t probe;
+    int32_t precision;
+    uint64_t seed;
+    int32_t power_iters;
+    int32_t power_trials;
+    double u_scale;
+    double u_override;
+    int32_t check_trace;
+    int32_t reserved;
+} vne_params;
+
+typedef struct vne_handle vne_handle;
+
+/* Create a handle bound to CUDA device `device`.  No workspace is allocated
+ * until the first estimator call. */
+vne_status vne_create(vne_handle** h, int device);
+/* Free the handle and its workspace (synchronises the device). NULL is a no-op. */
+void vne_destroy(vne_handle* h);
+
+/* Algorithm 1b (Section 3): H~ = -(1/s) sum_j g_j^T f_m(R) g_j with f_m the
+ * degree-m Chebyshev expansion of x ln x on [0, u] (Lemma lem:prior).
+ * The moments mu[k, j] = g_j^T T_k((2/u)R - I) g_j, k = 0..m, are produced by
+ * the forward three-term recurrence Y_k = 2((2/u)R - I)Y_{k-1} - Y_{k-2}
+ * (equivalent to the Clenshaw form of Appendix C) and combined in FP64.
+ *   H_out       : host, 1 double (required).
+ *   moments_out : host, (m+1)*s doubles, row k = moment k of every probe, or NULL.
+ *   u_out       : host, 1 double (the interval end u actually used), or NULL. */
+vne_status vne_entropy_chebyshev(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                                 double* H_out, double* moments_out, double* u_out,
+                                 void* stream);
+
+/* Algorithm 1a (Section 2): H~ = ln u^-1 + (1/s) sum_j sum_{k=1}^m
+ * g_j^T R (I - R/u)^k g_j / k.  moments_out (if not NULL) receives
+ * tau[k, j] = g_j^T R (I - R/u)^k g_j for k = 0..m ((m+1)*s doubles). */
+vne_status vne_entropy_taylor(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                              double* H_out, double* moments_out, double* u_out,
+                              void* stream);
+
+/* Both estimators on the same R, probes and u: one power method, and the two
+ * recurrences share every pass over R (their probe blocks are placed side by
+ * side, 2s columns).  Outputs as in the two calls above (moment buffers may be
+ * NULL). */
+vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                            double* H_cheb, double* H_taylor,
+                            double* moments_cheb, double* moments_taylor,
+                            double* u_out, void* stream);
+
+/* Algorithm alg:power: p1~ = max_j x_t^T R x_t / x_t^T x_t over q = power_trials
+ * start vectors in {+1,-1}^n after t = power_iters products (each iterate is
+ * divided by its 2-norm, which leaves the Rayleigh quotient unchanged).  The
+ * products use the arithmetic of p->precision (BF16 modes use bf16 R with FP32
+ * accumulation); the Rayleigh quotient is accumulated in FP64.
+ *   lam_out : host, 1 double. */
+vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                          double* lam_out, void* stream);
+
+/* The probe block the estimators draw: out[j*n + i] = g_j[i] (FP64, device,
+ * n*s doubles, caller-owned).  Lets callers check the generator. */
+vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, uint64_t seed,
+                           double* out, void* stream);
+
+/* Per-kernel timing: when enabled, the handle brackets every launch of the
+ * recurrence kernels with CUDA events on the call's stream.  vne_profile_read
+ * returns the total time (ms) and the launch count of kernel class `kind`
+ * (0 = dense tensor-core step, 1 = dense SIMT step, 2 = banded step,
+ * 3 = power-method step) since the last reset. */
+vne_status vne_profile_enable(vne_handle* h, int32_t on);
+vne_status vne_profile_read(vne_handle* h, int32_t kind, double* total_ms, int64_t* launches);
+vne_status vne_profile_reset(vne_handle* h);
+
+/* Number of the library's own kernel launches enqueued by this handle so far. */
+int64_t vne_launch_count(const vne_handle* h);
+
+/* Human-readable name of a status code (static string). */
+const char* vne_status_string(vne_status s);
+/* cudaError_t behind the last VNE_ERR_CUDA of this handle (0 if none). */
+int32_t vne_last_cuda_error(const vne_handle* h);
+/* Degree suggested by Theorem thm:taylor (m = ceil((u/l) ln(1/eps))) or
+ * Theorem thm:cheb (m = sqrt(u / (2 eps l ln(1/(1-l)))), rounded up);
+ * returns -1 for invalid arguments. */
+int32_t vne_suggest_m(int32_t method, double u, double ell, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VNE_H */

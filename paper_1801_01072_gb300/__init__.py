@@ -1,0 +1,246 @@
+"""GB300-native randomized von Neumann entropy estimators.
+
+Python binding of the C ABI in ``include/vne.h``: it only marshals torch
+tensors (data pointers, sizes, the current CUDA stream) into the library's
+calls.  Every step of the method runs in the library's CUDA kernels; there
+is no CPU fallback.
+
+    import paper_1801_01072_gb300 as vne
+    res = vne.entropy_chebyshev(R, m=20, s=50, seed=1)          # Algorithm 1b
+    res = vne.entropy_taylor(R, m=20, s=50, seed=1)             # Algorithm 1a
+    both = vne.entropy_both(R, m=40, s=128, precision="bf16")   # shared passes
+    lam = vne.lambda_max(R)                                     # Algorithm alg:power
+
+``R`` is a dense (n, n) tensor (row-major) or, with ``layout="dia"``, the
+(D, n) band storage ``vals[d, i] = R[i, i + d]`` of a symmetric banded R.
+It may live on the GPU (device pointer) or in host memory (the call then
+copies it itself).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import VneError
+
+__all__ = ["entropy_chebyshev", "entropy_taylor", "entropy_both", "lambda_max", "probe_block",
+           "Handle", "Result", "BothResult", "VneError", "suggest_m", "load"]
+
+
+def load():
+    return _lib.load()
+
+
+@dataclass
+class Result:
+    H: float
+    u: float
+    moments: np.ndarray | None  # (m+1, s)
+
+
+@dataclass
+class BothResult:
+    H_chebyshev: float
+    H_taylor: float
+    u: float
+    moments_chebyshev: np.ndarray | None
+    moments_taylor: np.ndarray | None
+
+
+class Handle:
+    """Owns a library handle (and its device workspace) on one device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _lib.load()
+        h = C.c_void_p()
+        st = self.lib.vne_create(C.byref(h), int(device))
+        if st != 0:
+            raise VneError(st, "vne_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.vne_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int, what: str):
+        if st != 0:
+            raise VneError(st, what, int(self.lib.vne_last_cuda_error(self.h)))
+
+    # profiling of the recurrence kernels (CUDA events inside the library)
+    def profile(self, on: bool = True):
+        self.check(self.lib.vne_profile_enable(self.h, 1 if on else 0), "vne_profile_enable")
+        self.check(self.lib.vne_profile_reset(self.h), "vne_profile_reset")
+
+    def profile_read(self, kind: int):
+        ms = C.c_double()
+        n = C.c_int64()
+        self.check(self.lib.vne_profile_read(self.h, kind, C.byref(ms), C.byref(n)),
+                   "vne_profile_read")
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(self.lib.vne_launch_count(self.h))
+
+
+_HANDLES: dict[int, Handle] = {}
+
+
+def _handle(device: int) -> Handle:
+    h = _HANDLES.get(device)
+    if h is None:
+        h = Handle(device)
+        _HANDLES[device] = h
+    return h
+
+
+def _matrix(R, layout: str):
+    import torch
+
+    if not isinstance(R, torch.Tensor):
+        R = torch.as_tensor(np.ascontiguousarray(R))
+    if R.dim() != 2:
+        raise ValueError("R must be 2-D")
+    if R.dtype not in (torch.float64, torch.float32):
+        raise ValueError("R must be float64 or float32")
+    if R.stride(1) != 1:
+        R = R.contiguous()
+    mat = _lib.VneMatrix()
+    if layout == "dense":
+        if R.shape[0] != R.shape[1]:
+            raise ValueError("dense R must be square")
+        mat.n = R.shape[0]
+        mat.layout = _lib.DENSE
+        mat.n_diags = 0
+    elif layout == "dia":
+        mat.n = R.shape[1]
+        mat.layout = _lib.DIA
+        mat.n_diags = R.shape[0]
+    else:
+        raise ValueError(layout)
+    mat.dtype = _lib.F64 if R.dtype == torch.float64 else _lib.F32
+    mat.data = R.data_ptr()
+    mat.ld = R.stride(0)
+    mat.memory = _lib.MEM_DEVICE if R.is_cuda else _lib.MEM_HOST
+    device = R.device.index if R.is_cuda else torch.cuda.current_device()
+    return mat, R, device
+
+
+def _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace):
+    p = _lib.VneParams()
+    p.m = int(m)
+    p.s = int(s)
+    p.probe = _lib.PROBE[probe]
+    p.precision = _lib.PREC[precision]
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.power_iters = int(power_iters)
+    p.power_trials = int(power_trials)
+    p.u_scale = float(u_scale)
+    p.u_override = float(u) if u is not None else 0.0
+    p.check_trace = 1 if check_trace else 0
+    return p
+
+
+def _stream(device, stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _estimate(fn_name, R, m, s, seed, probe, precision, power_iters, power_trials, u_scale,
+              u, check_trace, moments, layout, stream):
+    mat, keep, dev = _matrix(R, layout)
+    h = _handle(dev)
+    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace)
+    H = C.c_double()
+    uo = C.c_double()
+    mom = np.zeros((m + 1, s), dtype=np.float64) if moments else None
+    st = getattr(h.lib, fn_name)(h.h, C.byref(mat), C.byref(p), C.byref(H), _dptr(mom),
+                                 C.byref(uo), _stream(dev, stream))
+    h.check(st, fn_name)
+    del keep
+    return Result(H.value, uo.value, mom)
+
+
+def entropy_chebyshev(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
+                      precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
+                      u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
+                      moments: bool = False, layout: str = "dense", stream=None) -> Result:
+    """Algorithm 1b: -(1/s) sum_j g_j^T f_m(R) g_j (Section 3)."""
+    return _estimate("vne_entropy_chebyshev", R, m, s, seed, probe, precision, power_iters,
+                     power_trials, u_scale, u, check_trace, moments, layout, stream)
+
+
+def entropy_taylor(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
+                   precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
+                   u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
+                   moments: bool = False, layout: str = "dense", stream=None) -> Result:
+    """Algorithm 1a: ln u^-1 + (1/s) sum_j sum_k g_j^T R (I - R/u)^k g_j / k (Section 2)."""
+    return _estimate("vne_entropy_taylor", R, m, s, seed, probe, precision, power_iters,
+                     power_trials, u_scale, u, check_trace, moments, layout, stream)
+
+
+def entropy_both(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
+                 precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
+                 u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
+                 moments: bool = False, layout: str = "dense", stream=None) -> BothResult:
+    """Algorithms 1a and 1b on the same probes and u, sharing every pass over R."""
+    mat, keep, dev = _matrix(R, layout)
+    h = _handle(dev)
+    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace)
+    Hc, Ht, uo = C.c_double(), C.c_double(), C.c_double()
+    mc = np.zeros((m + 1, s)) if moments else None
+    mt = np.zeros((m + 1, s)) if moments else None
+    st = h.lib.vne_entropy_both(h.h, C.byref(mat), C.byref(p), C.byref(Hc), C.byref(Ht),
+                                _dptr(mc), _dptr(mt), C.byref(uo), _stream(dev, stream))
+    h.check(st, "vne_entropy_both")
+    del keep
+    return BothResult(Hc.value, Ht.value, uo.value, mc, mt)
+
+
+def lambda_max(R, power_iters: int = 30, power_trials: int = 1, seed: int = 0,
+               precision: str = "f64", u_scale: float = 1.0, layout: str = "dense",
+               stream=None) -> float:
+    """Algorithm alg:power: max over trials of the Rayleigh quotient of R^t x_0."""
+    mat, keep, dev = _matrix(R, layout)
+    h = _handle(dev)
+    p = _params(1, 1, seed, "rademacher", precision, power_iters, power_trials, u_scale, None,
+                False)
+    lam = C.c_double()
+    st = h.lib.vne_lambda_max(h.h, C.byref(mat), C.byref(p), C.byref(lam), _stream(dev, stream))
+    h.check(st, "vne_lambda_max")
+    del keep
+    return lam.value
+
+
+def probe_block(n: int, s: int, seed: int, probe: str = "rademacher", device: int = 0):
+    """The library's probe block as a (n, s) float64 CUDA tensor (column j = g_j)."""
+    import torch
+
+    h = _handle(device)
+    out = torch.empty((s, n), dtype=torch.float64, device=f"cuda:{device}")
+    st = h.lib.vne_probe_block(h.h, int(n), int(s), _lib.PROBE[probe], int(seed),
+                               C.c_void_p(out.data_ptr()), _stream(device, None))
+    h.check(st, "vne_probe_block")
+    return out.t()
+
+
+def suggest_m(method: str, u: float, ell: float, eps: float) -> int:
+    lib = _lib.load()
+    return int(lib.vne_suggest_m(0 if method == "taylor" else 1, u, ell, eps))

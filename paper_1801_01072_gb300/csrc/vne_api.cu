@@ -1,0 +1,650 @@
+// Host runtime behind the C ABI of include/vne.h: argument checks, the
+// workspace, and the launch sequence of one estimator call
+//   [H2D copy] -> [trace] -> operand prep -> power method (Appendix A) ->
+//   probes -> m (or m+1) recurrence steps -> FP64 combine -> D2H of scalars.
+// Every arithmetic step is a kernel of this library; the host only sequences.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/vne.h"
+#include "vne_common.cuh"
+#include "vne_internal.h"
+
+using namespace vne;
+
+struct ProfEvent {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct vne_handle {
+    int device = 0;
+    int sm_count = 0;
+    int32_t last_err = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* host_sc = nullptr;  // pinned
+    int prof_on = 0;
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfEvent> pending;
+    int64_t launches = 0;
+};
+
+namespace {
+
+enum Mode { MODE_CHEB = 1, MODE_TAYLOR = 2, MODE_BOTH = 3, MODE_POWER = 4 };
+
+struct Outputs {
+    double* H_cheb = nullptr;
+    double* H_taylor = nullptr;
+    double* mom_cheb = nullptr;
+    double* mom_taylor = nullptr;
+    double* u = nullptr;
+    double* lam = nullptr;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Two-pass bump allocator: pass 1 (base == nullptr) only measures.
+struct Bump {
+    char* base;
+    size_t off = 0;
+    explicit Bump(char* b) : base(b) {}
+    template <typename T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T) + 16;
+        return p;
+    }
+};
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct Call {
+    vne_handle* h;
+    cudaStream_t st;
+    cudaError_t err = cudaSuccess;
+    bool ok() const { return err == cudaSuccess; }
+    void chk(cudaError_t e) {
+        if (err == cudaSuccess && e != cudaSuccess) err = e;
+    }
+    void launched(cudaError_t e) {
+        h->launches++;
+        chk(e);
+    }
+    // profiling bracket around one launch of kernel class `kind`
+    cudaEvent_t ev() {
+        if (h->ev_used == h->ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            h->ev_pool.push_back(e);
+        }
+        return h->ev_pool[h->ev_used++];
+    }
+    cudaEvent_t pa = nullptr;
+    void prof_begin() {
+        pa = nullptr;
+        if (!h->prof_on) return;
+        pa = ev();
+        if (pa) cudaEventRecord(pa, st);
+    }
+    void prof_end(int kind) {
+        if (!h->prof_on || !pa) return;
+        cudaEvent_t b = ev();
+        if (!b) return;
+        cudaEventRecord(b, st);
+        h->pending.push_back({kind, pa, b});
+    }
+};
+
+vne_status map_err(vne_handle* h, cudaError_t e) {
+    if (e == cudaSuccess) return VNE_OK;
+    h->last_err = (int32_t)e;
+    if (e == cudaErrorMemoryAllocation) return VNE_ERR_OOM;
+    return VNE_ERR_CUDA;
+}
+
+vne_status ensure_ws(vne_handle* h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return VNE_OK;
+    if (h->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc((void**)&h->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        e = cudaMalloc((void**)&h->ws, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->ws = nullptr;
+            h->last_err = (int32_t)e;
+            return VNE_ERR_OOM;
+        }
+        want = bytes;
+    }
+    h->ws_bytes = want;
+    return VNE_OK;
+}
+
+size_t elt_size(int dtype) { return dtype == VNE_F64 ? 8 : 4; }
+
+vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
+    if (!R || !p) return VNE_ERR_INVALID_ARG;
+    if (R->n < 1 || !R->data) return VNE_ERR_INVALID_ARG;
+    if (R->layout != VNE_DENSE && R->layout != VNE_DIA) return VNE_ERR_INVALID_ARG;
+    if (R->dtype != VNE_F64 && R->dtype != VNE_F32) return VNE_ERR_INVALID_ARG;
+    if (R->memory != VNE_MEM_DEVICE && R->memory != VNE_MEM_HOST) return VNE_ERR_INVALID_ARG;
+    if (R->ld < R->n) return VNE_ERR_INVALID_ARG;
+    if (R->layout == VNE_DIA) {
+        if (R->n_diags < 1) return VNE_ERR_INVALID_ARG;
+        if (dia_supported_halfbw(R->n_diags) < 0) return VNE_ERR_UNSUPPORTED;
+    }
+    if (p->precision < VNE_PREC_F64 || p->precision > VNE_PREC_BF16X3) return VNE_ERR_INVALID_ARG;
+    if (p->probe != VNE_RADEMACHER && p->probe != VNE_GAUSSIAN) return VNE_ERR_INVALID_ARG;
+    // u_override > 0 replaces the power method; u must lie in (0, 1] (Algorithms 1a/1b step 3)
+    if (std::isnan(p->u_override) || std::isinf(p->u_override) || p->u_override > 1.0)
+        return VNE_ERR_BAD_INTERVAL;
+    if (!(p->u_scale >= 0.0) || std::isinf(p->u_scale)) return VNE_ERR_INVALID_ARG;
+    if (p->u_override <= 0.0) {
+        if (p->power_iters < 1 || p->power_trials < 1 || p->power_trials > 8)
+            return VNE_ERR_INVALID_ARG;
+    }
+    if (mode != MODE_POWER) {
+        if (p->m < 1 || p->s < 1) return VNE_ERR_INVALID_ARG;
+        if (p->m > 100000) return VNE_ERR_INVALID_ARG;
+        const int S = (mode == MODE_BOTH) ? 2 * p->s : p->s;
+        if (R->layout == VNE_DIA) {
+            if (p->precision > VNE_PREC_F32) return VNE_ERR_UNSUPPORTED;
+            if (p->s > 256 || S > 256) return VNE_ERR_UNSUPPORTED;
+        } else if (p->precision >= VNE_PREC_BF16) {
+            if (S > 512) return VNE_ERR_UNSUPPORTED;
+        }
+        if ((int64_t)S * R->n > ((int64_t)1 << 40)) return VNE_ERR_UNSUPPORTED;
+    } else {
+        if (R->layout == VNE_DIA && p->precision > VNE_PREC_F32) return VNE_ERR_UNSUPPORTED;
+    }
+    return VNE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One estimator call.
+// ---------------------------------------------------------------------------
+vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mode, Outputs out,
+               void* stream) {
+    if (!h) return VNE_ERR_INVALID_ARG;
+    vne_status vs = validate(Rin, p, mode);
+    if (vs != VNE_OK) return vs;
+    DeviceGuard guard(h->device);
+    Call c{h, (cudaStream_t)stream};
+
+    const vne_matrix R = *Rin;
+    const int64_t n = R.n;
+    const bool dense = R.layout == VNE_DENSE;
+    const int prec = p->precision;
+    const bool tc = dense && prec >= VNE_PREC_BF16;
+    const bool x3 = prec == VNE_PREC_BF16X3;
+    const bool f64 = prec == VNE_PREC_F64;
+    const bool has_cheb = mode == MODE_CHEB || mode == MODE_BOTH;
+    const bool has_tay = mode == MODE_TAYLOR || mode == MODE_BOTH;
+    const int s = mode == MODE_POWER ? 1 : p->s;
+    const int m = mode == MODE_POWER ? 0 : p->m;
+    const int S = mode == MODE_BOTH ? 2 * s : s;
+    const int q = p->power_trials < 1 ? 1 : p->power_trials;
+    const bool do_power = !(p->u_override > 0.0);
+    const double u_scale = p->u_scale > 0.0 ? p->u_scale : 1.0;
+    const int T_steps = mode == MODE_POWER ? 0 : (has_tay ? m + 1 : m);
+    const int D = dense ? 0 : R.n_diags;
+
+    // geometry of each path
+    const int64_t rows_pad = tc ? round_up(n, tc_tile_m()) : n;
+    const int64_t ldk = tc ? round_up(n, tc_tile_k()) : n;
+    const int S_pad = (int)round_up(S, 32);
+    int splitk = 1, ntiles = 1, ntiles0 = 1, dia_grid = 0;
+    int rows_per_tile0 = 256;
+    if (mode != MODE_POWER) {
+        if (dense && !tc) {
+            splitk = dense_simt_splitk(n, S, h->sm_count);
+            ntiles = ntiles0 = (int)((n + 255) / 256);
+        } else if (tc) {
+            rows_per_tile0 = tc_tile_m();
+            ntiles = ntiles0 = (int)(rows_pad / tc_tile_m());
+        } else {
+            dia_grid = dia_step_grid(f64, D, n, S, h->sm_count);
+            if (dia_grid < 1) return VNE_ERR_UNSUPPORTED;
+            ntiles = dia_grid;
+            rows_per_tile0 = 4096;
+            ntiles0 = (int)((n + rows_per_tile0 - 1) / rows_per_tile0);
+        }
+    }
+    const int power_blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 4 * h->sm_count)
+                                   : 4 * h->sm_count;
+
+    // ---- workspace plan (two passes) ----
+    const size_t vt = f64 ? 8 : 4;  // master / operand element size of SIMT & DIA paths
+    auto plan = [&](Bump& b, void** Rcopy, void** Rop, __nv_bfloat16** Rhi, __nv_bfloat16** Rlo,
+                    double** sc, double** ppart, unsigned int** counter, void** x0, void** x1,
+                    void** G, uint64_t** bits, void** Yb0, void** Yb1, void** Yb2, void** Zpart,
+                    __nv_bfloat16** Sh, double** part, double** mom_c, double** mom_t) {
+        *sc = b.take<double>(SC_COUNT);
+        *counter = b.take<unsigned int>(64);
+        *ppart = b.take<double>((size_t)std::max(power_blocks, 256) * 3 * q);
+        *Rcopy = nullptr;
+        if (R.memory == VNE_MEM_HOST)
+            *Rcopy = b.take<char>((size_t)(dense ? n : D) * R.ld * elt_size(R.dtype));
+        *Rop = nullptr;
+        *Rhi = *Rlo = nullptr;
+        if (tc) {
+            *Rhi = b.take<__nv_bfloat16>((size_t)rows_pad * ldk);
+            if (x3) *Rlo = b.take<__nv_bfloat16>((size_t)rows_pad * ldk);
+        } else {
+            const int want = f64 ? VNE_F64 : VNE_F32;
+            if (R.dtype != want) *Rop = b.take<char>((size_t)(dense ? n * n : (int64_t)D * n) * vt);
+        }
+        const size_t xs = tc ? 4 : vt;
+        *x0 = b.take<char>((size_t)n * q * xs);
+        *x1 = b.take<char>((size_t)n * q * xs);
+        *G = *Yb0 = *Yb1 = *Yb2 = *Zpart = nullptr;
+        *bits = nullptr;
+        *Sh = nullptr;
+        *part = *mom_c = *mom_t = nullptr;
+        if (mode == MODE_POWER) return;
+        const size_t ms = tc ? 4 : vt;
+        if (!dense && p->probe == VNE_RADEMACHER)
+            *bits = b.take<uint64_t>((size_t)n * ((s + 63) / 64));
+        else
+            *G = b.take<char>((size_t)n * s * ms);
+        *Yb0 = b.take<char>((size_t)n * S * ms);
+        *Yb1 = b.take<char>((size_t)n * S * ms);
+        *Yb2 = b.take<char>((size_t)n * S * ms);
+        if (dense && !tc) *Zpart = b.take<char>((size_t)splitk * S * n * vt);
+        if (tc) *Sh = b.take<__nv_bfloat16>((size_t)4 * S_pad * ldk);
+        *part = b.take<double>((size_t)ntiles0 * S + (size_t)T_steps * ntiles * S);
+        *mom_c = b.take<double>((size_t)(m + 1) * s);
+        *mom_t = b.take<double>((size_t)(m + 1) * s);
+    };
+    void *Rcopy, *Rop, *x0, *x1, *G, *Yb0, *Yb1, *Yb2, *Zpart;
+    __nv_bfloat16 *Rhi, *Rlo, *Sh;
+    double *sc, *ppart, *part, *mom_c, *mom_t;
+    unsigned int* counter;
+    uint64_t* bits;
+    {
+        Bump b0(nullptr);
+        plan(b0, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
+             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t);
+        vs = ensure_ws(h, b0.off + 4096);
+        if (vs != VNE_OK) return vs;
+        Bump b1(h->ws);
+        plan(b1, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
+             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t);
+    }
+    h->ev_used = 0;
+    h->pending.clear();
+
+    c.chk(cudaMemsetAsync(sc, 0, SC_COUNT * sizeof(double), c.st));
+    c.chk(cudaMemsetAsync(counter, 0, 64 * sizeof(unsigned int), c.st));
+
+    // ---- matrix to the device, trace check ----
+    const void* Rdata = R.data;
+    if (R.memory == VNE_MEM_HOST) {
+        const size_t bytes = (size_t)(dense ? n : D) * R.ld * elt_size(R.dtype);
+        c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
+        Rdata = Rcopy;
+    }
+    if (p->check_trace) c.launched(launch_trace(Rdata, R.layout, R.dtype, n, R.ld, ppart, counter, sc, c.st));
+
+    // ---- operands ----
+    const void* Rk = Rdata;  // operand of the SIMT / DIA / power kernels
+    int64_t ldr = R.ld;
+    if (tc) {
+        c.launched(launch_dense_convert_bf16(Rdata, R.dtype, n, R.ld, Rhi, Rlo, rows_pad, ldk, c.st));
+    } else if (Rop) {
+        if (dense) {
+            if (f64) c.launched(launch_dense_convert_f64(Rdata, R.dtype, n, R.ld, (double*)Rop, c.st));
+            else c.launched(launch_dense_convert_f32(Rdata, R.dtype, n, R.ld, (float*)Rop, c.st));
+        } else {
+            c.launched(launch_dia_convert(Rdata, R.dtype, n, R.ld, D, Rop, f64 ? VNE_F64 : VNE_F32, c.st));
+        }
+        Rk = Rop;
+        ldr = n;
+    }
+
+    // ---- power method (Algorithm alg:power) or the given u ----
+    if (do_power) {
+        if (f64) c.launched(launch_power_init<double>((double*)x0, n, q, p->seed, sc, c.st));
+        else c.launched(launch_power_init<float>((float*)x0, n, q, p->seed, sc, c.st));
+        void* xa = x0;
+        void* xb = x1;
+        const int rdt = tc ? 2 : (f64 ? 0 : 1);
+        const void* Rp = tc ? (const void*)Rhi : Rk;
+        const int64_t ldp = tc ? ldk : ldr;
+        for (int it = 0; it <= p->power_iters && c.ok(); ++it) {
+            const int fin = it == p->power_iters;
+            c.prof_begin();
+            if (dense)
+                c.launched(launch_power_step_dense(Rp, rdt, n, ldp, xa, xb, f64, q, sc, ppart,
+                                                   counter, fin, u_scale, power_blocks, c.st));
+            else
+                c.launched(launch_power_step_dia(Rk, f64 ? 0 : 1, n, ldr, D, xa, xb, q, sc, ppart,
+                                                 counter, fin, u_scale, power_blocks, c.st));
+            c.prof_end(3);
+            std::swap(xa, xb);
+        }
+    } else {
+        c.launched(launch_set_u(sc, p->u_override, c.st));
+    }
+
+    // ---- probes, recurrence, combine ----
+    if (mode != MODE_POWER && c.ok()) {
+        Partials P{part, ntiles0, ntiles, S};
+        __nv_bfloat16* sh_hi[2] = {nullptr, nullptr};
+        __nv_bfloat16* sh_lo[2] = {nullptr, nullptr};
+        if (tc) {
+            c.chk(cudaMemsetAsync(Sh, 0, (size_t)4 * S_pad * ldk * sizeof(__nv_bfloat16), c.st));
+            sh_hi[0] = Sh;
+            sh_hi[1] = Sh + (size_t)S_pad * ldk;
+            sh_lo[0] = Sh + (size_t)2 * S_pad * ldk;
+            sh_lo[1] = Sh + (size_t)3 * S_pad * ldk;
+        }
+        if (dense) {
+            if (f64)
+                c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, nullptr, 0,
+                                                     n, S, s, p->probe, p->seed, P, 256, c.st));
+            else
+                c.launched(launch_dense_init<float>((float*)G, (float*)Yb0, sh_hi[0],
+                                                    x3 ? sh_lo[0] : nullptr, ldk, n, S, s,
+                                                    p->probe, p->seed, P, rows_per_tile0, c.st));
+        } else {
+            const int Wd = (s + 63) / 64;
+            if (f64)
+                c.launched(launch_dia_init<double>((double*)G, bits, Wd, (double*)Yb0, n, S, s,
+                                                   p->probe, p->seed, P, rows_per_tile0, c.st));
+            else
+                c.launched(launch_dia_init<float>((float*)G, bits, Wd, (float*)Yb0, n, S, s,
+                                                  p->probe, p->seed, P, rows_per_tile0, c.st));
+        }
+        void* Yb[3] = {Yb0, Yb1, Yb2};
+        for (int t = 1; t <= T_steps && c.ok(); ++t) {
+            StepCols cols{};
+            const bool cheb_on = has_cheb && t <= m;
+            cols.cheb_c0 = 0;
+            cols.ncheb = cheb_on ? s : 0;
+            cols.cheb_kind = cheb_on ? (t == 1 ? EPI_CHEB1 : EPI_CHEB) : EPI_NONE;
+            cols.tay_c0 = has_cheb ? s : 0;
+            cols.ntay = has_tay ? s : 0;
+            const int col0 = cheb_on ? 0 : cols.tay_c0;
+            const int ncols = cols.ncheb + cols.ntay;
+            void* Yp = Yb[(t - 1) % 3];
+            void* Yp2 = Yb[(t + 1) % 3];
+            void* Yn = Yb[t % 3];
+            c.prof_begin();
+            if (tc) {
+                TcStep a{};
+                a.Rhi = Rhi;
+                a.Rlo = x3 ? Rlo : nullptr;
+                a.Yhi = sh_hi[(t - 1) & 1];
+                a.Ylo = x3 ? sh_lo[(t - 1) & 1] : nullptr;
+                a.Yhi_out = sh_hi[t & 1];
+                a.Ylo_out = x3 ? sh_lo[t & 1] : nullptr;
+                a.G = (const float*)G;
+                a.Yprev = (const float*)Yp;
+                a.Yprev2 = (const float*)Yp2;
+                a.Ynew = (float*)Yn;
+                a.n = n;
+                a.rows_pad = rows_pad;
+                a.ldk = ldk;
+                a.S = S;
+                a.s = s;
+                a.split = 1;
+                a.cols = cols;
+                a.sc = sc;
+                a.P = P;
+                a.t = t;
+                c.launched(launch_tc_step(a, h->sm_count, c.st));
+                c.prof_end(0);
+            } else if (dense) {
+                if (f64) {
+                    c.launched(launch_dense_simt_step<double>((const double*)Rk, ldr, n,
+                                                              (const double*)Yp, (double*)Zpart, S,
+                                                              col0, ncols, splitk, c.st));
+                    c.launched(launch_dense_simt_epilogue<double>(
+                        (const double*)Zpart, splitk, (const double*)G, (const double*)Yp,
+                        (const double*)Yp2, (double*)Yn, n, S, s, cols, sc, P, t, c.st));
+                } else {
+                    c.launched(launch_dense_simt_step<float>((const float*)Rk, ldr, n,
+                                                             (const float*)Yp, (float*)Zpart, S,
+                                                             col0, ncols, splitk, c.st));
+                    c.launched(launch_dense_simt_epilogue<float>(
+                        (const float*)Zpart, splitk, (const float*)G, (const float*)Yp,
+                        (const float*)Yp2, (float*)Yn, n, S, s, cols, sc, P, t, c.st));
+                }
+                c.prof_end(1);
+            } else {
+                const int Wd = (s + 63) / 64;
+                if (f64)
+                    c.launched(launch_dia_step<double>((const double*)Rk, ldr, D, n,
+                                                       (const double*)Yp, (const double*)Yp2,
+                                                       (double*)Yn, (const double*)G, bits, Wd, S,
+                                                       s, cols, sc, P, t, dia_grid, c.st));
+                else
+                    c.launched(launch_dia_step<float>((const float*)Rk, ldr, D, n,
+                                                      (const float*)Yp, (const float*)Yp2,
+                                                      (float*)Yn, (const float*)G, bits, Wd, S, s,
+                                                      cols, sc, P, t, dia_grid, c.st));
+                c.prof_end(2);
+            }
+        }
+        if (c.ok())
+            c.launched(launch_combine(P, s, m, has_cheb ? 0 : -1, has_tay ? (has_cheb ? s : 0) : -1,
+                                      mom_c, mom_t, sc, c.st));
+    }
+
+    // ---- results ----
+    if (c.ok()) c.chk(cudaMemcpyAsync(h->host_sc, sc, SC_COUNT * sizeof(double),
+                                      cudaMemcpyDeviceToHost, c.st));
+    if (c.ok() && out.mom_cheb && has_cheb)
+        c.chk(cudaMemcpyAsync(out.mom_cheb, mom_c, (size_t)(m + 1) * s * sizeof(double),
+                              cudaMemcpyDeviceToHost, c.st));
+    if (c.ok() && out.mom_taylor && has_tay)
+        c.chk(cudaMemcpyAsync(out.mom_taylor, mom_t, (size_t)(m + 1) * s * sizeof(double),
+                              cudaMemcpyDeviceToHost, c.st));
+    {
+        cudaError_t e = cudaStreamSynchronize(c.st);
+        c.chk(e);
+    }
+    if (!c.ok()) {
+        cudaGetLastError();
+        return map_err(h, c.err);
+    }
+    for (const ProfEvent& pe : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+            h->prof_ms[pe.kind] += ms;
+            h->prof_n[pe.kind] += 1;
+        }
+    }
+    h->pending.clear();
+    const double* hs = h->host_sc;
+    uint64_t flags;
+    std::memcpy(&flags, &hs[SC_FLAGS], sizeof(flags));
+    if (p->check_trace && !(std::fabs(hs[SC_TRACE] - 1.0) <= 1e-6)) return VNE_ERR_NOT_UNIT_TRACE;
+    if (flags & FLAG_TIMEOUT) return VNE_ERR_TIMEOUT;
+    if (flags & FLAG_BAD_INTERVAL) return VNE_ERR_BAD_INTERVAL;
+    if (flags & FLAG_NONFINITE) return VNE_ERR_NONFINITE;
+    if (out.H_cheb) *out.H_cheb = hs[SC_H_CHEB];
+    if (out.H_taylor) *out.H_taylor = hs[SC_H_TAYLOR];
+    if (out.u) *out.u = hs[SC_U];
+    if (out.lam) *out.lam = hs[SC_LAM];
+    return VNE_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+vne_status vne_create(vne_handle** out, int device) {
+    if (!out) return VNE_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return VNE_ERR_INVALID_ARG;
+    }
+    vne_handle* h = new (std::nothrow) vne_handle();
+    if (!h) return VNE_ERR_OOM;
+    h->device = device;
+    DeviceGuard guard(device);
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return VNE_ERR_CUDA;
+    }
+    if (cudaMallocHost((void**)&h->host_sc, SC_COUNT * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return VNE_ERR_OOM;
+    }
+    *out = h;
+    return VNE_OK;
+}
+
+void vne_destroy(vne_handle* h) {
+    if (!h) return;
+    DeviceGuard guard(h->device);
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    if (h->host_sc) cudaFreeHost(h->host_sc);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+vne_status vne_entropy_chebyshev(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                                 double* H_out, double* moments_out, double* u_out, void* stream) {
+    if (!H_out) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.H_cheb = H_out;
+    o.mom_cheb = moments_out;
+    o.u = u_out;
+    return run(h, R, p, MODE_CHEB, o, stream);
+}
+
+vne_status vne_entropy_taylor(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                              double* H_out, double* moments_out, double* u_out, void* stream) {
+    if (!H_out) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.H_taylor = H_out;
+    o.mom_taylor = moments_out;
+    o.u = u_out;
+    return run(h, R, p, MODE_TAYLOR, o, stream);
+}
+
+vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                            double* H_cheb, double* H_taylor, double* moments_cheb,
+                            double* moments_taylor, double* u_out, void* stream) {
+    if (!H_cheb || !H_taylor) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.H_cheb = H_cheb;
+    o.H_taylor = H_taylor;
+    o.mom_cheb = moments_cheb;
+    o.mom_taylor = moments_taylor;
+    o.u = u_out;
+    return run(h, R, p, MODE_BOTH, o, stream);
+}
+
+vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                          double* lam_out, void* stream) {
+    if (!lam_out) return VNE_ERR_INVALID_ARG;
+    if (p && p->u_override > 0.0) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.lam = lam_out;
+    return run(h, R, p, MODE_POWER, o, stream);
+}
+
+vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, uint64_t seed,
+                           double* out, void* stream) {
+    if (!h || !out || n < 1 || s < 1) return VNE_ERR_INVALID_ARG;
+    if (probe != VNE_RADEMACHER && probe != VNE_GAUSSIAN) return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    cudaError_t e = launch_probe_block_f64(out, n, s, probe, seed, (cudaStream_t)stream);
+    h->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return map_err(h, e);
+}
+
+vne_status vne_profile_enable(vne_handle* h, int32_t on) {
+    if (!h) return VNE_ERR_INVALID_ARG;
+    h->prof_on = on ? 1 : 0;
+    return VNE_OK;
+}
+
+vne_status vne_profile_read(vne_handle* h, int32_t kind, double* total_ms, int64_t* launches) {
+    if (!h || kind < 0 || kind > 3) return VNE_ERR_INVALID_ARG;
+    if (total_ms) *total_ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_n[kind];
+    return VNE_OK;
+}
+
+vne_status vne_profile_reset(vne_handle* h) {
+    if (!h) return VNE_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+    }
+    return VNE_OK;
+}
+
+int64_t vne_launch_count(const vne_handle* h) { return h ? h->launches : -1; }
+
+const char* vne_status_string(vne_status s) {
+    switch (s) {
+        case VNE_OK: return "VNE_OK";
+        case VNE_ERR_INVALID_ARG: return "VNE_ERR_INVALID_ARG";
+        case VNE_ERR_NOT_UNIT_TRACE: return "VNE_ERR_NOT_UNIT_TRACE";
+        case VNE_ERR_BAD_INTERVAL: return "VNE_ERR_BAD_INTERVAL";
+        case VNE_ERR_OOM: return "VNE_ERR_OOM";
+        case VNE_ERR_CUDA: return "VNE_ERR_CUDA";
+        case VNE_ERR_TIMEOUT: return "VNE_ERR_TIMEOUT";
+        case VNE_ERR_NONFINITE: return "VNE_ERR_NONFINITE";
+        case VNE_ERR_UNSUPPORTED: return "VNE_ERR_UNSUPPORTED";
+    }
+    return "VNE_ERR_UNKNOWN";
+}
+
+int32_t vne_last_cuda_error(const vne_handle* h) { return h ? h->last_err : 0; }
+
+int32_t vne_suggest_m(int32_t method, double u, double ell, double eps) {
+    if (!(u > 0.0 && u <= 1.0) || !(ell > 0.0 && ell <= u) || !(eps > 0.0 && eps < 1.0)) return -1;
+    double m;
+    if (method == VNE_METHOD_TAYLOR) m = std::ceil((u / ell) * std::log(1.0 / eps));
+    else if (method == VNE_METHOD_CHEBYSHEV)
+        m = std::ceil(std::sqrt(u / (2.0 * eps * ell * std::log(1.0 / (1.0 - ell)))));
+    else return -1;
+    if (!(m < 2.0e9)) return -1;
+    return (int32_t)m;
+}
+
+}  // extern "C"

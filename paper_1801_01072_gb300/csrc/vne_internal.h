@@ -1,0 +1,131 @@
+// Internal launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace vne {
+
+// Moment partial sums: slot 0 holds ntiles0 x S partials of g^T Y_0 terms
+// (written by the init kernels), slot t >= 1 holds ntiles x S partials
+// written by recurrence step t.  Column c of a step belongs to probe c % s.
+struct Partials {
+    double* base;
+    int ntiles0;
+    int ntiles;
+    int S;
+    __host__ __device__ double* slot(int t) const {
+        return t == 0 ? base : base + (size_t)ntiles0 * S + (size_t)(t - 1) * ntiles * S;
+    }
+};
+
+// Epilogue kinds of one recurrence step t (Z = R Y_{t-1}):
+//   CHEB1 : Y_1 = a Z - G              (a = 2/u), moment g^T Y_1
+//   CHEB  : Y_t = 2(a Z - Y_{t-1}) - Y_{t-2},      moment g^T Y_t
+//   TAYLOR: Y_t = Y_{t-1} - Z / u,                 moment g^T Z  (= tau_{t-1})
+enum EpiKind { EPI_NONE = 0, EPI_CHEB1 = 1, EPI_CHEB = 2, EPI_TAYLOR = 3 };
+
+struct StepCols {
+    // columns [c0, c0+ncheb) are Chebyshev, [t0, t0+ntay) are Taylor
+    int cheb_c0, ncheb, tay_c0, ntay;
+    int cheb_kind;  // EPI_CHEB1, EPI_CHEB or EPI_NONE for this step
+};
+
+// ---- probes / initial blocks (vne_probe.cu) --------------------------------
+cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint64_t seed,
+                                   cudaStream_t st);
+// Dense layout [column][row] with row stride n (master) / ldk (bf16 shadows).
+template <typename T>
+cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
+                              int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
+                              int rows_per_tile, cudaStream_t st);
+// Banded layout [row][column] (row stride S).  Rademacher probes are packed
+// as bits (bit j%64 of word j/64 of row i set when g_j[i] = -1; W words per
+// row); Gaussian probes are stored as values G[i*s + j].
+template <typename T>
+cudaError_t launch_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
+                            uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st);
+
+// ---- conversions / checks (vne_prep.cu) --------------------------------------
+cudaError_t launch_dense_convert_f64(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                     double* dst, cudaStream_t st);
+cudaError_t launch_dense_convert_f32(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                     float* dst, cudaStream_t st);
+// bf16 split, zero padded to rows_pad x ldk (ldk >= n): hi = bf16(R), lo = bf16(R - hi)
+cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                      __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t rows_pad,
+                                      int64_t ldk, cudaStream_t st);
+cudaError_t launch_dia_convert(const void* src, int src_dtype, int64_t n, int64_t ld, int D,
+                               void* dst, int dst_dtype, cudaStream_t st);
+cudaError_t launch_trace(const void* R, int layout, int dtype, int64_t n, int64_t ld,
+                         double* partial, unsigned int* counter, double* sc, cudaStream_t st);
+cudaError_t launch_set_u(double* sc, double u, cudaStream_t st);
+
+// ---- power method (vne_power.cu) ---------------------------------------------
+// x vectors are stored [trial][row] in float (bf16/FP32 paths) or double (FP64).
+template <typename TX>
+cudaError_t launch_power_init(TX* x0, int64_t n, int q, uint64_t seed, double* sc,
+                              cudaStream_t st);
+// One product y = R (x / ||x||).  `final_step` computes the Rayleigh quotients,
+// p1~ (SC_LAM) and u (SC_U) = min(1, u_scale * p1~).
+cudaError_t launch_power_step_dense(const void* R, int rdtype /*0 f64,1 f32,2 bf16*/, int64_t n,
+                                    int64_t ld, const void* x, void* y, int xdouble, int q,
+                                    double* sc, double* partial, unsigned int* counter,
+                                    int final_step, double u_scale, int nblocks_cap,
+                                    cudaStream_t st);
+cudaError_t launch_power_step_dia(const void* vals, int rdtype /*0 f64,1 f32*/, int64_t n,
+                                  int64_t ld, int D, const void* x, void* y, int q, double* sc,
+                                  double* partial, unsigned int* counter, int final_step,
+                                  double u_scale, int nblocks, cudaStream_t st);
+
+// ---- dense SIMT recurrence (vne_dense_simt.cu) ---------------------------------
+template <typename T>
+cudaError_t launch_dense_simt_step(const T* R, int64_t ld, int64_t n, const T* Yprev, T* Zpart,
+                                   int S, int col0, int ncols, int splitk, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dense_simt_epilogue(const T* Zpart, int splitk, const T* G, const T* Yprev,
+                                       const T* Yprev2, T* Ynew, int64_t n, int S, int s,
+                                       StepCols cols, const double* sc, Partials P, int t,
+                                       cudaStream_t st);
+int dense_simt_splitk(int64_t n, int ncols, int sm_count);
+
+// ---- banded recurrence (vne_dia.cu) --------------------------------------------
+template <typename T>
+cudaError_t launch_dia_step(const T* vals, int64_t ld, int D, int64_t n, const T* Yprev,
+                            const T* Yprev2, T* Ynew, const T* G, const uint64_t* bits, int W,
+                            int S, int s, StepCols cols, const double* sc, Partials P, int t,
+                            int nblocks, cudaStream_t st);
+int dia_supported_halfbw(int D);  // the compiled window >= D-1, or -1
+int dia_step_grid(int is_double, int D, int64_t n, int ncols, int sm_count);
+
+// ---- dense tensor-core recurrence (vne_tc.cu) -------------------------------------
+struct TcStep {
+    const __nv_bfloat16* Rhi;
+    const __nv_bfloat16* Rlo;   // NULL unless bf16x3
+    const __nv_bfloat16* Yhi;   // shadows of Y_{t-1}, [S][ldk]
+    const __nv_bfloat16* Ylo;   // NULL unless bf16x3
+    __nv_bfloat16* Yhi_out;     // shadows of Y_t
+    __nv_bfloat16* Ylo_out;
+    const float* G;             // [s][n]
+    const float* Yprev;         // FP32 master Y_{t-1} [S][n]
+    const float* Yprev2;        // FP32 master Y_{t-2}
+    float* Ynew;                // FP32 master Y_t
+    int64_t n, rows_pad, ldk;
+    int S, s, split;
+    StepCols cols;
+    const double* sc;
+    Partials P;
+    int t;
+};
+cudaError_t launch_tc_step(const TcStep& a, int sm_count, cudaStream_t st);
+int tc_tile_m();
+int tc_tile_k();
+
+// ---- combine (vne_combine.cu) ----------------------------------------------------
+// moments[k][j] for k = 0..m of the Chebyshev columns / Taylor columns, then
+// the FP64 estimates into sc.
+cudaError_t launch_combine(Partials P, int s, int m, int cheb_c0, int tay_c0, double* mom_cheb,
+                           double* mom_taylor, double* sc, cudaStream_t st);
+
+}  // namespace vne

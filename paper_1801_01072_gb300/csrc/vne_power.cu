@@ -1,0 +1,262 @@
+// Power method of Appendix A (Algorithm alg:power), q trials side by side.
+//
+// Each launch forms y = R x_hat for every trial, x_hat = x / ||x|| (the
+// printed algorithm does not normalise; dividing each iterate by its norm
+// leaves the Rayleigh quotient unchanged and keeps t in the tens finite).
+// The norms ||y||^2 (and, after the last product, x_hat^T y and x_hat^T x_hat)
+// are reduced in FP64: per-block partials, then the last block to finish
+// sums them in block order and writes the running sums to the scalar block.
+#include "vne_common.cuh"
+#include "vne_internal.h"
+
+namespace vne {
+
+constexpr int kMaxTrials = 8;
+
+template <typename TX>
+__global__ void k_power_init(TX* x0, int64_t n, int q, uint64_t seed, double* sc) {
+    const int64_t total = n * (int64_t)q;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        x0[e] = (TX)rademacher(seed ^ kPowerSeedXor, (uint64_t)e);
+    if (blockIdx.x == 0 && threadIdx.x < q) {
+        sc[SC_NORM + 3 * threadIdx.x + 0] = (double)n;  // ||x_0||^2 = n
+        sc[SC_NORM + 3 * threadIdx.x + 1] = 0.0;
+        sc[SC_NORM + 3 * threadIdx.x + 2] = 0.0;
+    }
+}
+
+template <typename TX>
+cudaError_t launch_power_init(TX* x0, int64_t n, int q, uint64_t seed, double* sc,
+                              cudaStream_t st) {
+    if (q < 1 || q > kMaxTrials) return cudaErrorInvalidValue;
+    int blocks = (int)((n * q + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_power_init<TX><<<blocks, 256, 0, st>>>(x0, n, q, seed, sc);
+    return cudaGetLastError();
+}
+template cudaError_t launch_power_init<float>(float*, int64_t, int, uint64_t, double*, cudaStream_t);
+template cudaError_t launch_power_init<double>(double*, int64_t, int, uint64_t, double*,
+                                               cudaStream_t);
+
+// Shared tail of a power step: block partials -> last block -> sc.
+// acc[3*j + {0,1,2}] = this thread's (y.y, xh.y, xh.xh) of trial j.
+__device__ void power_finish(double* acc, int q, double* partial, unsigned int* counter,
+                             double* sc, int final_step, double u_scale) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    for (int v = 0; v < 3 * q; ++v) {
+        const double t = block_sum(acc[v], sh);
+        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * 3 * q + v] = t;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // 3q sums over gridDim.x partials, one thread per sum, block order fixed
+    if (threadIdx.x < 3 * q) {
+        double tot = 0.0;
+        const volatile double* vp = partial;
+        for (unsigned b = 0; b < gridDim.x; ++b) tot += vp[(size_t)b * 3 * q + threadIdx.x];
+        sc[SC_NORM + threadIdx.x] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        if (final_step) {
+            double lam = -1.0;
+            bool ok = true;
+            for (int j = 0; j < q; ++j) {
+                const double r = sc[SC_NORM + 3 * j + 1] / sc[SC_NORM + 3 * j + 2];
+                if (!isfinite(r)) ok = false;
+                lam = fmax(lam, r);
+            }
+            double u = fmin(1.0, u_scale * lam);
+            sc[SC_LAM] = lam;
+            sc[SC_U] = u;
+            if (!ok || !(u > 0.0) || !isfinite(u)) {
+                unsigned long long* f = (unsigned long long*)&sc[SC_FLAGS];
+                *f |= FLAG_BAD_INTERVAL;
+            }
+        }
+    }
+}
+
+template <typename TR> struct Ld;
+template <> struct Ld<double> {
+    static __device__ __forceinline__ double get(const double* p) { return __ldg(p); }
+};
+template <> struct Ld<float> {
+    static __device__ __forceinline__ double get(const float* p) { return (double)__ldg(p); }
+};
+
+// Dense: one warp per row, lanes stride over the columns.
+template <typename TR, typename TX, typename TA>
+__global__ void __launch_bounds__(256) k_power_dense(const TR* R, int64_t n, int64_t ld,
+                                                     const TX* x, TX* y, int q, double* sc,
+                                                     double* partial, unsigned int* counter,
+                                                     int final_step, double u_scale) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double inv[kMaxTrials];
+    for (int j = 0; j < q; ++j) inv[j] = 1.0 / sqrt(sc[SC_NORM + 3 * j]);
+    double acc[3 * kMaxTrials];
+    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+        TA a[kMaxTrials];
+        for (int j = 0; j < q; ++j) a[j] = (TA)0;
+        const TR* row = R + i * ld;
+        for (int64_t k = lane; k < n; k += 32) {
+            const TA r = (TA)Ld<TR>::get(row + k);
+            for (int j = 0; j < q; ++j) a[j] += r * (TA)x[(int64_t)j * n + k];
+        }
+        for (int j = 0; j < q; ++j) {
+            const double yv = (double)warp_sum(a[j]) * inv[j];
+            if (lane == 0) {
+                y[(int64_t)j * n + i] = (TX)yv;
+                acc[3 * j + 0] += yv * yv;
+                if (final_step) {
+                    const double xh = (double)x[(int64_t)j * n + i] * inv[j];
+                    acc[3 * j + 1] += xh * yv;
+                    acc[3 * j + 2] += xh * xh;
+                }
+            }
+        }
+    }
+    power_finish(acc, q, partial, counter, sc, final_step, u_scale);
+}
+
+// bf16 rows (16-byte aligned, ld % 8 == 0): 8 entries per lane per load.
+__global__ void __launch_bounds__(256) k_power_dense_bf16(const __nv_bfloat16* R, int64_t n,
+                                                          int64_t ld, const float* x, float* y,
+                                                          int q, double* sc, double* partial,
+                                                          unsigned int* counter, int final_step,
+                                                          double u_scale) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double inv[kMaxTrials];
+    for (int j = 0; j < q; ++j) inv[j] = 1.0 / sqrt(sc[SC_NORM + 3 * j]);
+    double acc[3 * kMaxTrials];
+    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.0;
+    const int64_t nvec = n / 8;  // full 8-wide groups
+    for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+        float a[kMaxTrials];
+        for (int j = 0; j < q; ++j) a[j] = 0.f;
+        const __nv_bfloat16* row = R + i * ld;
+        for (int64_t g = lane; g < nvec; g += 32) {
+            const uint4 raw = __ldg((const uint4*)(row + g * 8));
+            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&raw;
+            float r[8];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h2[e]);
+                r[2 * e] = f.x;
+                r[2 * e + 1] = f.y;
+            }
+            for (int j = 0; j < q; ++j) {
+                const float4* xv = (const float4*)(x + (int64_t)j * n + g * 8);
+                const float4 x0 = xv[0], x1 = xv[1];
+                a[j] += r[0] * x0.x + r[1] * x0.y + r[2] * x0.z + r[3] * x0.w + r[4] * x1.x +
+                        r[5] * x1.y + r[6] * x1.z + r[7] * x1.w;
+            }
+        }
+        for (int64_t k = nvec * 8 + lane; k < n; k += 32) {
+            const float r = __bfloat162float(row[k]);
+            for (int j = 0; j < q; ++j) a[j] += r * x[(int64_t)j * n + k];
+        }
+        for (int j = 0; j < q; ++j) {
+            const double yv = (double)warp_sum(a[j]) * inv[j];
+            if (lane == 0) {
+                y[(int64_t)j * n + i] = (float)yv;
+                acc[3 * j + 0] += yv * yv;
+                if (final_step) {
+                    const double xh = (double)x[(int64_t)j * n + i] * inv[j];
+                    acc[3 * j + 1] += xh * yv;
+                    acc[3 * j + 2] += xh * xh;
+                }
+            }
+        }
+    }
+    power_finish(acc, q, partial, counter, sc, final_step, u_scale);
+}
+
+cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_t ld,
+                                    const void* x, void* y, int xdouble, int q, double* sc,
+                                    double* partial, unsigned int* counter, int final_step,
+                                    double u_scale, int nblocks_cap, cudaStream_t st) {
+    if (q < 1 || q > kMaxTrials) return cudaErrorInvalidValue;
+    int blocks = (int)((n + 7) / 8);
+    if (blocks > nblocks_cap) blocks = nblocks_cap;
+    if (rdtype == 0) {
+        if (!xdouble) return cudaErrorInvalidValue;
+        k_power_dense<double, double, double><<<blocks, 256, 0, st>>>(
+            (const double*)R, n, ld, (const double*)x, (double*)y, q, sc, partial, counter,
+            final_step, u_scale);
+    } else if (rdtype == 1) {
+        if (xdouble) return cudaErrorInvalidValue;
+        k_power_dense<float, float, float><<<blocks, 256, 0, st>>>(
+            (const float*)R, n, ld, (const float*)x, (float*)y, q, sc, partial, counter,
+            final_step, u_scale);
+    } else {
+        if (xdouble || (ld % 8) != 0) return cudaErrorInvalidValue;
+        k_power_dense_bf16<<<blocks, 256, 0, st>>>((const __nv_bfloat16*)R, n, ld,
+                                                   (const float*)x, (float*)y, q, sc, partial,
+                                                   counter, final_step, u_scale);
+    }
+    return cudaGetLastError();
+}
+
+// Banded: one thread per row,
+// y_i = sum_d R[i,i+d] x_{i+d} + sum_{d>0} R[i-d,i] x_{i-d}.
+template <typename T>
+__global__ void __launch_bounds__(256) k_power_dia(const T* vals, int64_t n, int64_t ld, int D,
+                                                   const T* x, T* y, int q, double* sc,
+                                                   double* partial, unsigned int* counter,
+                                                   int final_step, double u_scale) {
+    double inv[kMaxTrials];
+    for (int j = 0; j < q; ++j) inv[j] = 1.0 / sqrt(sc[SC_NORM + 3 * j]);
+    double acc[3 * kMaxTrials];
+    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int j = 0; j < q; ++j) {
+            const T* xj = x + (int64_t)j * n;
+            T a = vals[i] * xj[i];
+            for (int d = 1; d < D; ++d) {
+                if (i + d < n) a += vals[(int64_t)d * ld + i] * xj[i + d];
+                if (i - d >= 0) a += vals[(int64_t)d * ld + i - d] * xj[i - d];
+            }
+            const double yv = (double)a * inv[j];
+            y[(int64_t)j * n + i] = (T)yv;
+            acc[3 * j + 0] += yv * yv;
+            if (final_step) {
+                const double xh = (double)xj[i] * inv[j];
+                acc[3 * j + 1] += xh * yv;
+                acc[3 * j + 2] += xh * xh;
+            }
+        }
+    }
+    power_finish(acc, q, partial, counter, sc, final_step, u_scale);
+}
+
+cudaError_t launch_power_step_dia(const void* vals, int rdtype, int64_t n, int64_t ld, int D,
+                                  const void* x, void* y, int q, double* sc, double* partial,
+                                  unsigned int* counter, int final_step, double u_scale,
+                                  int nblocks, cudaStream_t st) {
+    if (q < 1 || q > kMaxTrials) return cudaErrorInvalidValue;
+    int64_t want = (n + 255) / 256;
+    int blocks = (int)(want < nblocks ? want : nblocks);
+    if (blocks < 1) blocks = 1;
+    if (rdtype == 0)
+        k_power_dia<double><<<blocks, 256, 0, st>>>((const double*)vals, n, ld, D,
+                                                    (const double*)x, (double*)y, q, sc, partial,
+                                                    counter, final_step, u_scale);
+    else
+        k_power_dia<float><<<blocks, 256, 0, st>>>((const float*)vals, n, ld, D,
+                                                   (const float*)x, (float*)y, q, sc, partial,
+                                                   counter, final_step, u_scale);
+    return cudaGetLastError();
+}
+
+}  // namespace vne

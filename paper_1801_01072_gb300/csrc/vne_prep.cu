@@ -1,0 +1,141 @@
+// Operand preparation: storage-type conversion of R, the bf16 hi/lo split
+// of the tensor-core path, the unit-trace check of Section 1.1, and u.
+#include "vne_common.cuh"
+#include "vne_internal.h"
+
+namespace vne {
+
+__device__ __forceinline__ double load_entry(const void* src, int dtype, int64_t idx) {
+    return dtype == 0 ? ((const double*)src)[idx] : (double)((const float*)src)[idx];
+}
+
+template <typename TO>
+__global__ void k_dense_convert(const void* src, int dtype, int64_t n, int64_t ld, TO* dst) {
+    const int64_t total = n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n, k = e - i * n;
+        dst[e] = (TO)load_entry(src, dtype, i * ld + k);
+    }
+}
+
+static int grid_for(int64_t total) {
+    int64_t b = (total + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_dense_convert_f64(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                     double* dst, cudaStream_t st) {
+    k_dense_convert<double><<<grid_for(n * n), 256, 0, st>>>(src, src_dtype, n, ld, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_dense_convert_f32(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                     float* dst, cudaStream_t st) {
+    k_dense_convert<float><<<grid_for(n * n), 256, 0, st>>>(src, src_dtype, n, ld, dst);
+    return cudaGetLastError();
+}
+
+// hi = bf16(R), lo = bf16(R - hi) (R first rounded to FP32), zero padding
+// outside the n x n block.  Each thread converts 8 consecutive columns.
+__global__ void k_dense_convert_bf16(const void* src, int dtype, int64_t n, int64_t ld,
+                                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t rows_pad,
+                                     int64_t ldk) {
+    const int64_t groups = ldk / 8;
+    const int64_t total = rows_pad * groups;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / groups, k0 = (e - i * groups) * 8;
+        __align__(16) __nv_bfloat16 h8[8], l8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t k = k0 + q;
+            float v = 0.f;
+            if (i < n && k < n) v = (float)load_entry(src, dtype, i * ld + k);
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            h8[q] = h;
+            l8[q] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+        *(uint4*)(hi + i * ldk + k0) = *(const uint4*)h8;
+        if (lo) *(uint4*)(lo + i * ldk + k0) = *(const uint4*)l8;
+    }
+}
+
+cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                      __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t rows_pad,
+                                      int64_t ldk, cudaStream_t st) {
+    if (ldk % 8 != 0) return cudaErrorInvalidValue;
+    k_dense_convert_bf16<<<grid_for(rows_pad * (ldk / 8)), 256, 0, st>>>(src, src_dtype, n, ld, hi,
+                                                                         lo, rows_pad, ldk);
+    return cudaGetLastError();
+}
+
+__global__ void k_dia_convert(const void* src, int sdt, int64_t n, int64_t ld, int D, void* dst,
+                              int ddt) {
+    const int64_t total = (int64_t)D * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = e / n, i = e - d * n;
+        const double v = (i < n - d) ? load_entry(src, sdt, d * ld + i) : 0.0;
+        if (ddt == 0) ((double*)dst)[e] = v;
+        else ((float*)dst)[e] = (float)v;
+    }
+}
+
+cudaError_t launch_dia_convert(const void* src, int src_dtype, int64_t n, int64_t ld, int D,
+                               void* dst, int dst_dtype, cudaStream_t st) {
+    k_dia_convert<<<grid_for((int64_t)D * n), 256, 0, st>>>(src, src_dtype, n, ld, D, dst,
+                                                            dst_dtype);
+    return cudaGetLastError();
+}
+
+// tr R in FP64: per-block partials, the last block to finish sums them in
+// block order (deterministic) and resets the counter.
+__global__ void k_trace(const void* R, int layout, int dtype, int64_t n, int64_t ld,
+                        double* partial, unsigned int* counter, double* sc) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    double v = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v += load_entry(R, dtype, layout == 0 ? i * ld + i : i);
+    const double t = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = t;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double tot = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) tot += ((volatile double*)partial)[b];
+        sc[SC_TRACE] = tot;
+        *counter = 0u;
+    }
+}
+
+cudaError_t launch_trace(const void* R, int layout, int dtype, int64_t n, int64_t ld,
+                         double* partial, unsigned int* counter, double* sc, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 256) blocks = 256;
+    k_trace<<<blocks, 256, 0, st>>>(R, layout, dtype, n, ld, partial, counter, sc);
+    return cudaGetLastError();
+}
+
+__global__ void k_set_u(double* sc, double u) {
+    sc[SC_U] = u;
+    sc[SC_LAM] = 0.0;
+    if (!(u > 0.0 && u <= 1.0)) {
+        unsigned long long* f = (unsigned long long*)&sc[SC_FLAGS];
+        *f |= FLAG_BAD_INTERVAL;
+    }
+}
+
+cudaError_t launch_set_u(double* sc, double u, cudaStream_t st) {
+    k_set_u<<<1, 1, 0, st>>>(sc, u);
+    return cudaGetLastError();
+}
+
+}  // namespace vne

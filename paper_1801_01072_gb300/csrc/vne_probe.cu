@@ -1,0 +1,134 @@
+// Probe generation and the initial recurrence blocks Y_0 = G.
+//
+// The trace estimator of Lemma thm:trace (used by Algorithms 1a and 1b)
+// draws s i.i.d. probe vectors g_j.  They come from the SplitMix64 counter
+// generator of vne_common.cuh, entry (i, j) at counter j*n + i.
+#include "vne_common.cuh"
+#include "vne_internal.h"
+
+namespace vne {
+
+__global__ void k_probe_block_f64(double* out, int64_t n, int s, int kind, uint64_t seed) {
+    const int64_t total = n * (int64_t)s;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = probe_value(kind, seed, (uint64_t)e);
+}
+
+cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint64_t seed,
+                                   cudaStream_t st) {
+    const int64_t total = n * (int64_t)s;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_probe_block_f64<<<blocks, 256, 0, st>>>(out, n, s, kind, seed);
+    return cudaGetLastError();
+}
+
+// Dense layout: one thread per row of a row tile (blockDim.x = rows_per_tile),
+// blockIdx.y = probe j.  Writes G[j][i], Y0[c][i] for every column c = j + r*s
+// (r < S/s), the bf16 hi/lo shadows of Y0 if requested, and the slot-0
+// partials sum_i g_j[i]^2 of each row tile.
+template <typename T>
+__global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
+                             int64_t n, int S, int s, int kind, uint64_t seed, Partials P) {
+    __shared__ double sh[32];
+    const int j = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double g = 0.0;
+    if (i < n) {
+        g = probe_value(kind, seed, (uint64_t)j * (uint64_t)n + (uint64_t)i);
+        const T gt = (T)g;
+        G[(int64_t)j * n + i] = gt;
+        for (int c = j; c < S; c += s) {
+            Y0[(int64_t)c * n + i] = gt;
+            if (Yhi) {
+                const float gf = (float)gt;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(gf);
+                Yhi[(int64_t)c * ldk + i] = hi;
+                if (Ylo) Ylo[(int64_t)c * ldk + i] = __float2bfloat16_rn(gf - __bfloat162float(hi));
+            }
+        }
+    }
+    const double tot = block_sum(g * g, sh);
+    if (threadIdx.x == 0)
+        for (int c = j; c < S; c += s) P.slot(0)[(size_t)blockIdx.x * S + c] = tot;
+}
+
+template <typename T>
+cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
+                              int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
+                              int rows_per_tile, cudaStream_t st) {
+    dim3 grid((unsigned)((n + rows_per_tile - 1) / rows_per_tile), (unsigned)s);
+    k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, Yhi, Ylo, ldk, n, S, s, kind, seed, P);
+    return cudaGetLastError();
+}
+template cudaError_t launch_dense_init<double>(double*, double*, __nv_bfloat16*, __nv_bfloat16*,
+                                               int64_t, int64_t, int, int, int, uint64_t, Partials,
+                                               int, cudaStream_t);
+template cudaError_t launch_dense_init<float>(float*, float*, __nv_bfloat16*, __nv_bfloat16*,
+                                              int64_t, int64_t, int, int, int, uint64_t, Partials,
+                                              int, cudaStream_t);
+
+// Banded layout: a block of 8 warps owns a tile of rows_per_tile rows; each
+// warp walks rows w, w+8, ... of the tile and lane l covers probes l, l+32, ...
+template <typename T>
+__global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
+                           uint64_t seed, Partials P, int rows_per_tile) {
+    __shared__ double sh[8][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nchunk = (s + 31) >> 5;  // <= 8
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_tile;
+    int64_t r1 = r0 + rows_per_tile;
+    if (r1 > n) r1 = n;
+    for (int64_t i = r0 + w; i < r1; i += 8) {
+        uint32_t words[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            words[q] = 0u;
+            if (q < nchunk) {
+                const int j = q * 32 + lane;
+                double g = 0.0;
+                if (j < s) g = probe_value(kind, seed, (uint64_t)j * (uint64_t)n + (uint64_t)i);
+                words[q] = __ballot_sync(0xffffffffu, g < 0.0);
+                if (j < s) {
+                    const T gt = (T)g;
+                    if (G) G[i * s + j] = gt;
+                    for (int c = j; c < S; c += s) Y0[i * S + c] = gt;
+                    acc[q] += g * g;
+                }
+            }
+        }
+        if (bits && lane < W) {
+            const uint64_t lo = words[2 * lane], hi = words[2 * lane + 1];
+            bits[i * W + lane] = lo | (hi << 32);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (q < nchunk) sh[w][q * 32 + lane] = acc[q];
+    __syncthreads();
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        double t = 0.0;
+        for (int ww = 0; ww < 8; ++ww) t += sh[ww][j];
+        for (int c = j; c < S; c += s) P.slot(0)[(size_t)blockIdx.x * S + c] = t;
+    }
+}
+
+template <typename T>
+cudaError_t launch_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
+                            uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st) {
+    if (s > 256 || W > 4) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)((n + rows_per_tile - 1) / rows_per_tile);
+    k_dia_init<T><<<grid, 256, 0, st>>>(G, bits, W, Y0, n, S, s, kind, seed, P, rows_per_tile);
+    return cudaGetLastError();
+}
+template cudaError_t launch_dia_init<double>(double*, uint64_t*, int, double*, int64_t, int, int,
+                                             int, uint64_t, Partials, int, cudaStream_t);
+template cudaError_t launch_dia_init<float>(float*, uint64_t*, int, float*, int64_t, int, int, int,
+                                            uint64_t, Partials, int, cudaStream_t);
+
+}  // namespace vne

@@ -1,0 +1,462 @@
+// Dense recurrence step on the 5th-generation tensor cores (tcgen05, TMEM,
+// TMA), BF16 operands with FP32 accumulation, optionally split precision
+// (bf16x3: R_hi Y_hi + R_hi Y_lo + R_lo Y_hi).
+//
+// One CTA computes a 128 x BN tile of Z = R Y_{t-1} (rows of R x probe
+// columns) and applies the fused epilogue of the step:
+//   Chebyshev (Section 3, forward form of the Clenshaw recurrence of
+//   Appendix C): Y_t = 2((2/u) Z - Y_{t-1}) - Y_{t-2}  (Y_1 = (2/u) Z - G),
+//   moment partial g^T Y_t;
+//   Taylor (Section 2, Algorithm 1a): moment partial g^T Z (= g^T R C^{t-1} g),
+//   Y_t = Y_{t-1} - Z/u;
+// and writes the bf16 hi/lo shadows of Y_t that are the next step's B operand.
+//
+// Operands: R_hi/R_lo [rows_pad][ldk] and the Y shadows [S_pad][ldk], both
+// K-major bf16, loaded by TMA into 128-byte-swizzled shared memory tiles
+// (BK = 64 elements = 128 bytes per row).  Roles (256 threads, 8 warps):
+//   warp 0 lane 0 : TMA producer over a ring of `stages` buffers
+//   warp 1        : TMEM allocation; lane 0 issues tcgen05.mma (M=128, N=BN,
+//                   K=16 per instruction) and commits to the ring's "empty"
+//                   barriers and finally to the "accumulator full" barrier
+//   all 8 warps   : epilogue; warp w reads TMEM lanes 32*(w%4).. (its 32 rows)
+//                   and the column chunks of parity w/4.
+// Every wait on an mbarrier is bounded by a %globaltimer deadline; on
+// timeout the CTA raises FLAG_TIMEOUT, drains what it issued and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "vne_common.cuh"
+#include "vne_internal.h"
+
+namespace vne {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;
+constexpr int TC_THREADS = 256;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+
+int tc_tile_m() { return TC_BM; }
+int tc_tile_k() { return TC_BK; }
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false on timeout or when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0u) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > kWaitNs) return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+// kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+#define TMEM_LD32(taddr, r)                                                                     \
+    asm volatile(                                                                               \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"      \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),   \
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),           \
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),        \
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),        \
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),        \
+          "=r"(r[31])                                                                           \
+        : "r"(taddr))
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Kernel
+// ---------------------------------------------------------------------------
+struct TcArgs {
+    const float* G;
+    const float* Yprev;
+    const float* Yprev2;
+    float* Ynew;
+    __nv_bfloat16* Yhi_out;
+    __nv_bfloat16* Ylo_out;
+    int64_t n, ldk;
+    int S, s;
+    int col0, col_end;  // active columns [col0, col_end)
+    int BN, stages, nkb, x3;
+    uint32_t tmem_cols;
+    StepCols cols;
+    const double* sc;
+    Partials P;
+    int t;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_step(const __grid_constant__ CUtensorMap mapRhi, const __grid_constant__ CUtensorMap mapRlo,
+              const __grid_constant__ CUtensorMap mapYhi, const __grid_constant__ CUtensorMap mapYlo,
+              const TcArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned carve-out: [stages][A_hi | B_hi | (A_lo | B_lo)] then barriers
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+    const uint32_t bytesA = TC_BM * TC_BK * 2;
+    const uint32_t bytesB = (uint32_t)a.BN * TC_BK * 2;
+    const uint32_t stage_bytes = (bytesA + bytesB) * (a.x3 ? 2u : 1u);
+    uint8_t* tail = smem + (size_t)a.stages * stage_bytes;
+    uint64_t* full_bar = reinterpret_cast<uint64_t*>(tail);
+    uint64_t* empty_bar = full_bar + a.stages;
+    uint64_t* accum_bar = empty_bar + a.stages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum_bar + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][BN]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_BM;
+    const int n0 = a.col0 + blockIdx.y * a.BN;
+
+    if (threadIdx.x == 0) {
+        for (int s2 = 0; s2 < a.stages; ++s2) {
+            mbar_init(&full_bar[s2], 1);
+            mbar_init(&empty_bar[s2], 1);
+        }
+        mbar_init(accum_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapRhi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapYhi)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    bool timed_out = false;
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued_kb = 0;
+        for (int kb = 0; kb < a.nkb; ++kb) {
+            const int st = kb % a.stages;
+            const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
+            if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) {
+                timed_out = true;
+                break;
+            }
+            uint8_t* sA = smem + (size_t)st * stage_bytes;
+            uint8_t* sB = sA + bytesA;
+            mbar_expect_tx(&full_bar[st], stage_bytes);
+            tma_load_2d(sA, &mapRhi, &full_bar[st], kb * TC_BK, m0);
+            tma_load_2d(sB, &mapYhi, &full_bar[st], kb * TC_BK, n0);
+            if (a.x3) {
+                uint8_t* sAl = sB + bytesB;
+                uint8_t* sBl = sAl + bytesA;
+                tma_load_2d(sAl, &mapRlo, &full_bar[st], kb * TC_BK, m0);
+                tma_load_2d(sBl, &mapYlo, &full_bar[st], kb * TC_BK, n0);
+            }
+            issued_kb = kb + 1;
+        }
+        if (timed_out) {
+            *abort_flag = 1;
+            // drain: wait (bounded) for the loads of the last `stages` issued blocks
+            int first = issued_kb - a.stages;
+            if (first < 0) first = 0;
+            volatile int never = 0;
+            for (int kb = first; kb < issued_kb; ++kb)
+                mbar_wait(&full_bar[kb % a.stages], (uint32_t)(kb / a.stages) & 1u, &never);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_bf16(TC_BM, a.BN);
+        for (int kb = 0; kb < a.nkb; ++kb) {
+            const int st = kb % a.stages;
+            const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
+            if (!mbar_wait(&full_bar[st], ph, abort_flag)) {
+                timed_out = true;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t aA = smem_u32(smem + (size_t)st * stage_bytes);
+            const uint32_t aB = aA + bytesA;
+            const uint64_t dA = desc_sw128(aA), dB = desc_sw128(aB);
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+                // +32 bytes along K per K=16 slice (descriptor units of 16 B)
+                umma_bf16(tmem_base, dA + 2 * k, dB + 2 * k, idesc, (kb | k) != 0);
+            }
+            if (a.x3) {
+                const uint32_t aAl = aB + bytesB, aBl = aAl + bytesA;
+                const uint64_t dAl = desc_sw128(aAl), dBl = desc_sw128(aBl);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k) {
+                    umma_bf16(tmem_base, dA + 2 * k, dBl + 2 * k, idesc, 1u);
+                    umma_bf16(tmem_base, dAl + 2 * k, dB + 2 * k, idesc, 1u);
+                }
+            }
+            tc_commit(&empty_bar[st]);  // frees the ring slot once these MMAs finish
+        }
+        if (timed_out) *abort_flag = 1;
+        tc_commit(accum_bar);  // all issued MMAs (possibly none) complete -> arrive
+    }
+    __syncwarp();
+
+    // ---------------- epilogue (all warps) ----------------
+    bool have_acc = mbar_wait(accum_bar, 0u, abort_flag);
+    if (!have_acc) {
+        // the accumulator barrier may still arrive: wait for it before TMEM is freed
+        volatile int never = 0;
+        if (threadIdx.x == 0) mbar_wait(accum_bar, 0u, &never);
+    }
+    const bool aborted = (*abort_flag != 0) || !have_acc;
+    tc_fence_after();
+    __syncwarp();
+
+    const int rg = warp & 3, chalf = warp >> 2;
+    const int row = m0 + rg * 32 + lane;
+    const bool row_ok = row < a.n;
+    const double u = a.sc[SC_U];
+    const float fa = (float)(2.0 / u), finvu = (float)(1.0 / u);
+    const int nchunks = a.BN / 32;
+    if (!aborted) {
+        for (int ck = chalf; ck < nchunks; ck += 2) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32);
+            TMEM_LD32(taddr, r);
+            tmem_wait_ld();
+            float v[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int c = n0 + ck * 32 + q;  // warp-uniform
+                v[q] = 0.f;
+                if (c >= a.col_end || !row_ok) continue;
+                const float z = __uint_as_float(r[q]);
+                const int j = c % a.s;
+                const int64_t idx = (int64_t)c * a.n + row;
+                const float g = a.G[(int64_t)j * a.n + row];
+                const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
+                float y;
+                if (cheb) {
+                    if (a.cols.cheb_kind == EPI_CHEB1) y = fmaf(fa, z, -g);
+                    else y = 2.f * fmaf(fa, z, -a.Yprev[idx]) - a.Yprev2[idx];
+                    v[q] = g * y;
+                } else {
+                    v[q] = g * z;
+                    y = fmaf(-z, finvu, a.Yprev[idx]);
+                }
+                a.Ynew[idx] = y;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+                a.Yhi_out[(int64_t)c * a.ldk + row] = hi;
+                if (a.Ylo_out)
+                    a.Ylo_out[(int64_t)c * a.ldk + row] = __float2bfloat16_rn(y - __bfloat162float(hi));
+            }
+            // transpose-reduce: afterwards lane l holds the 32-row sum of column l
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const bool upper = (lane & o) != 0;
+#pragma unroll
+                for (int k = 0; k < o; ++k) {
+                    const float send = upper ? v[k] : v[k + o];
+                    const float keep = upper ? v[k + o] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            red[rg * a.BN + ck * 32 + lane] = v[0];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (!aborted) {
+        for (int cl = threadIdx.x; cl < a.BN; cl += blockDim.x) {
+            const int c = n0 + cl;
+            if (c >= a.col_end) continue;
+            const double tot = (double)red[cl] + (double)red[a.BN + cl] +
+                               (double)red[2 * a.BN + cl] + (double)red[3 * a.BN + cl];
+            a.P.slot(a.t)[(size_t)blockIdx.x * a.S + c] = tot;
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(a.tmem_cols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && aborted) {
+        unsigned long long* f = (unsigned long long*)&a.sc[SC_FLAGS];
+        atomicOr(f, (unsigned long long)FLAG_TIMEOUT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows,
+                     int64_t row_stride_elems, int box_inner, int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
+    (void)sm_count;
+    int col0, col_end;
+    if (s.cols.ncheb > 0) {
+        col0 = s.cols.cheb_c0;
+        col_end = s.cols.ntay > 0 ? s.cols.tay_c0 + s.cols.ntay : s.cols.cheb_c0 + s.cols.ncheb;
+    } else {
+        col0 = s.cols.tay_c0;
+        col_end = s.cols.tay_c0 + s.cols.ntay;
+    }
+    const int ncols = col_end - col0;
+    if (ncols <= 0) return cudaSuccess;
+    const int ntn = (ncols + 255) / 256;
+    int BN = (ncols + ntn - 1) / ntn;
+    BN = (BN + 31) / 32 * 32;
+    const int S_pad = (s.S + 31) / 32 * 32;
+    const bool x3 = s.Rlo != nullptr;
+    if (x3 && (!s.Ylo || !s.Ylo_out)) return cudaErrorInvalidValue;
+    if ((s.ldk % TC_BK) != 0 || (s.rows_pad % TC_BM) != 0) return cudaErrorInvalidValue;
+
+    CUtensorMap mRhi, mRlo, mYhi, mYlo;
+    if (!make_map(&mRhi, s.Rhi, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
+    if (!make_map(&mYhi, s.Yhi, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
+    if (x3) {
+        if (!make_map(&mRlo, s.Rlo, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
+        if (!make_map(&mYlo, s.Ylo, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
+    } else {
+        mRlo = mRhi;
+        mYlo = mYhi;
+    }
+    const uint32_t stage_bytes = (uint32_t)(TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (x3 ? 2u : 1u);
+    const size_t tail = 2 * 8 * 16 + 8 + 16 + 4 * 256 * 4;  // barriers, slot, flag, red
+    const size_t max_smem = 227 * 1024;
+    int stages = (int)((max_smem - 1024 - tail) / stage_bytes);
+    if (stages > 8) stages = 8;
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = 1024 + (size_t)stages * stage_bytes + tail;
+
+    TcArgs a{};
+    a.G = s.G;
+    a.Yprev = s.Yprev;
+    a.Yprev2 = s.Yprev2;
+    a.Ynew = s.Ynew;
+    a.Yhi_out = s.Yhi_out;
+    a.Ylo_out = s.Ylo_out;
+    a.n = s.n;
+    a.ldk = s.ldk;
+    a.S = s.S;
+    a.s = s.s;
+    a.col0 = col0;
+    a.col_end = col_end;
+    a.BN = BN;
+    a.stages = stages;
+    a.nkb = (int)(s.ldk / TC_BK);
+    a.x3 = x3 ? 1 : 0;
+    a.tmem_cols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+    a.cols = s.cols;
+    a.sc = s.sc;
+    a.P = s.P;
+    a.t = s.t;
+
+    cudaError_t e = cudaFuncSetAttribute(k_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(s.rows_pad / TC_BM), (unsigned)ntn);
+    k_tc_step<<<grid, TC_THREADS, smem, st>>>(mRhi, mRlo, mYhi, mYlo, a);
+    return cudaGetLastError();
+}
+
+}  // namespace vne
