@@ -164,6 +164,35 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
 vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,
                           double* lam_out, void* stream);
 
+/* Allocation-free variant of vne_lambda_max, for callers that cannot
+ * allocate device memory when they need the estimate: code running under an
+ * allocator that forbids new allocations, plug-ins inside applications that
+ * own the device memory budget, or loops that cannot afford cudaMalloc's
+ * implicit synchronisation.  The paper has no counterpart: it is a
+ * deployment convenience of this library.
+ *
+ * It runs the same power-method kernels as vne_lambda_max but keeps all of
+ * its scratch in one fixed device array inside the library
+ * (VNE_STATIC_SCRATCH_BYTES on every GPU that loads the library, held until
+ * the process exits), needs no handle, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The caller still passes R and receives lam_out.
+ *   - Device: the calling thread's current device.  The first call on a
+ *     device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
+ *   - Limits: R must be device memory stored in the computed precision
+ *     (F64 with VNE_PREC_F64, F32 with VNE_PREC_F32); n * power_trials
+ *     must not exceed VNE_STATIC_MAX_VECTOR_ELEMS.  Anything else returns
+ *     VNE_ERR_UNSUPPORTED; bad arguments return VNE_ERR_INVALID_ARG.
+ *   - Sharing: every call on a device uses the same array, which keeps the
+ *     previous call's contents (the call clears what must start at zero).
+ *     Calls that overlap on the GPU (other streams or host threads) race on
+ *     it and must be serialised by the caller.
+ *   - Synchronises `stream` before returning. */
+#define VNE_STATIC_MAX_VECTOR_ELEMS 131072
+#define VNE_STATIC_SCRATCH_BYTES 2359296
+vne_status vne_lambda_max_static(const vne_matrix* R, const vne_params* p, double* lam_out,
+                                 void* stream);
+
 /* The probe block the estimators draw: out[j*n + i] = g_j[i] (FP64, device,
  * n*s doubles, caller-owned).  Lets callers check the generator. */
 vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, uint64_t seed,
