@@ -238,7 +238,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             ntiles0 = (int)((n + rows_per_tile0 - 1) / rows_per_tile0);
         }
     }
-    const int power_blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 4 * h->sm_count)
+    const int power_blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 8 * h->sm_count)
                                    : 4 * h->sm_count;
 
     // ---- workspace plan (two passes) ----

@@ -36,28 +36,33 @@ __device__ double cheb_alpha(int k, double u) {
     return ((k & 1) ? -u : u) / (kk * kk * kk - kk);
 }
 
+// One warp per moment index k (k = warp, warp + nwarps, ...): lanes sum the
+// s probes, lane 0 folds alpha_k (or 1/k) in; warps are then summed in order.
 __global__ void k_combine_final(int s, int m, int cheb, int taylor, const double* mom_cheb,
                                 const double* mom_taylor, double* sc) {
     __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double u = sc[SC_U];
     if (cheb) {
-        double acc = 0.0;  // thread k-strided partial of sum_k alpha_k sum_j mu
-        for (int k = threadIdx.x; k <= m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int k = w; k <= m; k += nw) {
             double sk = 0.0;
-            for (int j = 0; j < s; ++j) sk += mom_cheb[k * s + j];
-            acc += cheb_alpha(k, u) * sk;
+            for (int j = lane; j < s; j += 32) sk += mom_cheb[(size_t)k * s + j];
+            sk = warp_sum(sk);
+            if (lane == 0) acc += cheb_alpha(k, u) * sk;
         }
-        const double tot = block_sum(acc, sh);
+        const double tot = block_sum(lane == 0 ? acc : 0.0, sh);
         if (threadIdx.x == 0) sc[SC_H_CHEB] = -tot / (double)s;
     }
     if (taylor) {
         double acc = 0.0;
-        for (int k = 1 + threadIdx.x; k <= m; k += blockDim.x) {
+        for (int k = 1 + w; k <= m; k += nw) {
             double sk = 0.0;
-            for (int j = 0; j < s; ++j) sk += mom_taylor[k * s + j];
-            acc += sk / (double)k;
+            for (int j = lane; j < s; j += 32) sk += mom_taylor[(size_t)k * s + j];
+            sk = warp_sum(sk);
+            if (lane == 0) acc += sk / (double)k;
         }
-        const double tot = block_sum(acc, sh);
+        const double tot = block_sum(lane == 0 ? acc : 0.0, sh);
         if (threadIdx.x == 0) sc[SC_H_TAYLOR] = log(1.0 / u) + tot / (double)s;
     }
     if (threadIdx.x == 0) {

@@ -35,6 +35,17 @@ __device__ __forceinline__ double gaussian(uint64_t seed, uint64_t e) {
     return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793238462643383279502884 * u2);
 }
 
+// The same Box-Muller draw evaluated in FP32 (for the FP32 / bf16 paths,
+// whose probe block is stored in FP32 anyway): the uniforms are the same
+// 53-bit values rounded to float.
+__device__ __forceinline__ float gaussian_f32(uint64_t seed, uint64_t e) {
+    const uint64_t a = splitmix_out(seed, 2ull * e);
+    const uint64_t b = splitmix_out(seed, 2ull * e + 1ull);
+    const float u1 = (float)((double)((a >> 11) + 1ull) * 0x1.0p-53);
+    const float u2 = (float)((double)(b >> 11) * 0x1.0p-53);
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
 __device__ __forceinline__ double probe_value(int kind, uint64_t seed, uint64_t e) {
     return kind == 0 ? rademacher(seed, e) : gaussian(seed, e);
 }

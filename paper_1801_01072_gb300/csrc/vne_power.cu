@@ -56,12 +56,14 @@ __device__ void power_finish(double* acc, int q, double* partial, unsigned int* 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // 3q sums over gridDim.x partials, one thread per sum, block order fixed
-    if (threadIdx.x < 3 * q) {
-        double tot = 0.0;
-        const volatile double* vp = partial;
-        for (unsigned b = 0; b < gridDim.x; ++b) tot += vp[(size_t)b * 3 * q + threadIdx.x];
-        sc[SC_NORM + threadIdx.x] = tot;
+    // each of the 3q sums over gridDim.x partials: every thread takes a fixed
+    // strided subset, then a fixed-order block reduction (deterministic)
+    const volatile double* vp = partial;
+    for (int v = 0; v < 3 * q; ++v) {
+        double t = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += vp[(size_t)b * 3 * q + v];
+        const double tot = block_sum(t, sh);
+        if (threadIdx.x == 0) sc[SC_NORM + v] = tot;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -181,6 +183,58 @@ __global__ void __launch_bounds__(256) k_power_dense_bf16(const __nv_bfloat16* R
     power_finish(acc, q, partial, counter, sc, final_step, u_scale);
 }
 
+// bf16 rows, one trial: U independent 16-byte loads per lane in flight.
+template <int U>
+__global__ void __launch_bounds__(256) k_power_dense_bf16_q1(
+    const __nv_bfloat16* __restrict__ R, int64_t n, int64_t ld, const float* __restrict__ x,
+    float* __restrict__ y, double* sc, double* partial, unsigned int* counter, int final_step,
+    double u_scale) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double inv = 1.0 / sqrt(sc[SC_NORM]);
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int64_t nvec = n / 8;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
+        const __nv_bfloat16* row = R + i * ld;
+        float a = 0.f;
+        for (int64_t g0 = lane; g0 < nvec; g0 += 32 * U) {
+            uint4 raw[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = g0 + 32 * u;
+                raw[u] = g < nvec ? __ldg(reinterpret_cast<const uint4*>(row + g * 8))
+                                  : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = g0 + 32 * u;
+                if (g < nvec) {
+                    const float4 x0 = __ldg(reinterpret_cast<const float4*>(x + g * 8));
+                    const float4 x1 = __ldg(reinterpret_cast<const float4*>(x + g * 8 + 4));
+                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw[u]);
+                    const float2 r0 = __bfloat1622float2(h2[0]), r1 = __bfloat1622float2(h2[1]);
+                    const float2 r2 = __bfloat1622float2(h2[2]), r3 = __bfloat1622float2(h2[3]);
+                    a = fmaf(r0.x, x0.x, a); a = fmaf(r0.y, x0.y, a);
+                    a = fmaf(r1.x, x0.z, a); a = fmaf(r1.y, x0.w, a);
+                    a = fmaf(r2.x, x1.x, a); a = fmaf(r2.y, x1.y, a);
+                    a = fmaf(r3.x, x1.z, a); a = fmaf(r3.y, x1.w, a);
+                }
+            }
+        }
+        for (int64_t k = nvec * 8 + lane; k < n; k += 32) a += __bfloat162float(row[k]) * x[k];
+        const double yv = (double)warp_sum(a) * inv;
+        if (lane == 0) {
+            y[i] = (float)yv;
+            acc[0] += yv * yv;
+            if (final_step) {
+                const double xh = (double)x[i] * inv;
+                acc[1] += xh * yv;
+                acc[2] += xh * xh;
+            }
+        }
+    }
+    power_finish(acc, 1, partial, counter, sc, final_step, u_scale);
+}
+
 cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_t ld,
                                     const void* x, void* y, int xdouble, int q, double* sc,
                                     double* partial, unsigned int* counter, int final_step,
@@ -200,6 +254,12 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
             final_step, u_scale);
     } else {
         if (xdouble || (ld % 8) != 0) return cudaErrorInvalidValue;
+        if (q == 1) {
+            k_power_dense_bf16_q1<8><<<blocks, 256, 0, st>>>(
+                (const __nv_bfloat16*)R, n, ld, (const float*)x, (float*)y, sc, partial, counter,
+                final_step, u_scale);
+            return cudaGetLastError();
+        }
         k_power_dense_bf16<<<blocks, 256, 0, st>>>((const __nv_bfloat16*)R, n, ld,
                                                    (const float*)x, (float*)y, q, sc, partial,
                                                    counter, final_step, u_scale);

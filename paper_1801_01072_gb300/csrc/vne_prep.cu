@@ -107,10 +107,12 @@ __global__ void k_trace(const void* R, int layout, int dtype, int64_t n, int64_t
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double tot = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) tot += ((volatile double*)partial)[b];
+    if (!last) return;
+    __threadfence();
+    double t2 = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t2 += ((volatile double*)partial)[b];
+    const double tot = block_sum(t2, sh);
+    if (threadIdx.x == 0) {
         sc[SC_TRACE] = tot;
         *counter = 0u;
     }

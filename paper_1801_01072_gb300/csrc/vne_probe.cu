@@ -37,7 +37,9 @@ __global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double g = 0.0;
     if (i < n) {
-        g = probe_value(kind, seed, (uint64_t)j * (uint64_t)n + (uint64_t)i);
+        const uint64_t e = (uint64_t)j * (uint64_t)n + (uint64_t)i;
+        if (sizeof(T) == 4 && kind == 1) g = (double)gaussian_f32(seed, e);
+        else g = probe_value(kind, seed, e);
         const T gt = (T)g;
         G[(int64_t)j * n + i] = gt;
         for (int c = j; c < S; c += s) {

@@ -25,6 +25,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "vne_common.cuh"
 #include "vne_internal.h"
 
@@ -85,6 +88,65 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+// Tiled 2-D TMA load with an L2 cache-policy hint; with mask != 0 the tile is
+// multicast to every CTA of the cluster in `mask` (same smem offset and the
+// same mbarrier offset in each destination CTA).
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                                 int x, int y, uint16_t mask, uint64_t policy) {
+    if (mask == 0) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+            " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+            "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+            : "memory");
+    } else {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            ".multicast::cluster.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5, %6;" ::"r"(
+                smem_u32(dst)),
+            "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask),
+            "l"(policy)
+            : "memory");
+    }
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_ctaid_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_ctaid_y() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.y;" : "=r"(r));
+    return r;
+}
+// Arrive on the mbarrier at this offset in every CTA of `mask` once all
+// previously issued tcgen05.mma of this thread have completed.
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
         : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -153,6 +215,7 @@ struct TcArgs {
     int S, s;
     int col0, col_end;  // active columns [col0, col_end)
     int BN, stages, nkb, x3;
+    int CM, CN;  // cluster shape: CM CTAs along M share B tiles, CN along N share A tiles
     uint32_t tmem_cols;
     StepCols cols;
     const double* sc;
@@ -182,11 +245,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM;
     const int n0 = a.col0 + blockIdx.y * a.BN;
+    // Cluster of CM x CN CTAs: the CN CTAs of one M row share the A tile (each
+    // loads 128/CN rows and multicasts them), the CM CTAs of one N column share
+    // the B tile (BN/CM rows each).  A ring slot is refilled only when every
+    // CTA of the cluster has released it (empty barrier count = cluster size).
+    const int csize = a.CM * a.CN;
+    int cx = 0, cy = 0;
+    bool rank_ok = true;
+    if (csize > 1) {
+        cx = (int)cluster_ctaid_x();
+        cy = (int)cluster_ctaid_y();
+        rank_ok = (int)cluster_ctarank() == cx + cy * a.CM;
+    }
+    uint16_t maskA = 0, maskB = 0, mask_all = 0;
+    if (csize > 1) {
+        for (int y = 0; y < a.CN; ++y) maskA |= (uint16_t)(1u << (cx + y * a.CM));
+        for (int x = 0; x < a.CM; ++x) maskB |= (uint16_t)(1u << (x + cy * a.CM));
+        mask_all = (uint16_t)((1u << csize) - 1u);
+        if (a.CN == 1) maskA = 0;
+        if (a.CM == 1) maskB = 0;
+    }
+    const int arows = TC_BM / a.CN, brows = a.BN / a.CM;
 
     if (threadIdx.x == 0) {
         for (int s2 = 0; s2 < a.stages; ++s2) {
             mbar_init(&full_bar[s2], 1);
-            mbar_init(&empty_bar[s2], 1);
+            mbar_init(&empty_bar[s2], (uint32_t)csize);
         }
         mbar_init(accum_bar, 1);
         *abort_flag = 0;
@@ -203,14 +287,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (csize > 1) cluster_sync_all();  // peers' barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    if (!rank_ok && threadIdx.x == 0) *abort_flag = 1;
 
     bool timed_out = false;
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
+        // R streams through L2 once (evict first); the Y shadows are re-read
+        // by every row tile (evict last).
+        const uint64_t pol_R = policy_evict_first();
+        const uint64_t pol_Y = policy_evict_last();
         int issued_kb = 0;
-        for (int kb = 0; kb < a.nkb; ++kb) {
+        for (int kb = 0; kb < a.nkb && rank_ok; ++kb) {
             const int st = kb % a.stages;
             const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
             if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) {
@@ -219,14 +309,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             uint8_t* sA = smem + (size_t)st * stage_bytes;
             uint8_t* sB = sA + bytesA;
-            mbar_expect_tx(&full_bar[st], stage_bytes);
-            tma_load_2d(sA, &mapRhi, &full_bar[st], kb * TC_BK, m0);
-            tma_load_2d(sB, &mapYhi, &full_bar[st], kb * TC_BK, n0);
+            // this CTA's slices: rows [cy*arows, +arows) of A, [cx*brows, +brows) of B
+            const uint32_t offA = (uint32_t)(cy * arows) * (TC_BK * 2);
+            const uint32_t offB = (uint32_t)(cx * brows) * (TC_BK * 2);
+            mbar_expect_tx(&full_bar[st], stage_bytes);  // whole tiles arrive here
+            tma_load_2d_hint(sA + offA, &mapRhi, &full_bar[st], kb * TC_BK, m0 + cy * arows, maskA,
+                             pol_R);
+            tma_load_2d_hint(sB + offB, &mapYhi, &full_bar[st], kb * TC_BK, n0 + cx * brows, maskB,
+                             pol_Y);
             if (a.x3) {
                 uint8_t* sAl = sB + bytesB;
                 uint8_t* sBl = sAl + bytesA;
-                tma_load_2d(sAl, &mapRlo, &full_bar[st], kb * TC_BK, m0);
-                tma_load_2d(sBl, &mapYlo, &full_bar[st], kb * TC_BK, n0);
+                tma_load_2d_hint(sAl + offA, &mapRlo, &full_bar[st], kb * TC_BK, m0 + cy * arows,
+                                 maskA, pol_R);
+                tma_load_2d_hint(sBl + offB, &mapYlo, &full_bar[st], kb * TC_BK, n0 + cx * brows,
+                                 maskB, pol_Y);
             }
             issued_kb = kb + 1;
         }
@@ -242,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16(TC_BM, a.BN);
-        for (int kb = 0; kb < a.nkb; ++kb) {
+        for (int kb = 0; kb < a.nkb && rank_ok; ++kb) {
             const int st = kb % a.stages;
             const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
             if (!mbar_wait(&full_bar[st], ph, abort_flag)) {
@@ -267,7 +364,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     umma_bf16(tmem_base, dAl + 2 * k, dB + 2 * k, idesc, 1u);
                 }
             }
-            tc_commit(&empty_bar[st]);  // frees the ring slot once these MMAs finish
+            // frees the ring slot (in every CTA of the cluster) once these MMAs finish
+            if (csize > 1) tc_commit_mc(&empty_bar[st], mask_all);
+            else tc_commit(&empty_bar[st]);
         }
         if (timed_out) *abort_flag = 1;
         tc_commit(accum_bar);  // all issued MMAs (possibly none) complete -> arrive
@@ -296,26 +395,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t r[32];
             const uint32_t taddr = tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32);
             TMEM_LD32(taddr, r);
+            // Issue every global load of the chunk before the first store, so
+            // the 32 columns' loads are in flight together (the stores could
+            // otherwise alias them and serialise the chunk).
+            const int cbase = n0 + ck * 32;
+            float gv[32], yp[32], yp2[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int c = cbase + q;  // warp-uniform
+                gv[q] = 0.f;
+                yp[q] = 0.f;
+                yp2[q] = 0.f;
+                if (c >= a.col_end || !row_ok) continue;
+                const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
+                const int64_t idx = (int64_t)c * a.n + row;
+                gv[q] = __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
+                if (!cheb || a.cols.cheb_kind == EPI_CHEB) yp[q] = __ldg(a.Yprev + idx);
+                if (cheb && a.cols.cheb_kind == EPI_CHEB) yp2[q] = __ldg(a.Yprev2 + idx);
+            }
             tmem_wait_ld();
             float v[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                const int c = n0 + ck * 32 + q;  // warp-uniform
+                const int c = cbase + q;
                 v[q] = 0.f;
                 if (c >= a.col_end || !row_ok) continue;
                 const float z = __uint_as_float(r[q]);
-                const int j = c % a.s;
+                const float g = gv[q];
                 const int64_t idx = (int64_t)c * a.n + row;
-                const float g = a.G[(int64_t)j * a.n + row];
                 const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
                 float y;
                 if (cheb) {
                     if (a.cols.cheb_kind == EPI_CHEB1) y = fmaf(fa, z, -g);
-                    else y = 2.f * fmaf(fa, z, -a.Yprev[idx]) - a.Yprev2[idx];
+                    else y = 2.f * fmaf(fa, z, -yp[q]) - yp2[q];
                     v[q] = g * y;
                 } else {
                     v[q] = g * z;
-                    y = fmaf(-z, finvu, a.Yprev[idx]);
+                    y = fmaf(-z, finvu, yp[q]);
                 }
                 a.Ynew[idx] = y;
                 const __nv_bfloat16 hi = __float2bfloat16_rn(y);
@@ -348,6 +464,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             a.P.slot(a.t)[(size_t)blockIdx.x * a.S + c] = tot;
         }
     }
+    // no CTA leaves while a peer may still multicast into it or arrive on it
+    if (csize > 1) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -378,6 +496,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows,
                      int64_t row_stride_elems, int box_inner, int box_rows) {
+    // small cache: consecutive steps reuse the same few operand buffers
+    struct Entry {
+        const void* base;
+        int64_t inner, rows, stride;
+        int bi, br;
+        CUtensorMap map;
+    };
+    static Entry cache[16];
+    static int next = 0;
+    for (const Entry& e : cache)
+        if (e.base == base && e.inner == inner && e.rows == rows && e.stride == row_stride_elems &&
+            e.bi == box_inner && e.br == box_rows) {
+            *map = e.map;
+            return true;
+        }
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
@@ -387,7 +520,46 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t 
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    if (r != CUDA_SUCCESS) return false;
+    Entry& e = cache[next];
+    next = (next + 1) % 16;
+    e = Entry{base, inner, rows, row_stride_elems, box_inner, box_rows, *map};
+    return true;
+}
+
+// Tile shape and cluster shape of one step.  BN: probe columns per CTA
+// (multiple of 32, <= 256); CM x CN: cluster along M (row tiles sharing the
+// Y tile) and N (column tiles sharing the R tile).  VNE_TC_TILE="BN,CM,CN"
+// overrides the default (used to sweep shapes); invalid overrides are ignored.
+struct TcShape {
+    int BN, ntn, CM, CN;
+};
+
+static int pick_cluster(int tiles, int want) {
+    int c = want;
+    while (c > 1 && tiles % c != 0) c /= 2;
+    return c < 1 ? 1 : c;
+}
+
+static TcShape choose_shape(int ncols, int mtiles) {
+    TcShape sh;
+    sh.BN = ncols <= 128 ? (ncols + 31) / 32 * 32 : 128;
+    sh.ntn = (ncols + sh.BN - 1) / sh.BN;
+    sh.CN = pick_cluster(sh.ntn, 2);
+    sh.CM = pick_cluster(mtiles, sh.CN == 2 ? 2 : 4);
+    static int o_bn = -1, o_cm = 0, o_cn = 0;
+    if (o_bn < 0) {
+        o_bn = 0;
+        if (const char* e = getenv("VNE_TC_TILE")) {
+            if (sscanf(e, "%d,%d,%d", &o_bn, &o_cm, &o_cn) != 3) o_bn = 0;
+        }
+    }
+    if (o_bn >= 32 && o_bn <= 256 && o_bn % 32 == 0 && o_cm >= 1 && o_cn >= 1 &&
+        o_cm * o_cn <= 8 && (o_bn / o_cm) % 8 == 0 && (TC_BM / o_cn) % 8 == 0) {
+        TcShape t{o_bn, (ncols + o_bn - 1) / o_bn, o_cm, o_cn};
+        if (mtiles % t.CM == 0 && t.ntn % t.CN == 0) sh = t;
+    }
+    return sh;
 }
 
 cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
@@ -402,20 +574,21 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     }
     const int ncols = col_end - col0;
     if (ncols <= 0) return cudaSuccess;
-    const int ntn = (ncols + 255) / 256;
-    int BN = (ncols + ntn - 1) / ntn;
-    BN = (BN + 31) / 32 * 32;
+    if ((s.ldk % TC_BK) != 0 || (s.rows_pad % TC_BM) != 0) return cudaErrorInvalidValue;
+    const int mtiles = (int)(s.rows_pad / TC_BM);
+    const TcShape sh = choose_shape(ncols, mtiles);
+    const int BN = sh.BN;
     const int S_pad = (s.S + 31) / 32 * 32;
     const bool x3 = s.Rlo != nullptr;
     if (x3 && (!s.Ylo || !s.Ylo_out)) return cudaErrorInvalidValue;
-    if ((s.ldk % TC_BK) != 0 || (s.rows_pad % TC_BM) != 0) return cudaErrorInvalidValue;
 
     CUtensorMap mRhi, mRlo, mYhi, mYlo;
-    if (!make_map(&mRhi, s.Rhi, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mYhi, s.Yhi, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
+    const int arows = TC_BM / sh.CN, brows = BN / sh.CM;
+    if (!make_map(&mRhi, s.Rhi, s.ldk, s.rows_pad, s.ldk, TC_BK, arows)) return cudaErrorInvalidValue;
+    if (!make_map(&mYhi, s.Yhi, s.ldk, S_pad, s.ldk, TC_BK, brows)) return cudaErrorInvalidValue;
     if (x3) {
-        if (!make_map(&mRlo, s.Rlo, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
-        if (!make_map(&mYlo, s.Ylo, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
+        if (!make_map(&mRlo, s.Rlo, s.ldk, s.rows_pad, s.ldk, TC_BK, arows)) return cudaErrorInvalidValue;
+        if (!make_map(&mYlo, s.Ylo, s.ldk, S_pad, s.ldk, TC_BK, brows)) return cudaErrorInvalidValue;
     } else {
         mRlo = mRhi;
         mYlo = mYhi;
@@ -445,18 +618,34 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.stages = stages;
     a.nkb = (int)(s.ldk / TC_BK);
     a.x3 = x3 ? 1 : 0;
+    a.CM = sh.CM;
+    a.CN = sh.CN;
     a.tmem_cols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
     a.cols = s.cols;
     a.sc = s.sc;
     a.P = s.P;
     a.t = s.t;
 
-    cudaError_t e = cudaFuncSetAttribute(k_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(s.rows_pad / TC_BM), (unsigned)ntn);
-    k_tc_step<<<grid, TC_THREADS, smem, st>>>(mRhi, mRlo, mYhi, mYlo, a);
-    return cudaGetLastError();
+    static size_t smem_set = 0;
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)mtiles, (unsigned)sh.ntn, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)sh.CM;
+    attr[0].val.clusterDim.y = (unsigned)sh.CN;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tc_step, mRhi, mRlo, mYhi, mYlo, a);
 }
 
 }  // namespace vne

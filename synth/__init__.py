@@ -149,4 +149,7 @@ WORKLOADS = {
                                  probe="gaussian", power_iters=30),
     "band33_n1e7": dict(kind="band", n=10_000_000, half_bw=16, offdiag_scale=0.02,
                         seed=3, m=30, s=64, probe="rademacher", power_iters=30),
+    # the same band at n = 2e6 (profiling captures of the banded kernels)
+    "band33_n2e6": dict(kind="band", n=2_000_000, half_bw=16, offdiag_scale=0.02,
+                        seed=3, m=30, s=64, probe="rademacher", power_iters=30),
 }
