@@ -378,11 +378,13 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         } else {
             const int Wd = (s + 63) / 64;
             if (f64)
-                c.launched(launch_dia_init<double>((double*)G, bits, Wd, (double*)Yb0, n, S, s,
+                c.launched(launch_dia_init<double>((double*)G, bits, Wd,
+                                                   bits ? nullptr : (double*)Yb0, n, S, s,
                                                    p->probe, p->seed, P, rows_per_tile0, c.st));
             else
-                c.launched(launch_dia_init<float>((float*)G, bits, Wd, (float*)Yb0, n, S, s,
-                                                  p->probe, p->seed, P, rows_per_tile0, c.st));
+                c.launched(launch_dia_init<float>((float*)G, bits, Wd, bits ? nullptr : (float*)Yb0,
+                                                  n, S, s, p->probe, p->seed, P, rows_per_tile0,
+                                                  c.st));
         }
         void* Yb[3] = {Yb0, Yb1, Yb2};
         for (int t = 1; t <= T_steps && c.ok(); ++t) {

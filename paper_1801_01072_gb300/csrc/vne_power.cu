@@ -4,8 +4,11 @@
 // printed algorithm does not normalise; dividing each iterate by its norm
 // leaves the Rayleigh quotient unchanged and keeps t in the tens finite).
 // The norms ||y||^2 (and, after the last product, x_hat^T y and x_hat^T x_hat)
-// are reduced in FP64: per-block partials, then the last block to finish
-// sums them in block order and writes the running sums to the scalar block.
+// are reduced per block and then across blocks in FP64: the last block to
+// finish sums the block partials in a fixed order and writes the running sums
+// to the scalar block.  Per-thread arithmetic uses the accumulation type of
+// the path (FP64 on the FP64 path, FP32 otherwise): FP64 throughput on this
+// part is a small fraction of FP32, so FP64 stays off the per-element path.
 #include "vne_common.cuh"
 #include "vne_internal.h"
 
@@ -18,7 +21,7 @@ __global__ void k_power_init(TX* x0, int64_t n, int q, uint64_t seed, double* sc
     const int64_t total = n * (int64_t)q;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x)
-        x0[e] = (TX)rademacher(seed ^ kPowerSeedXor, (uint64_t)e);
+        x0[e] = (TX)((splitmix_out(seed ^ kPowerSeedXor, (uint64_t)e) >> 63) ? -1 : 1);
     if (blockIdx.x == 0 && threadIdx.x < q) {
         sc[SC_NORM + 3 * threadIdx.x + 0] = (double)n;  // ||x_0||^2 = n
         sc[SC_NORM + 3 * threadIdx.x + 1] = 0.0;
@@ -39,16 +42,35 @@ template cudaError_t launch_power_init<float>(float*, int64_t, int, uint64_t, do
 template cudaError_t launch_power_init<double>(double*, int64_t, int, uint64_t, double*,
                                                cudaStream_t);
 
-// Shared tail of a power step: block partials -> last block -> sc.
-// acc[3*j + {0,1,2}] = this thread's (y.y, xh.y, xh.xh) of trial j.
-__device__ void power_finish(double* acc, int q, double* partial, unsigned int* counter,
+// 1/||x_j|| of the current iterates, computed once per block (FP64) and
+// broadcast through shared memory.
+template <typename TA>
+__device__ __forceinline__ void load_inv_norms(const double* sc, int q, TA* inv_sh) {
+    if (threadIdx.x < q) inv_sh[threadIdx.x] = (TA)(1.0 / sqrt(sc[SC_NORM + 3 * threadIdx.x]));
+    __syncthreads();
+}
+
+// Block partials -> last block -> sc.  acc[3*j + {0,1,2}] holds this
+// thread's (y.y, xh.y, xh.xh) of trial j in the path's accumulation type.
+template <typename TA>
+__device__ void power_finish(const TA* acc, int q, double* partial, unsigned int* counter,
                              double* sc, int final_step, double u_scale) {
+    __shared__ double wsum[8][3 * kMaxTrials];
     __shared__ double sh[32];
     __shared__ bool last;
-    for (int v = 0; v < 3 * q; ++v) {
-        const double t = block_sum(acc[v], sh);
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * 3 * q + v] = t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nv = 3 * q;
+    for (int v = 0; v < nv; ++v) {
+        const TA t = warp_sum(acc[v]);
+        if (lane == 0) wsum[w][v] = (double)t;
     }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double t = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += wsum[ww][threadIdx.x];
+        partial[(size_t)blockIdx.x * 3 * q + threadIdx.x] = t;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
@@ -59,7 +81,7 @@ __device__ void power_finish(double* acc, int q, double* partial, unsigned int* 
     // each of the 3q sums over gridDim.x partials: every thread takes a fixed
     // strided subset, then a fixed-order block reduction (deterministic)
     const volatile double* vp = partial;
-    for (int v = 0; v < 3 * q; ++v) {
+    for (int v = 0; v < nv; ++v) {
         double t = 0.0;
         for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += vp[(size_t)b * 3 * q + v];
         const double tot = block_sum(t, sh);
@@ -92,20 +114,20 @@ template <> struct Ld<double> {
     static __device__ __forceinline__ double get(const double* p) { return __ldg(p); }
 };
 template <> struct Ld<float> {
-    static __device__ __forceinline__ double get(const float* p) { return (double)__ldg(p); }
+    static __device__ __forceinline__ float get(const float* p) { return __ldg(p); }
 };
 
-// Dense: one warp per row, lanes stride over the columns.
+// Dense, any q: one warp per row, lanes stride over the columns.
 template <typename TR, typename TX, typename TA>
 __global__ void __launch_bounds__(256) k_power_dense(const TR* R, int64_t n, int64_t ld,
                                                      const TX* x, TX* y, int q, double* sc,
                                                      double* partial, unsigned int* counter,
                                                      int final_step, double u_scale) {
+    __shared__ TA inv[kMaxTrials];
+    load_inv_norms<TA>(sc, q, inv);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double inv[kMaxTrials];
-    for (int j = 0; j < q; ++j) inv[j] = 1.0 / sqrt(sc[SC_NORM + 3 * j]);
-    double acc[3 * kMaxTrials];
-    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.0;
+    TA acc[3 * kMaxTrials];
+    for (int v = 0; v < 3 * q; ++v) acc[v] = (TA)0;
     for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
         TA a[kMaxTrials];
         for (int j = 0; j < q; ++j) a[j] = (TA)0;
@@ -115,32 +137,32 @@ __global__ void __launch_bounds__(256) k_power_dense(const TR* R, int64_t n, int
             for (int j = 0; j < q; ++j) a[j] += r * (TA)x[(int64_t)j * n + k];
         }
         for (int j = 0; j < q; ++j) {
-            const double yv = (double)warp_sum(a[j]) * inv[j];
+            const TA yv = warp_sum(a[j]) * inv[j];
             if (lane == 0) {
                 y[(int64_t)j * n + i] = (TX)yv;
                 acc[3 * j + 0] += yv * yv;
                 if (final_step) {
-                    const double xh = (double)x[(int64_t)j * n + i] * inv[j];
+                    const TA xh = (TA)x[(int64_t)j * n + i] * inv[j];
                     acc[3 * j + 1] += xh * yv;
                     acc[3 * j + 2] += xh * xh;
                 }
             }
         }
     }
-    power_finish(acc, q, partial, counter, sc, final_step, u_scale);
+    power_finish<TA>(acc, q, partial, counter, sc, final_step, u_scale);
 }
 
-// bf16 rows (16-byte aligned, ld % 8 == 0): 8 entries per lane per load.
+// bf16 rows (16-byte aligned, ld % 8 == 0), any q: 8 entries per lane per load.
 __global__ void __launch_bounds__(256) k_power_dense_bf16(const __nv_bfloat16* R, int64_t n,
                                                           int64_t ld, const float* x, float* y,
                                                           int q, double* sc, double* partial,
                                                           unsigned int* counter, int final_step,
                                                           double u_scale) {
+    __shared__ float inv[kMaxTrials];
+    load_inv_norms<float>(sc, q, inv);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double inv[kMaxTrials];
-    for (int j = 0; j < q; ++j) inv[j] = 1.0 / sqrt(sc[SC_NORM + 3 * j]);
-    double acc[3 * kMaxTrials];
-    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.0;
+    float acc[3 * kMaxTrials];
+    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.f;
     const int64_t nvec = n / 8;  // full 8-wide groups
     for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
         float a[kMaxTrials];
@@ -168,30 +190,33 @@ __global__ void __launch_bounds__(256) k_power_dense_bf16(const __nv_bfloat16* R
             for (int j = 0; j < q; ++j) a[j] += r * x[(int64_t)j * n + k];
         }
         for (int j = 0; j < q; ++j) {
-            const double yv = (double)warp_sum(a[j]) * inv[j];
+            const float yv = warp_sum(a[j]) * inv[j];
             if (lane == 0) {
-                y[(int64_t)j * n + i] = (float)yv;
+                y[(int64_t)j * n + i] = yv;
                 acc[3 * j + 0] += yv * yv;
                 if (final_step) {
-                    const double xh = (double)x[(int64_t)j * n + i] * inv[j];
+                    const float xh = x[(int64_t)j * n + i] * inv[j];
                     acc[3 * j + 1] += xh * yv;
                     acc[3 * j + 2] += xh * xh;
                 }
             }
         }
     }
-    power_finish(acc, q, partial, counter, sc, final_step, u_scale);
+    power_finish<float>(acc, q, partial, counter, sc, final_step, u_scale);
 }
 
 // bf16 rows, one trial: U independent 16-byte loads per lane in flight.
+// (Sharing x loads across two rows per warp was measured slower.)
 template <int U>
 __global__ void __launch_bounds__(256) k_power_dense_bf16_q1(
     const __nv_bfloat16* __restrict__ R, int64_t n, int64_t ld, const float* __restrict__ x,
     float* __restrict__ y, double* sc, double* partial, unsigned int* counter, int final_step,
     double u_scale) {
+    __shared__ float inv_sh[1];
+    load_inv_norms<float>(sc, 1, inv_sh);
+    const float inv = inv_sh[0];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const double inv = 1.0 / sqrt(sc[SC_NORM]);
-    double acc[3] = {0.0, 0.0, 0.0};
+    float acc[3] = {0.f, 0.f, 0.f};
     const int64_t nvec = n / 8;
     for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < n; i += (int64_t)gridDim.x * 8) {
         const __nv_bfloat16* row = R + i * ld;
@@ -221,18 +246,18 @@ __global__ void __launch_bounds__(256) k_power_dense_bf16_q1(
             }
         }
         for (int64_t k = nvec * 8 + lane; k < n; k += 32) a += __bfloat162float(row[k]) * x[k];
-        const double yv = (double)warp_sum(a) * inv;
+        const float yv = warp_sum(a) * inv;
         if (lane == 0) {
-            y[i] = (float)yv;
+            y[i] = yv;
             acc[0] += yv * yv;
             if (final_step) {
-                const double xh = (double)x[i] * inv;
+                const float xh = x[i] * inv;
                 acc[1] += xh * yv;
                 acc[2] += xh * xh;
             }
         }
     }
-    power_finish(acc, 1, partial, counter, sc, final_step, u_scale);
+    power_finish<float>(acc, 1, partial, counter, sc, final_step, u_scale);
 }
 
 cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_t ld,
@@ -255,7 +280,21 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
     } else {
         if (xdouble || (ld % 8) != 0) return cudaErrorInvalidValue;
         if (q == 1) {
-            k_power_dense_bf16_q1<8><<<blocks, 256, 0, st>>>(
+            // one wave of resident blocks (grid-stride over rows): a partial
+            // second wave would leave most of the memory system idle
+            static int per_sm = 0, sms = 0;
+            if (!per_sm) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_power_dense_bf16_q1<16>,
+                                                                  256, 0) != cudaSuccess ||
+                    per_sm < 1)
+                    per_sm = 1;
+            }
+            int b1 = per_sm * sms;
+            if (b1 > blocks) b1 = blocks;
+            k_power_dense_bf16_q1<16><<<b1, 256, 0, st>>>(
                 (const __nv_bfloat16*)R, n, ld, (const float*)x, (float*)y, sc, partial, counter,
                 final_step, u_scale);
             return cudaGetLastError();
@@ -270,14 +309,15 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
 // Banded: one thread per row,
 // y_i = sum_d R[i,i+d] x_{i+d} + sum_{d>0} R[i-d,i] x_{i-d}.
 template <typename T>
-__global__ void __launch_bounds__(256) k_power_dia(const T* vals, int64_t n, int64_t ld, int D,
-                                                   const T* x, T* y, int q, double* sc,
+__global__ void __launch_bounds__(256) k_power_dia(const T* __restrict__ vals, int64_t n,
+                                                   int64_t ld, int D, const T* __restrict__ x,
+                                                   T* __restrict__ y, int q, double* sc,
                                                    double* partial, unsigned int* counter,
                                                    int final_step, double u_scale) {
-    double inv[kMaxTrials];
-    for (int j = 0; j < q; ++j) inv[j] = 1.0 / sqrt(sc[SC_NORM + 3 * j]);
-    double acc[3 * kMaxTrials];
-    for (int v = 0; v < 3 * q; ++v) acc[v] = 0.0;
+    __shared__ T inv[kMaxTrials];
+    load_inv_norms<T>(sc, q, inv);
+    T acc[3 * kMaxTrials];
+    for (int v = 0; v < 3 * q; ++v) acc[v] = (T)0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         for (int j = 0; j < q; ++j) {
@@ -287,17 +327,70 @@ __global__ void __launch_bounds__(256) k_power_dia(const T* vals, int64_t n, int
                 if (i + d < n) a += vals[(int64_t)d * ld + i] * xj[i + d];
                 if (i - d >= 0) a += vals[(int64_t)d * ld + i - d] * xj[i - d];
             }
-            const double yv = (double)a * inv[j];
-            y[(int64_t)j * n + i] = (T)yv;
+            const T yv = a * inv[j];
+            y[(int64_t)j * n + i] = yv;
             acc[3 * j + 0] += yv * yv;
             if (final_step) {
-                const double xh = (double)xj[i] * inv[j];
+                const T xh = xj[i] * inv[j];
                 acc[3 * j + 1] += xh * yv;
                 acc[3 * j + 2] += xh * xh;
             }
         }
     }
-    power_finish(acc, q, partial, counter, sc, final_step, u_scale);
+    power_finish<T>(acc, q, partial, counter, sc, final_step, u_scale);
+}
+
+// Banded, one trial, compile-time window: every band and x load of a row is
+// independent and unrolled; interior rows skip the bounds checks.
+template <typename T, int HB>
+__global__ void __launch_bounds__(256) k_power_dia_q1(const T* __restrict__ vals, int64_t n,
+                                                      int64_t ld, int D, const T* __restrict__ x,
+                                                      T* __restrict__ y, double* sc,
+                                                      double* partial, unsigned int* counter,
+                                                      int final_step, double u_scale) {
+    __shared__ T inv_sh[1];
+    load_inv_norms<T>(sc, 1, inv_sh);
+    const T inv = inv_sh[0];
+    T acc[3] = {(T)0, (T)0, (T)0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T a = __ldg(vals + i) * __ldg(x + i);
+        if (i >= HB && i + HB < n && D == HB + 1) {
+#pragma unroll
+            for (int d = 1; d <= HB; ++d) {
+                a = Math<T>::fma(__ldg(vals + (int64_t)d * ld + i), __ldg(x + i + d), a);
+                a = Math<T>::fma(__ldg(vals + (int64_t)d * ld + i - d), __ldg(x + i - d), a);
+            }
+        } else {
+#pragma unroll
+            for (int d = 1; d <= HB; ++d) {
+                if (d < D && i + d < n) a += __ldg(vals + (int64_t)d * ld + i) * __ldg(x + i + d);
+                if (d < D && i - d >= 0) a += __ldg(vals + (int64_t)d * ld + i - d) * __ldg(x + i - d);
+            }
+        }
+        const T yv = a * inv;
+        y[i] = yv;
+        acc[0] += yv * yv;
+        if (final_step) {
+            const T xh = __ldg(x + i) * inv;
+            acc[1] += xh * yv;
+            acc[2] += xh * xh;
+        }
+    }
+    power_finish<T>(acc, 1, partial, counter, sc, final_step, u_scale);
+}
+
+template <typename T>
+static void launch_power_dia_q1(int hb, int blocks, cudaStream_t st, const T* vals, int64_t n,
+                                int64_t ld, int D, const T* x, T* y, double* sc, double* partial,
+                                unsigned int* counter, int final_step, double u_scale) {
+    switch (hb) {
+        case 1: k_power_dia_q1<T, 1><<<blocks, 256, 0, st>>>(vals, n, ld, D, x, y, sc, partial, counter, final_step, u_scale); break;
+        case 2: k_power_dia_q1<T, 2><<<blocks, 256, 0, st>>>(vals, n, ld, D, x, y, sc, partial, counter, final_step, u_scale); break;
+        case 4: k_power_dia_q1<T, 4><<<blocks, 256, 0, st>>>(vals, n, ld, D, x, y, sc, partial, counter, final_step, u_scale); break;
+        case 8: k_power_dia_q1<T, 8><<<blocks, 256, 0, st>>>(vals, n, ld, D, x, y, sc, partial, counter, final_step, u_scale); break;
+        default: k_power_dia_q1<T, 16><<<blocks, 256, 0, st>>>(vals, n, ld, D, x, y, sc, partial, counter, final_step, u_scale); break;
+    }
 }
 
 cudaError_t launch_power_step_dia(const void* vals, int rdtype, int64_t n, int64_t ld, int D,
@@ -308,6 +401,18 @@ cudaError_t launch_power_step_dia(const void* vals, int rdtype, int64_t n, int64
     int64_t want = (n + 255) / 256;
     int blocks = (int)(want < nblocks ? want : nblocks);
     if (blocks < 1) blocks = 1;
+    const int hb = dia_supported_halfbw(D);
+    if (q == 1 && hb > 0) {
+        if (rdtype == 0)
+            launch_power_dia_q1<double>(hb, blocks, st, (const double*)vals, n, ld, D,
+                                        (const double*)x, (double*)y, sc, partial, counter,
+                                        final_step, u_scale);
+        else
+            launch_power_dia_q1<float>(hb, blocks, st, (const float*)vals, n, ld, D,
+                                       (const float*)x, (float*)y, sc, partial, counter,
+                                       final_step, u_scale);
+        return cudaGetLastError();
+    }
     if (rdtype == 0)
         k_power_dia<double><<<blocks, 256, 0, st>>>((const double*)vals, n, ld, D,
                                                     (const double*)x, (double*)y, q, sc, partial,

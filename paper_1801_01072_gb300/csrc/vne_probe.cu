@@ -52,9 +52,15 @@ __global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo
             }
         }
     }
-    const double tot = block_sum(g * g, sh);
-    if (threadIdx.x == 0)
+    // g^2 summed in the path's precision within each warp, FP64 across warps
+    const T gw = warp_sum((T)(g * g));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)gw;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
         for (int c = j; c < S; c += s) P.slot(0)[(size_t)blockIdx.x * S + c] = tot;
+    }
 }
 
 template <typename T>
@@ -80,9 +86,9 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
     __shared__ double sh[8][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nchunk = (s + 31) >> 5;  // <= 8
-    double acc[8];
+    T acc[8];  // per-lane sums of g^2 in the path's precision
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 8; ++q) acc[q] = (T)0;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_tile;
     int64_t r1 = r0 + rows_per_tile;
     if (r1 > n) r1 = n;
@@ -93,14 +99,19 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
             words[q] = 0u;
             if (q < nchunk) {
                 const int j = q * 32 + lane;
-                double g = 0.0;
-                if (j < s) g = probe_value(kind, seed, (uint64_t)j * (uint64_t)n + (uint64_t)i);
-                words[q] = __ballot_sync(0xffffffffu, g < 0.0);
+                // Rademacher signs straight from the hash bit (no FP64 on this path)
+                T gt = (T)0;
                 if (j < s) {
-                    const T gt = (T)g;
+                    const uint64_t e = (uint64_t)j * (uint64_t)n + (uint64_t)i;
+                    if (kind == 0) gt = (splitmix_out(seed, e) >> 63) ? (T)-1 : (T)1;
+                    else gt = (T)gaussian(seed, e);
+                }
+                words[q] = __ballot_sync(0xffffffffu, gt < (T)0);
+                if (j < s) {
                     if (G) G[i * s + j] = gt;
-                    for (int c = j; c < S; c += s) Y0[i * S + c] = gt;
-                    acc[q] += g * g;
+                    if (Y0)  // the Rademacher path reads Y_0 from the bits instead
+                        for (int c = j; c < S; c += s) Y0[i * S + c] = gt;
+                    acc[q] += gt * gt;
                 }
             }
         }
@@ -111,7 +122,7 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-        if (q < nchunk) sh[w][q * 32 + lane] = acc[q];
+        if (q < nchunk) sh[w][q * 32 + lane] = (double)acc[q];
     __syncthreads();
     for (int j = threadIdx.x; j < s; j += blockDim.x) {
         double t = 0.0;

@@ -135,6 +135,22 @@ __device__ __forceinline__ uint32_t cluster_ctaid_x() {
     asm volatile("mov.u32 %0, %%cluster_ctaid.x;" : "=r"(r));
     return r;
 }
+__device__ __forceinline__ uint32_t cluster_ctaid_z() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.z;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t mapa_peer(uint32_t local_addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                              uint32_t d) {
+    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b),
+                 "r"(c), "r"(d)
+                 : "memory");
+}
 __device__ __forceinline__ uint32_t cluster_ctaid_y() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctaid.y;" : "=r"(r));
@@ -216,6 +232,7 @@ struct TcArgs {
     int col0, col_end;  // active columns [col0, col_end)
     int BN, stages, nkb, x3;
     int CM, CN;  // cluster shape: CM CTAs along M share B tiles, CN along N share A tiles
+    int ksplit;  // 2: a CTA pair (cluster along z) splits K and swaps half accumulators
     uint32_t tmem_cols;
     StepCols cols;
     const double* sc;
@@ -249,14 +266,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // loads 128/CN rows and multicasts them), the CM CTAs of one N column share
     // the B tile (BN/CM rows each).  A ring slot is refilled only when every
     // CTA of the cluster has released it (empty barrier count = cluster size).
-    const int csize = a.CM * a.CN;
-    int cx = 0, cy = 0;
+    const int csize = a.CM * a.CN;  // multicast group
+    const bool in_cluster = csize > 1 || a.ksplit > 1;
+    int cx = 0, cy = 0, kz = 0;
     bool rank_ok = true;
-    if (csize > 1) {
+    if (in_cluster) {
         cx = (int)cluster_ctaid_x();
         cy = (int)cluster_ctaid_y();
-        rank_ok = (int)cluster_ctarank() == cx + cy * a.CM;
+        kz = (int)cluster_ctaid_z();
+        rank_ok = (int)cluster_ctarank() == cx + cy * a.CM + kz * csize;
     }
+    // K range of this CTA (the whole K unless the pair splits it)
+    const int kb_begin = a.ksplit > 1 ? kz * (a.nkb / 2) : 0;
+    const int kb_end = a.ksplit > 1 ? (kz == 0 ? a.nkb / 2 : a.nkb) : a.nkb;
+    const int nkb_local = kb_end - kb_begin;
     uint16_t maskA = 0, maskB = 0, mask_all = 0;
     if (csize > 1) {
         for (int y = 0; y < a.CN; ++y) maskA |= (uint16_t)(1u << (cx + y * a.CM));
@@ -287,7 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (csize > 1) cluster_sync_all();  // peers' barriers are initialised before any multicast
+    if (in_cluster) cluster_sync_all();  // peers' barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     if (!rank_ok && threadIdx.x == 0) *abort_flag = 1;
@@ -300,9 +323,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint64_t pol_R = policy_evict_first();
         const uint64_t pol_Y = policy_evict_last();
         int issued_kb = 0;
-        for (int kb = 0; kb < a.nkb && rank_ok; ++kb) {
-            const int st = kb % a.stages;
-            const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
+        for (int i = 0; i < nkb_local && rank_ok; ++i) {
+            const int kb = kb_begin + i;
+            const int st = i % a.stages;
+            const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
             if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) {
                 timed_out = true;
                 break;
@@ -325,7 +349,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d_hint(sBl + offB, &mapYlo, &full_bar[st], kb * TC_BK, n0 + cx * brows,
                                  maskB, pol_Y);
             }
-            issued_kb = kb + 1;
+            issued_kb = i + 1;
         }
         if (timed_out) {
             *abort_flag = 1;
@@ -333,15 +357,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int first = issued_kb - a.stages;
             if (first < 0) first = 0;
             volatile int never = 0;
-            for (int kb = first; kb < issued_kb; ++kb)
-                mbar_wait(&full_bar[kb % a.stages], (uint32_t)(kb / a.stages) & 1u, &never);
+            for (int i = first; i < issued_kb; ++i)
+                mbar_wait(&full_bar[i % a.stages], (uint32_t)(i / a.stages) & 1u, &never);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16(TC_BM, a.BN);
-        for (int kb = 0; kb < a.nkb && rank_ok; ++kb) {
-            const int st = kb % a.stages;
-            const uint32_t ph = (uint32_t)(kb / a.stages) & 1u;
+        for (int i = 0; i < nkb_local && rank_ok; ++i) {
+            const int st = i % a.stages;
+            const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
             if (!mbar_wait(&full_bar[st], ph, abort_flag)) {
                 timed_out = true;
                 break;
@@ -353,7 +377,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < TC_BK / 16; ++k) {
                 // +32 bytes along K per K=16 slice (descriptor units of 16 B)
-                umma_bf16(tmem_base, dA + 2 * k, dB + 2 * k, idesc, (kb | k) != 0);
+                umma_bf16(tmem_base, dA + 2 * k, dB + 2 * k, idesc, (i | k) != 0);
             }
             if (a.x3) {
                 const uint32_t aAl = aB + bytesB, aBl = aAl + bytesA;
@@ -373,6 +397,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     __syncwarp();
 
+    const int rg = warp & 3, chalf = warp >> 2;
+    const int row = m0 + rg * 32 + lane;
+    const bool row_ok = row < a.n;
+    const float uf = (float)a.sc[SC_U];  // FP32 from here on (FP64 is slow on this part)
+    const float fa = 2.0f / uf, finvu = 1.0f / uf;
+    const int nchunks = a.BN / 32;
+    // Split K: the pair swaps halves of their partial accumulators through
+    // distributed shared memory (the operand ring is free by now); CTA kz
+    // then finishes the chunks [kz*nchunks/2, (kz+1)*nchunks/2).
+    const int half = nchunks / 2;
+    const int ck_lo = a.ksplit > 1 ? kz * half : 0;
+    const int ck_hi = a.ksplit > 1 ? ck_lo + half : nchunks;
+    const int RS = half * 32 + 4;  // padded row stride (floats) of the receive buffer
+    // Epilogue operands (G, Y_{t-1}, Y_{t-2}) of a 32-column chunk: every load
+    // of the chunk is issued before any store (the stores could otherwise alias
+    // them and serialise the chunk).  Issuing them during the mainloop instead
+    // was measured slower: they compete with the operand stream.
+    float gv[32], yp[32], yp2[32];
+    auto prefetch = [&](int ck) {
+        const int cbase = n0 + ck * 32;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int c = cbase + q;  // warp-uniform
+            gv[q] = 0.f;
+            yp[q] = 0.f;
+            yp2[q] = 0.f;
+            if (c >= a.col_end || !row_ok) continue;
+            const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
+            const int64_t idx = (int64_t)c * a.n + row;
+            gv[q] = __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
+            if (!cheb || a.cols.cheb_kind == EPI_CHEB) yp[q] = __ldg(a.Yprev + idx);
+            if (cheb && a.cols.cheb_kind == EPI_CHEB) yp2[q] = __ldg(a.Yprev2 + idx);
+        }
+    };
+    const int ck_first = ck_lo + chalf;
+
     // ---------------- epilogue (all warps) ----------------
     bool have_acc = mbar_wait(accum_bar, 0u, abort_flag);
     if (!have_acc) {
@@ -384,36 +444,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     __syncwarp();
 
-    const int rg = warp & 3, chalf = warp >> 2;
-    const int row = m0 + rg * 32 + lane;
-    const bool row_ok = row < a.n;
-    const double u = a.sc[SC_U];
-    const float fa = (float)(2.0 / u), finvu = (float)(1.0 / u);
-    const int nchunks = a.BN / 32;
+    const float* recv = reinterpret_cast<const float*>(smem);
+    if (a.ksplit > 1) {
+        cluster_sync_all();  // both accumulators are final and both rings are idle
+        if (!aborted) {
+            const int peer = 1 - kz;
+            const uint32_t rbase = mapa_peer(smem_u32(smem), (uint32_t)peer);
+            for (int ck = peer * half + chalf; ck < peer * half + half; ck += 2) {
+                uint32_t r[32];
+                TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
+                tmem_wait_ld();
+                const uint32_t dst =
+                    rbase + (uint32_t)(((rg * 32 + lane) * RS + (ck - peer * half) * 32) * 4);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    st_cluster_v4(dst + 16 * q, r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+            }
+        }
+        cluster_sync_all();  // the peer's half has landed here
+    }
     if (!aborted) {
-        for (int ck = chalf; ck < nchunks; ck += 2) {
+        for (int ck = ck_first; ck < ck_hi; ck += 2) {
             uint32_t r[32];
             const uint32_t taddr = tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32);
             TMEM_LD32(taddr, r);
-            // Issue every global load of the chunk before the first store, so
-            // the 32 columns' loads are in flight together (the stores could
-            // otherwise alias them and serialise the chunk).
             const int cbase = n0 + ck * 32;
-            float gv[32], yp[32], yp2[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int c = cbase + q;  // warp-uniform
-                gv[q] = 0.f;
-                yp[q] = 0.f;
-                yp2[q] = 0.f;
-                if (c >= a.col_end || !row_ok) continue;
-                const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
-                const int64_t idx = (int64_t)c * a.n + row;
-                gv[q] = __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
-                if (!cheb || a.cols.cheb_kind == EPI_CHEB) yp[q] = __ldg(a.Yprev + idx);
-                if (cheb && a.cols.cheb_kind == EPI_CHEB) yp2[q] = __ldg(a.Yprev2 + idx);
-            }
+            prefetch(ck);
             tmem_wait_ld();
+            if (a.ksplit > 1) {
+                const float4* rp = reinterpret_cast<const float4*>(
+                    recv + (rg * 32 + lane) * RS + (ck - ck_lo) * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 p4 = rp[q];
+                    r[4 * q] = __float_as_uint(__uint_as_float(r[4 * q]) + p4.x);
+                    r[4 * q + 1] = __float_as_uint(__uint_as_float(r[4 * q + 1]) + p4.y);
+                    r[4 * q + 2] = __float_as_uint(__uint_as_float(r[4 * q + 2]) + p4.z);
+                    r[4 * q + 3] = __float_as_uint(__uint_as_float(r[4 * q + 3]) + p4.w);
+                }
+            }
             float v[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
@@ -456,7 +525,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     if (!aborted) {
-        for (int cl = threadIdx.x; cl < a.BN; cl += blockDim.x) {
+        for (int cl = ck_lo * 32 + threadIdx.x; cl < ck_hi * 32; cl += blockDim.x) {
             const int c = n0 + cl;
             if (c >= a.col_end) continue;
             const double tot = (double)red[cl] + (double)red[a.BN + cl] +
@@ -465,7 +534,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     }
     // no CTA leaves while a peer may still multicast into it or arrive on it
-    if (csize > 1) cluster_sync_all();
+    if (in_cluster) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -532,7 +601,7 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t 
 // Y tile) and N (column tiles sharing the R tile).  VNE_TC_TILE="BN,CM,CN"
 // overrides the default (used to sweep shapes); invalid overrides are ignored.
 struct TcShape {
-    int BN, ntn, CM, CN;
+    int BN, ntn, CM, CN, ksplit;
 };
 
 static int pick_cluster(int tiles, int want) {
@@ -541,29 +610,36 @@ static int pick_cluster(int tiles, int want) {
     return c < 1 ? 1 : c;
 }
 
-static TcShape choose_shape(int ncols, int mtiles) {
+// Default: the widest tile (BN up to 256 columns, the largest N of one MMA);
+// when that leaves most SMs idle, a CTA pair splits K (ksplit = 2).
+static TcShape choose_shape(int ncols, int mtiles, int nkb, int sm_count) {
     TcShape sh;
-    sh.BN = ncols <= 128 ? (ncols + 31) / 32 * 32 : 128;
+    const int ntn = (ncols + 255) / 256;
+    sh.BN = ((ncols + ntn - 1) / ntn + 31) / 32 * 32;
     sh.ntn = (ncols + sh.BN - 1) / sh.BN;
-    sh.CN = pick_cluster(sh.ntn, 2);
-    sh.CM = pick_cluster(mtiles, sh.CN == 2 ? 2 : 4);
-    static int o_bn = -1, o_cm = 0, o_cn = 0;
+    sh.CM = sh.CN = 1;
+    sh.ksplit = 1;
+    if ((int64_t)mtiles * sh.ntn * 4 < (int64_t)sm_count * 3 && sh.BN % 64 == 0 && nkb >= 2)
+        sh.ksplit = 2;
+    static int o_bn = -1, o_cm = 0, o_cn = 0, o_ks = 1;
     if (o_bn < 0) {
         o_bn = 0;
         if (const char* e = getenv("VNE_TC_TILE")) {
-            if (sscanf(e, "%d,%d,%d", &o_bn, &o_cm, &o_cn) != 3) o_bn = 0;
+            const int got = sscanf(e, "%d,%d,%d,%d", &o_bn, &o_cm, &o_cn, &o_ks);
+            if (got < 3) o_bn = 0;
+            if (got < 4) o_ks = 1;
         }
     }
     if (o_bn >= 32 && o_bn <= 256 && o_bn % 32 == 0 && o_cm >= 1 && o_cn >= 1 &&
-        o_cm * o_cn <= 8 && (o_bn / o_cm) % 8 == 0 && (TC_BM / o_cn) % 8 == 0) {
-        TcShape t{o_bn, (ncols + o_bn - 1) / o_bn, o_cm, o_cn};
+        o_cm * o_cn <= 8 && (o_bn / o_cm) % 8 == 0 && (TC_BM / o_cn) % 8 == 0 &&
+        (o_ks == 1 || (o_ks == 2 && o_cm == 1 && o_cn == 1 && o_bn % 64 == 0 && nkb >= 2))) {
+        TcShape t{o_bn, (ncols + o_bn - 1) / o_bn, o_cm, o_cn, o_ks};
         if (mtiles % t.CM == 0 && t.ntn % t.CN == 0) sh = t;
     }
     return sh;
 }
 
 cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
-    (void)sm_count;
     int col0, col_end;
     if (s.cols.ncheb > 0) {
         col0 = s.cols.cheb_c0;
@@ -576,7 +652,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     if (ncols <= 0) return cudaSuccess;
     if ((s.ldk % TC_BK) != 0 || (s.rows_pad % TC_BM) != 0) return cudaErrorInvalidValue;
     const int mtiles = (int)(s.rows_pad / TC_BM);
-    const TcShape sh = choose_shape(ncols, mtiles);
+    const TcShape sh = choose_shape(ncols, mtiles, (int)(s.ldk / TC_BK), sm_count);
     const int BN = sh.BN;
     const int S_pad = (s.S + 31) / 32 * 32;
     const bool x3 = s.Rlo != nullptr;
@@ -620,6 +696,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.x3 = x3 ? 1 : 0;
     a.CM = sh.CM;
     a.CN = sh.CN;
+    a.ksplit = sh.ksplit;
     a.tmem_cols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
     a.cols = s.cols;
     a.sc = s.sc;
@@ -634,7 +711,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
         smem_set = smem;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)mtiles, (unsigned)sh.ntn, 1);
+    cfg.gridDim = dim3((unsigned)mtiles, (unsigned)sh.ntn, (unsigned)sh.ksplit);
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -642,7 +719,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)sh.CM;
     attr[0].val.clusterDim.y = (unsigned)sh.CN;
-    attr[0].val.clusterDim.z = 1;
+    attr[0].val.clusterDim.z = (unsigned)sh.ksplit;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_tc_step, mRhi, mRlo, mYhi, mYlo, a);

@@ -95,6 +95,20 @@ def test_power_method_f64(q):
     assert p.max() / 6 <= lam <= p.max() * (1 + 1e-12)  # Lemma lem:power bracket
 
 
+@pytest.mark.parametrize("n,q", [(300, 1), (1024, 1), (2500, 1), (1024, 3)])
+def test_power_method_tensor_core_path(n, q):
+    """The BF16 path's power method (per-row-scaled e4m3 copy of R for one
+    trial, bf16 for several) stays within the BF16 path's 1e-3 of the FP64
+    power method.  (After t = 30 products the iterate is not converged, so the
+    Rayleigh quotient moves to first order with the rounding of R; the
+    deviation, ~1e-4, is far below the method's own gap to p_1.)"""
+    R, p, _ = synth.dense_exp(n, n / 10.0, seed=40 + n)
+    lam = vne.lambda_max(dev(R), power_iters=30, power_trials=q, seed=2, precision="bf16")
+    ref, _ = O.power_method(R, rng.power_start(n, q, 2), 30)
+    assert rel(lam, ref) < 1e-3
+    assert abs(lam - ref) < 0.1 * (p.max() - ref)  # well inside the power method's own error
+
+
 def test_dense_n512_exp_spectrum_full_pipeline():
     """n = 512, p_i ~ exp(-i/50), m = 20, s = 50 Rademacher, t = 30, FP64."""
     R, p, _ = synth.dense_exp(512, 50.0, seed=1)
