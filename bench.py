@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -45,6 +46,24 @@ def peaks():
         except Exception:
             pass
     return dict(FALLBACK_PEAKS), "fallback"
+
+
+def profiled_traffic(profile_name, source):
+    """DRAM bytes per launch recorded in profiles/<profile_name> by an ncu
+    capture, or None when the kernel source changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", profile_name)
+    src = os.path.join(ROOT, "paper_1801_01072_gb300", "csrc", source)
+    if not (os.path.exists(prof) and os.path.exists(src)):
+        return None
+    text = open(prof).read()
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if f"{source} {digest}" not in text:
+        return None
+    for line in text.splitlines():
+        if line.strip().startswith("- traffic_bytes_per_launch:"):
+            return int(line.split(":")[1])
+    return None
 
 
 def peak_value(d, *keys):
@@ -87,7 +106,7 @@ class Clocks:
 
     def __init__(self, device_index=0):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"vne_clocks_{os.getpid()}.csv")
         self.dev = device_index
 
     def __enter__(self):
@@ -288,23 +307,36 @@ def run_gpu(args):
             bound, unit = "tensor", "TFLOP/s"
         else:
             peak, bound, unit = None, "alu", "TFLOP/s"
+        # DRAM bytes of one fused 256-column launch (ncu), when the source is unchanged
+        traffic = profiled_traffic("k_tc_step_dense_n8192.md", "vne_tc.cu") \
+            if (kind == 0 and args.workload == "dense_powerlaw_n8192") else None
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": traffic,
                 "kernel": "k_tc_step" if kind == 0 else "k_simt_step",
                 "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
                 "peak_source": pk_src + (" bf16 sustained" if peak else "")}
     else:
-        bytes_step = (3 * 4 * n * s + w["half_bw"] * 0 + (w["half_bw"] + 1) * 4 * n) * m
-        achieved = bytes_step * args.steps / (k_ms / 1e3) / 1e9 if k_ms > 0 else None
+        # algorithmic bytes of the m banded steps of one estimate: every step reads
+        # the band (4n(D)) and the packed signs (8n per 64 probes) and writes Y_t
+        # (4ns); step t >= 2 reads Y_{t-1}; step t >= 3 also reads Y_{t-2}
+        # (steps 1 and 2 take Y_0 from the signs)
+        band_b = 4 * n * (w["half_bw"] + 1) + 8 * n * ((s + 63) // 64)
+        y_b = 4 * n * s
+        bytes_est = sum(band_b + y_b + (y_b if t >= 2 else 0) + (y_b if t >= 3 else 0)
+                        for t in range(1, m + 1))
+        achieved = bytes_est * args.steps / (k_ms / 1e3) / 1e9 if k_ms > 0 else None
         peak = peak_value(pk, "hbm_gbs")
+        # DRAM bytes of one general step at n = 2e6 (ncu), scaled to this n
+        tr = profiled_traffic("k_dia_step_band_n2e6.md", "vne_dia.cu")
+        traffic = int(tr * n / 2e6) if tr else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if (achieved and peak) else None, "traffic": None,
+                "frac": achieved / peak if (achieved and peak) else None, "traffic": traffic,
                 "kernel": "k_dia_step", "launches": k_n,
                 "avg_launch_us": k_ms / max(k_n, 1) * 1e3, "peak_source": pk_src + " hbm"}
 
     cpu = None
     if world == 1 and not args.skip_cpu:
-        s_sample = args.cpu_probes
+        s_sample = args.cpu_probes if dense else min(args.cpu_probes, 2)
         t_full, desc, threads = oracle_sample_time(w, Rh, s_sample)
         cpu = {"value": 1.0 / t_full, "unit": "entropies/s", "cores": threads, "kind": "oracle",
                "sample": desc}
