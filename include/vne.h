@@ -198,11 +198,13 @@ vne_status vne_lambda_max_static(const vne_matrix* R, const vne_params* p, doubl
 vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, uint64_t seed,
                            double* out, void* stream);
 
-/* Per-kernel timing: when enabled, the handle brackets every launch of the
- * recurrence kernels with CUDA events on the call's stream.  vne_profile_read
- * returns the total time (ms) and the launch count of kernel class `kind`
- * (0 = dense tensor-core step, 1 = dense SIMT step, 2 = banded step,
- * 3 = power-method step) since the last reset. */
+/* Per-kernel timing: when enabled, the handle records CUDA events on the call's
+ * stream around the launches of kernel class `kind` (0 = dense tensor-core
+ * steps, 1 = dense SIMT steps, 2 = banded steps, 3 = power-method products):
+ * around each launch for classes 1-3, and around the whole run of consecutive
+ * tensor-core steps of a call for class 0 (those launches overlap each other's
+ * start-up, which an event between them would prevent).  vne_profile_read
+ * returns the total time (ms) and the number of launches since the last reset. */
 vne_status vne_profile_enable(vne_handle* h, int32_t on);
 vne_status vne_profile_read(vne_handle* h, int32_t kind, double* total_ms, int64_t* launches);
 vne_status vne_profile_reset(vne_handle* h);

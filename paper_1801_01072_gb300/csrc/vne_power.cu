@@ -11,6 +11,7 @@
 // part is a small fraction of FP32, so FP64 stays off the per-element path.
 #include "vne_common.cuh"
 #include "vne_internal.h"
+#include "vne_ptx.cuh"
 
 namespace vne {
 
@@ -260,6 +261,128 @@ __global__ void __launch_bounds__(256) k_power_dense_bf16_q1(
     power_finish<float>(acc, 1, partial, counter, sc, final_step, u_scale);
 }
 
+// bf16 rows, one trial, streamed.  A persistent CTA owns a contiguous range of
+// rows and streams them through shared memory with 1-D bulk copies (a ring of
+// ST stages of RB rows, one mbarrier each), so the HBM stream needs a handful
+// of instructions per 16 KB row.  Each thread keeps the x values of its NG
+// column groups (8 columns each) in registers for the whole launch; a row's
+// dot product is a per-thread partial plus one block reduction per RB rows.
+constexpr int kStreamRB = 4;      // rows per stage
+constexpr int kStreamStages = 3;  // ring depth
+
+template <int NG>
+__global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
+    const __nv_bfloat16* __restrict__ R, int64_t n, int64_t ld, const float* __restrict__ x,
+    float* __restrict__ y, double* sc, double* partial, unsigned int* counter, int final_step,
+    double u_scale) {
+    extern __shared__ __align__(128) uint8_t sraw[];
+    __shared__ uint64_t full[kStreamStages];
+    __shared__ float red[8][kStreamRB];
+    __shared__ float inv_sh[1];
+    __shared__ int timeout;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t row_bytes = (uint32_t)(ld * 2);
+    const int nvec = (int)(ld / 8);  // 8-column groups of a padded row
+    // rows of this CTA
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per;
+    int64_t r1 = r0 + per;
+    if (r1 > n) r1 = n;
+    const int nblk = r0 < r1 ? (int)((r1 - r0 + kStreamRB - 1) / kStreamRB) : 0;
+    if (tid == 0) {
+        for (int st = 0; st < kStreamStages; ++st) mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        timeout = 0;
+    }
+    load_inv_norms<float>(sc, 1, inv_sh);  // includes __syncthreads
+    const float inv = inv_sh[0];
+    auto issue = [&](int blk) {
+        const int st = blk % kStreamStages;
+        const int64_t rb = r0 + (int64_t)blk * kStreamRB;
+        const int nr = (int)((r1 - rb) < kStreamRB ? (r1 - rb) : kStreamRB);
+        mbar_expect_tx(&full[st], (uint32_t)nr * row_bytes);
+        for (int r = 0; r < nr; ++r)
+            bulk_load(sraw + ((size_t)st * kStreamRB + r) * row_bytes, R + (rb + r) * ld, row_bytes,
+                      &full[st]);
+    };
+    if (tid == 0)
+        for (int blk = 0; blk < nblk && blk < kStreamStages; ++blk) issue(blk);
+    // x of this thread's column groups, already divided by ||x||
+    float xr[NG][8];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int g = tid + 256 * i;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t k = (int64_t)g * 8 + e;
+            xr[i][e] = (g < nvec && k < n) ? x[k] * inv : 0.f;
+        }
+    }
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int st = blk % kStreamStages;
+        // bounded wait, then a block-wide vote so that every thread leaves the
+        // loop together (no thread may skip the barriers below)
+        const bool got = mbar_wait(&full[st], (uint32_t)(blk / kStreamStages) & 1u, &timeout);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) {
+                timeout = 1;
+                // let the copies already issued land before the block exits
+                volatile int never = 0;
+                const int last = blk + kStreamStages < nblk ? blk + kStreamStages : nblk;
+                for (int b2 = blk; b2 < last; ++b2)
+                    mbar_wait(&full[b2 % kStreamStages], (uint32_t)(b2 / kStreamStages) & 1u, &never);
+            }
+            break;
+        }
+        const int64_t rb = r0 + (int64_t)blk * kStreamRB;
+        float part[kStreamRB];
+#pragma unroll
+        for (int r = 0; r < kStreamRB; ++r) {
+            const uint4* row = reinterpret_cast<const uint4*>(sraw + ((size_t)st * kStreamRB + r) * row_bytes);
+            float a = 0.f;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const int g = tid + 256 * i;
+                if (g < nvec) {
+                    const uint4 raw = row[g];
+                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+                    const float2 f0 = __bfloat1622float2(h2[0]), f1 = __bfloat1622float2(h2[1]);
+                    const float2 f2 = __bfloat1622float2(h2[2]), f3 = __bfloat1622float2(h2[3]);
+                    a = fmaf(f0.x, xr[i][0], a); a = fmaf(f0.y, xr[i][1], a);
+                    a = fmaf(f1.x, xr[i][2], a); a = fmaf(f1.y, xr[i][3], a);
+                    a = fmaf(f2.x, xr[i][4], a); a = fmaf(f2.y, xr[i][5], a);
+                    a = fmaf(f3.x, xr[i][6], a); a = fmaf(f3.y, xr[i][7], a);
+                }
+            }
+            part[r] = warp_sum(a);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int r = 0; r < kStreamRB; ++r) red[w][r] = part[r];
+        __syncthreads();  // stage st fully read; partials visible
+        if (tid == 0 && blk + kStreamStages < nblk) issue(blk + kStreamStages);
+        if (tid < kStreamRB && rb + tid < r1) {
+            float yv = 0.f;
+            for (int ww = 0; ww < 8; ++ww) yv += red[ww][tid];
+            const int64_t i = rb + tid;
+            y[i] = yv;
+            acc[0] += yv * yv;
+            if (final_step) {
+                const float xh = x[i] * inv;
+                acc[1] += xh * yv;
+                acc[2] += xh * xh;
+            }
+        }
+        __syncthreads();  // red reused by the next block
+    }
+    if (tid == 0 && timeout) {
+        unsigned long long* f = (unsigned long long*)&sc[SC_FLAGS];
+        atomicOr(f, (unsigned long long)FLAG_TIMEOUT);
+    }
+    power_finish<float>(acc, 1, partial, counter, sc, final_step, u_scale);
+}
+
 cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_t ld,
                                     const void* x, void* y, int xdouble, int q, double* sc,
                                     double* partial, unsigned int* counter, int final_step,
@@ -279,6 +402,39 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
             final_step, u_scale);
     } else {
         if (xdouble || (ld % 8) != 0) return cudaErrorInvalidValue;
+        const int nvec = (int)(ld / 8);
+        if (q == 1 && nvec <= 256 * 8 && (ld * 2) % 16 == 0) {
+            // streamed: one persistent CTA per SM
+            static int sms = 0;
+            if (!sms) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            }
+            int g = sms;
+            if (g > blocks) g = blocks;
+            if (g < 1) g = 1;
+            const size_t smem = (size_t)kStreamStages * kStreamRB * (size_t)ld * 2;
+            const int ng = (nvec + 255) / 256;
+            cudaError_t e = cudaSuccess;
+#define VNE_STREAM(NGV)                                                                        \
+    do {                                                                                       \
+        auto kern = k_power_dense_bf16_stream<NGV>;                                            \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess)                                                                  \
+            kern<<<g, 256, smem, st>>>((const __nv_bfloat16*)R, n, ld, (const float*)x,      \
+                                       (float*)y, sc, partial, counter, final_step, u_scale); \
+    } while (0)
+            if (smem <= 200 * 1024) {
+                if (ng <= 1) VNE_STREAM(1);
+                else if (ng <= 2) VNE_STREAM(2);
+                else if (ng <= 4) VNE_STREAM(4);
+                else VNE_STREAM(8);
+#undef VNE_STREAM
+                if (e != cudaSuccess) return e;
+                return cudaGetLastError();
+            }
+        }
         if (q == 1) {
             // one wave of resident blocks (grid-stride over rows): a partial
             // second wave would leave most of the memory system idle

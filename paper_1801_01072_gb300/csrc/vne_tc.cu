@@ -30,66 +30,17 @@
 
 #include "vne_common.cuh"
 #include "vne_internal.h"
+#include "vne_ptx.cuh"
 
 namespace vne {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
 constexpr int TC_THREADS = 256;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 int tc_tile_m() { return TC_BM; }
 int tc_tile_k() { return TC_BK; }
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait; false on timeout or when another role already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0u) {
-            if (*abort_flag) return false;
-            if (globaltimer() - t0 > kWaitNs) return false;
-        }
-    }
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                            int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
 // Tiled 2-D TMA load with an L2 cache-policy hint; with mask != 0 the tile is
 // multicast to every CTA of the cluster in `mask` (same smem offset and the
 // same mbarrier offset in each destination CTA).
@@ -233,6 +184,9 @@ struct TcArgs {
     int BN, stages, nkb, x3;
     int CM, CN;  // cluster shape: CM CTAs along M share B tiles, CN along N share A tiles
     int ksplit;  // 2: a CTA pair (cluster along z) splits K and swaps half accumulators
+    int epi_tma;       // 1: Y_{t-1}, Y_{t-2} of the CTA's own chunks arrive by TMA into smem
+    uint32_t ops_off;  // byte offset of that operand area in the 1024-aligned smem
+    uint32_t body;     // bytes before the barrier tail: max(operand ring, operand area end)
     uint32_t tmem_cols;
     StepCols cols;
     const double* sc;
@@ -243,6 +197,7 @@ struct TcArgs {
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_step(const __grid_constant__ CUtensorMap mapRhi, const __grid_constant__ CUtensorMap mapRlo,
               const __grid_constant__ CUtensorMap mapYhi, const __grid_constant__ CUtensorMap mapYlo,
+              const __grid_constant__ CUtensorMap mapYp, const __grid_constant__ CUtensorMap mapYp2,
               const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned carve-out: [stages][A_hi | B_hi | (A_lo | B_lo)] then barriers
@@ -251,11 +206,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t bytesA = TC_BM * TC_BK * 2;
     const uint32_t bytesB = (uint32_t)a.BN * TC_BK * 2;
     const uint32_t stage_bytes = (bytesA + bytesB) * (a.x3 ? 2u : 1u);
-    uint8_t* tail = smem + (size_t)a.stages * stage_bytes;
+    uint8_t* tail = smem + a.body;  // barriers etc. after both the ring and the operand area
     uint64_t* full_bar = reinterpret_cast<uint64_t*>(tail);
     uint64_t* empty_bar = full_bar + a.stages;
     uint64_t* accum_bar = empty_bar + a.stages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum_bar + 1);
+    uint64_t* epi_bar = accum_bar + 1;  // epilogue operands landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epi_bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][BN]
 
@@ -296,6 +252,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&empty_bar[s2], (uint32_t)csize);
         }
         mbar_init(accum_bar, 1);
+        mbar_init(epi_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapRhi)) : "memory");
@@ -312,6 +269,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (in_cluster) cluster_sync_all();  // peers' barriers are initialised before any multicast
     tc_fence_after();
+    // Launched as a programmatic dependent of the previous step: everything
+    // above (barriers, TMEM, tensor-map prefetch) overlapped that step's tail;
+    // from here on this step reads what the previous one wrote.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t tmem_base = *tmem_slot;
     if (!rank_ok && threadIdx.x == 0) *abort_flag = 1;
 
@@ -433,6 +394,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     const int ck_first = ck_lo + chalf;
 
+    // the next step may start its prologue on free SMs now
+    if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // ---------------- epilogue (all warps) ----------------
     bool have_acc = mbar_wait(accum_bar, 0u, abort_flag);
     if (!have_acc) {
@@ -443,6 +406,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool aborted = (*abort_flag != 0) || !have_acc;
     tc_fence_after();
     __syncwarp();
+
+    // Y_{t-1} and Y_{t-2} of this CTA's own chunks, [chunk][2][32 cols][128 rows]
+    // FP32 in smem, by TMA: the operand ring is idle now, and the copies overlap
+    // the accumulator exchange below.
+    float* ops = reinterpret_cast<float*>(smem + a.ops_off);
+    const int nown = ck_hi - ck_lo;
+    if (a.epi_tma && !aborted && threadIdx.x == 0) {
+        mbar_expect_tx(epi_bar, (uint32_t)nown * 2u * 32u * TC_BM * 4u);
+        for (int oc = 0; oc < nown; ++oc) {
+            const int c0 = n0 + (ck_lo + oc) * 32;
+            tma_load_2d(ops + (size_t)(oc * 2 + 0) * 32 * TC_BM, &mapYp, epi_bar, m0, c0);
+            tma_load_2d(ops + (size_t)(oc * 2 + 1) * 32 * TC_BM, &mapYp2, epi_bar, m0, c0);
+        }
+    }
 
     const float* recv = reinterpret_cast<const float*>(smem);
     if (a.ksplit > 1) {
@@ -463,13 +440,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         cluster_sync_all();  // the peer's half has landed here
     }
+    const bool ops_ready = a.epi_tma && !aborted && mbar_wait(epi_bar, 0u, abort_flag);
     if (!aborted) {
         for (int ck = ck_first; ck < ck_hi; ck += 2) {
             uint32_t r[32];
             const uint32_t taddr = tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32);
             TMEM_LD32(taddr, r);
             const int cbase = n0 + ck * 32;
-            prefetch(ck);
+            if (ops_ready) {
+                const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int c = cbase + q;
+                    gv[q] = (c < a.col_end && row_ok) ? __ldg(a.G + (int64_t)(c % a.s) * a.n + row)
+                                                      : 0.f;
+                    yp[q] = ob[q * TC_BM];
+                    yp2[q] = ob[32 * TC_BM + q * TC_BM];
+                }
+            } else {
+                prefetch(ck);
+            }
             tmem_wait_ld();
             if (a.ksplit > 1) {
                 const float4* rp = reinterpret_cast<const float4*>(
@@ -564,35 +554,38 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows,
-                     int64_t row_stride_elems, int box_inner, int box_rows) {
+                     int64_t row_stride_elems, int box_inner, int box_rows, bool fp32 = false) {
     // small cache: consecutive steps reuse the same few operand buffers
     struct Entry {
         const void* base;
         int64_t inner, rows, stride;
         int bi, br;
+        bool fp32;
         CUtensorMap map;
     };
     static Entry cache[16];
     static int next = 0;
     for (const Entry& e : cache)
         if (e.base == base && e.inner == inner && e.rows == rows && e.stride == row_stride_elems &&
-            e.bi == box_inner && e.br == box_rows) {
+            e.bi == box_inner && e.br == box_rows && e.fp32 == fp32) {
             *map = e.map;
             return true;
         }
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * (fp32 ? 4 : 2)};
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
-                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    CUresult r = enc(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     2, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
     Entry& e = cache[next];
     next = (next + 1) % 16;
-    e = Entry{base, inner, rows, row_stride_elems, box_inner, box_rows, *map};
+    e = Entry{base, inner, rows, row_stride_elems, box_inner, box_rows, fp32, *map};
     return true;
 }
 
@@ -670,12 +663,21 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
         mYlo = mYhi;
     }
     const uint32_t stage_bytes = (uint32_t)(TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (x3 ? 2u : 1u);
-    const size_t tail = 2 * 8 * 16 + 8 + 16 + 4 * 256 * 4;  // barriers, slot, flag, red
+    const size_t tail = 2 * 8 * 16 + 16 + 16 + 4 * 256 * 4;  // barriers, slot, flag, red
     const size_t max_smem = 227 * 1024;
     int stages = (int)((max_smem - 1024 - tail) / stage_bytes);
     if (stages > 8) stages = 8;
     if (stages < 2) return cudaErrorInvalidValue;
-    const size_t smem = 1024 + (size_t)stages * stage_bytes + tail;
+    // epilogue operand area (after the split-K receive buffer, if any)
+    const int nch = BN / 32;
+    const int nown = sh.ksplit > 1 ? nch / 2 : nch;
+    const size_t recv_bytes = sh.ksplit > 1 ? (size_t)TC_BM * (nch / 2 * 32 + 4) * 4 : 0;
+    const size_t ops_off = (recv_bytes + 1023) / 1024 * 1024;
+    const size_t ops_end = ops_off + (size_t)nown * 2 * 32 * TC_BM * 4;
+    size_t body = (size_t)stages * stage_bytes;
+    bool epi_tma = (s.n % 4 == 0) && (1024 + ops_end + tail <= max_smem);
+    if (epi_tma && ops_end > body) body = ops_end;
+    const size_t smem = 1024 + body + tail;
 
     TcArgs a{};
     a.G = s.G;
@@ -697,13 +699,25 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.CM = sh.CM;
     a.CN = sh.CN;
     a.ksplit = sh.ksplit;
+    CUtensorMap mYp, mYp2;
+    if (epi_tma) {
+        epi_tma = make_map(&mYp, s.Yprev, s.n, s.S, s.n, TC_BM, 32, true) &&
+                  make_map(&mYp2, s.Yprev2, s.n, s.S, s.n, TC_BM, 32, true);
+    }
+    if (!epi_tma) {
+        mYp = mRhi;
+        mYp2 = mRhi;
+    }
+    a.epi_tma = epi_tma ? 1 : 0;
+    a.ops_off = (uint32_t)ops_off;
+    a.body = (uint32_t)body;
     a.tmem_cols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
     a.cols = s.cols;
     a.sc = s.sc;
     a.P = s.P;
     a.t = s.t;
 
-    static size_t smem_set = 0;
+    static size_t smem_set = 0;  // raised as needed, never lowered
     if (smem > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -715,14 +729,16 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)sh.CM;
     attr[0].val.clusterDim.y = (unsigned)sh.CN;
     attr[0].val.clusterDim.z = (unsigned)sh.ksplit;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc_step, mRhi, mRlo, mYhi, mYlo, a);
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k_tc_step, mRhi, mRlo, mYhi, mYlo, mYp, mYp2, a);
 }
 
 }  // namespace vne
