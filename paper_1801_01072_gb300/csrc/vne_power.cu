@@ -263,12 +263,28 @@ __global__ void __launch_bounds__(256) k_power_dense_bf16_q1(
 
 // bf16 rows, one trial, streamed.  A persistent CTA owns a contiguous range of
 // rows and streams them through shared memory with 1-D bulk copies (a ring of
-// ST stages of RB rows, one mbarrier each), so the HBM stream needs a handful
-// of instructions per 16 KB row.  Each thread keeps the x values of its NG
-// column groups (8 columns each) in registers for the whole launch; a row's
-// dot product is a per-thread partial plus one block reduction per RB rows.
-constexpr int kStreamRB = 4;      // rows per stage
-constexpr int kStreamStages = 3;  // ring depth
+// kStreamStages stages of kStreamRB rows, one mbarrier each), so the HBM
+// stream costs a handful of instructions per 16 KB row.  The CTA's two halves
+// (128 threads each) consume alternate stages, so one half's reduction and
+// barrier overlap the other half's arithmetic.  Each thread keeps the x values
+// of its NG column groups (8 columns each) in registers for the whole launch.
+constexpr int kStreamRB = 3;      // rows per stage
+constexpr int kStreamStages = 4;  // ring depth
+
+// all `nthreads` threads of named barrier `id` arrive; true iff v held for all
+__device__ __forceinline__ bool group_all(bool v, int id, int nthreads) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 template <int NG>
 __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
@@ -277,10 +293,11 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
     double u_scale) {
     extern __shared__ __align__(128) uint8_t sraw[];
     __shared__ uint64_t full[kStreamStages];
-    __shared__ float red[8][kStreamRB];
+    __shared__ float red[2][4][kStreamRB];
     __shared__ float inv_sh[1];
     __shared__ int timeout;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int grp = tid >> 7, gt = tid & 127, gw = gt >> 5;  // half, thread and warp in half
     const uint32_t row_bytes = (uint32_t)(ld * 2);
     const int nvec = (int)(ld / 8);  // 8-column groups of a padded row
     // rows of this CTA
@@ -307,11 +324,11 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
     };
     if (tid == 0)
         for (int blk = 0; blk < nblk && blk < kStreamStages; ++blk) issue(blk);
-    // x of this thread's column groups, already divided by ||x||
+    // x of this thread's column groups (g = gt + 128 i), already divided by ||x||
     float xr[NG][8];
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
-        const int g = tid + 256 * i;
+        const int g = gt + 128 * i;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int64_t k = (int64_t)g * 8 + e;
@@ -319,20 +336,14 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
         }
     }
     float acc[3] = {0.f, 0.f, 0.f};
-    for (int blk = 0; blk < nblk; ++blk) {
+    const int bar_id = 1 + grp;
+    for (int blk = grp; blk < nblk; blk += 2) {
         const int st = blk % kStreamStages;
-        // bounded wait, then a block-wide vote so that every thread leaves the
-        // loop together (no thread may skip the barriers below)
+        // bounded wait, then a vote across this half so that all its threads
+        // leave the loop together
         const bool got = mbar_wait(&full[st], (uint32_t)(blk / kStreamStages) & 1u, &timeout);
-        if (!__syncthreads_and(got)) {
-            if (tid == 0) {
-                timeout = 1;
-                // let the copies already issued land before the block exits
-                volatile int never = 0;
-                const int last = blk + kStreamStages < nblk ? blk + kStreamStages : nblk;
-                for (int b2 = blk; b2 < last; ++b2)
-                    mbar_wait(&full[b2 % kStreamStages], (uint32_t)(b2 / kStreamStages) & 1u, &never);
-            }
+        if (!group_all(got, bar_id, 128)) {
+            if (gt == 0) timeout = 1;
             break;
         }
         const int64_t rb = r0 + (int64_t)blk * kStreamRB;
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
             float a = 0.f;
 #pragma unroll
             for (int i = 0; i < NG; ++i) {
-                const int g = tid + 256 * i;
+                const int g = gt + 128 * i;
                 if (g < nvec) {
                     const uint4 raw = row[g];
                     const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
@@ -359,13 +370,12 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
         }
         if (lane == 0)
 #pragma unroll
-            for (int r = 0; r < kStreamRB; ++r) red[w][r] = part[r];
-        __syncthreads();  // stage st fully read; partials visible
-        if (tid == 0 && blk + kStreamStages < nblk) issue(blk + kStreamStages);
-        if (tid < kStreamRB && rb + tid < r1) {
-            float yv = 0.f;
-            for (int ww = 0; ww < 8; ++ww) yv += red[ww][tid];
-            const int64_t i = rb + tid;
+            for (int r = 0; r < kStreamRB; ++r) red[grp][gw][r] = part[r];
+        group_sync(bar_id, 128);  // stage st fully read by this half; partials visible
+        if (gt == 0 && blk + kStreamStages < nblk) issue(blk + kStreamStages);
+        if (gt < kStreamRB && rb + gt < r1) {
+            const float yv = red[grp][0][gt] + red[grp][1][gt] + red[grp][2][gt] + red[grp][3][gt];
+            const int64_t i = rb + gt;
             y[i] = yv;
             acc[0] += yv * yv;
             if (final_step) {
@@ -374,9 +384,16 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
                 acc[2] += xh * xh;
             }
         }
-        __syncthreads();  // red reused by the next block
+        group_sync(bar_id, 128);  // red[grp] reused by this half's next block
     }
+    __syncthreads();
     if (tid == 0 && timeout) {
+        // let every copy already issued land before the block exits
+        volatile int never = 0;
+        for (int b2 = 0; b2 < nblk && b2 < kStreamStages; ++b2) {
+            const int last = ((nblk - 1 - b2) / kStreamStages) * kStreamStages + b2;
+            mbar_wait(&full[b2], (uint32_t)(last / kStreamStages) & 1u, &never);
+        }
         unsigned long long* f = (unsigned long long*)&sc[SC_FLAGS];
         atomicOr(f, (unsigned long long)FLAG_TIMEOUT);
     }
@@ -403,7 +420,7 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
     } else {
         if (xdouble || (ld % 8) != 0) return cudaErrorInvalidValue;
         const int nvec = (int)(ld / 8);
-        if (q == 1 && nvec <= 256 * 8 && (ld * 2) % 16 == 0) {
+        if (q == 1 && nvec <= 128 * 8 && (ld * 2) % 16 == 0) {
             // streamed: one persistent CTA per SM
             static int sms = 0;
             if (!sms) {
@@ -415,7 +432,7 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
             if (g > blocks) g = blocks;
             if (g < 1) g = 1;
             const size_t smem = (size_t)kStreamStages * kStreamRB * (size_t)ld * 2;
-            const int ng = (nvec + 255) / 256;
+            const int ng = (nvec + 127) / 128;
             cudaError_t e = cudaSuccess;
 #define VNE_STREAM(NGV)                                                                        \
     do {                                                                                       \

@@ -449,11 +449,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int cbase = n0 + ck * 32;
             if (ops_ready) {
                 const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
+                // probe index of the chunk's first column; the 32 columns map to
+                // consecutive probes unless the chunk wraps past s
+                const int j0 = cbase % a.s;
+                const bool nowrap = j0 + 32 <= a.s;
+                const float* gcol = a.G + (int64_t)j0 * a.n + row;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int c = cbase + q;
-                    gv[q] = (c < a.col_end && row_ok) ? __ldg(a.G + (int64_t)(c % a.s) * a.n + row)
-                                                      : 0.f;
+                    gv[q] = 0.f;
+                    if (c < a.col_end && row_ok)
+                        gv[q] = nowrap ? __ldg(gcol + (int64_t)q * a.n)
+                                       : __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
                     yp[q] = ob[q * TC_BM];
                     yp2[q] = ob[32 * TC_BM + q * TC_BM];
                 }
