@@ -249,6 +249,7 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     kind = 0 if (dense and prec in ("bf16", "bf16x3")) else (1 if dense else 2)
     k_ms, k_n = h.profile_read(kind)
+    p_ms, p_n = h.profile_read(3)  # power-method products
     h.profile(False)
     t = torch.tensor([ms], device=dev)
     if world > 1:
@@ -366,6 +367,8 @@ def run_gpu(args):
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
                 "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": 200 * 8},
         "gpu_launches": int(n_launch),
+        "phases_ms_per_step": {"recurrence": k_ms / args.steps, "power_method": p_ms / args.steps,
+                               "other": ms_max / args.steps - (k_ms + p_ms) / args.steps},
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clocks,
