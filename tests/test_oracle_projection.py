@@ -1,0 +1,73 @@
+"""Pins of the oracle's random-projection estimator (Algorithm alg:EN), CPU."""
+import numpy as np
+import pytest
+from scipy import linalg
+
+import oracle.projection as P
+import synth
+from oracle import rng
+
+
+@pytest.mark.parametrize("n", [1, 2, 16, 64])
+def test_hadamard_matches_library_and_is_orthogonal(n):
+    H = P.hadamard(n)
+    np.testing.assert_array_equal(H, linalg.hadamard(n) / np.sqrt(n))
+    np.testing.assert_allclose(H.T @ H, np.eye(n), atol=1e-14)
+
+
+def test_sketch_structure():
+    n, s, seed = 64, 24, 9
+    cs = P.sketch(n, s, "countsketch", seed)
+    assert np.all((cs != 0).sum(axis=1) == 1)                 # one +-1 per row
+    assert set(np.unique(cs[cs != 0])) <= {-1.0, 1.0}
+    sr = P.sketch(n, s, "srht", seed)
+    # every column is sqrt(n/s) * D h_i: norm sqrt(n/s), entries +-1/sqrt(s)
+    np.testing.assert_allclose(np.linalg.norm(sr, axis=0), np.sqrt(n / s), rtol=1e-13)
+    np.testing.assert_allclose(np.abs(sr), 1.0 / np.sqrt(s), rtol=1e-13)
+    g = P.sketch(n, s, "gaussian", seed)
+    np.testing.assert_allclose(g, rng.gaussian(n, s, seed) / np.sqrt(s))
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "countsketch"])
+def test_sketch_isotropic_on_average(kind):
+    n, s = 32, 64
+    acc = np.zeros((n, n))
+    T = 300
+    for seed in range(T):
+        Pi = P.sketch(n, s, kind, 1000 + seed)
+        acc += Pi @ Pi.T
+    acc /= T
+    # E[Pi Pi^T] = I (CountSketch: s/s rows hit -> also I on the diagonal)
+    np.testing.assert_allclose(np.diag(acc), 1.0, atol=0.15)
+    off = acc - np.diag(np.diag(acc))
+    assert np.abs(off).max() < 0.2
+
+
+def test_orthogonal_sketch_recovers_spectrum_exactly():
+    # with an orthogonal n x n "sketch" the singular values of R Pi are the
+    # eigenvalues of R, so the estimate is the exact entropy of the top k
+    n, k = 40, 7
+    psi = synth.haar_orthogonal(n, 3)[:, :k]
+    p = synth.spectrum_exponential(k, 2.0)
+    R = (psi * p) @ psi.T
+    Q = synth.haar_orthogonal(n, 5)
+    sv = np.linalg.svd(R @ Q, compute_uv=False)[:k]
+    np.testing.assert_allclose(np.sort(sv)[::-1], np.sort(p)[::-1], rtol=1e-12)
+    H = float((p * np.log(1 / p)).sum())
+    pos = sv[sv > 0]
+    assert abs(float((pos * np.log(1 / pos)).sum()) - H) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "srht", "countsketch"])
+def test_low_rank_estimate_is_close(kind):
+    # rank-10 density matrix, s = 256: the paper reports ~0.3 % errors
+    n, k, s = 256, 10, 256
+    psi = synth.haar_orthogonal(n, 11)[:, :k]
+    p = synth.spectrum_exponential(k, 3.0)
+    R = (psi * p) @ psi.T
+    out = P.estimate_projection(R, k, s, kind, seed=4)
+    H = float((p * np.log(1 / p)).sum())
+    assert abs(out["H"] - H) / H < 0.1
+    # Theorem thm:rp: |p_i^2 - p~_i^2| <= eps p_i^2 with a moderate eps here
+    rel = np.abs(out["p"] ** 2 - p ** 2) / p ** 2
+    assert rel.max() < 0.6
