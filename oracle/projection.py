@@ -8,10 +8,13 @@ H~ = sum_i p~_i ln(1/p~_i).  The random projection Pi is one of
 * Gaussian: i.i.d. N(0, 1) entries (the experiments of Section 6), scaled
   by 1/sqrt(s) so that E[Pi Pi^T] = I (reading: the scaling is unstated);
 * subsampled randomized Hadamard transform (Algorithm alg:SHD):
-  Pi = D H S with D = diag(+-1), H the normalised n x n Hadamard matrix
-  (n a power of two) and S = s columns e_i drawn uniformly with replacement,
-  scaled by sqrt(n/s) so that E[Pi Pi^T] = I (reading: Lemma lem:rp1 prints
-  n/k where the usual normalisation is n/s);
+  Pi = D H S with D = diag(+-1), H the normalised N x N Hadamard matrix and
+  S = s columns e_i drawn uniformly with replacement, scaled by sqrt(N/s) so
+  that E[Pi Pi^T] = I (reading: Lemma lem:rp1 prints n/k where the usual
+  normalisation is n/s).  H exists for N a power of two; for other n the
+  matrix is read as R zero-padded to N = the next power of two, whose
+  non-zero spectrum is that of R, so Pi is the first n rows of the N x s
+  transform (reading: the paper assumes n a power of two);
 * input-sparsity transform (Algorithm alg:IS): Pi = D S with each row of S a
   canonical row vector e_{h(j)}^T, h(j) uniform in {1..s}, unscaled.
 
@@ -56,12 +59,13 @@ def sketch(n: int, s: int, kind: str, seed: int) -> np.ndarray:
     if kind == "gaussian":
         return rng.gaussian(n, s, seed) / np.sqrt(s)
     if kind == "srht":
-        D = signs(seed, n)
-        idx = uniform_index(seed, s, n)
-        H = hadamard(n)
-        S = np.zeros((n, s))
+        N = 1 << max(0, (n - 1).bit_length())
+        D = signs(seed, N)
+        idx = uniform_index(seed, s, N)
+        H = hadamard(N)
+        S = np.zeros((N, s))
         S[idx, np.arange(s)] = 1.0
-        return np.sqrt(n / s) * (D[:, None] * (H @ S))
+        return (np.sqrt(N / s) * (D[:, None] * (H @ S)))[:n]
     if kind == "countsketch":
         D = signs(seed, n)
         h = uniform_index(seed, n, s)

@@ -30,6 +30,8 @@ __all__ = [
     "dense_density",
     "dense_exp",
     "dense_powerlaw",
+    "orthonormal_columns",
+    "dense_lowrank",
     "band_diag_dominant",
     "band_poisson",
     "dia_to_dense",
@@ -94,6 +96,22 @@ def dense_powerlaw(n: int = 8192, k: int = 2048, alpha: float = 1.5,
     return dense_density(psi, p), p, psi
 
 
+def orthonormal_columns(n: int, k: int, seed: int) -> np.ndarray:
+    """n x k with orthonormal columns: Q of the QR factorisation of a seeded
+    n x k N(0,1) matrix, sign-fixed (the first k columns of a Haar matrix)."""
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.standard_normal((n, k)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def dense_lowrank(n: int = 8192, k: int = 64, tau: float = 16.0, seed: int = 4):
+    """Density matrix of rank k (a mixture of k pure states, the setting of
+    Algorithm alg:EN) with p_i ~ exp(-i/tau); returns (R, p, Psi)."""
+    psi = orthonormal_columns(n, k, seed)
+    p = spectrum_exponential(k, tau)
+    return dense_density(psi, p), p, psi
+
+
 def band_diag_dominant(n: int, half_bw: int = 16, offdiag_scale: float = 0.02,
                        seed: int = 3, dtype=np.float32) -> np.ndarray:
     """Symmetric banded density matrix in DIA storage, shape (half_bw+1, n).
@@ -149,6 +167,9 @@ WORKLOADS = {
                                  probe="gaussian", power_iters=30),
     "band33_n1e7": dict(kind="band", n=10_000_000, half_bw=16, offdiag_scale=0.02,
                         seed=3, m=30, s=64, probe="rademacher", power_iters=30),
+    # rank-64 mixture for the random-projection estimator (Algorithm alg:EN)
+    "lowrank_n8192_k64": dict(kind="lowrank", n=8192, k=64, tau=16.0, seed=4, s=256,
+                              sketch="gaussian"),
     # the same band at n = 2e6 (profiling captures of the banded kernels)
     "band33_n2e6": dict(kind="band", n=2_000_000, half_bw=16, offdiag_scale=0.02,
                         seed=3, m=30, s=64, probe="rademacher", power_iters=30),

@@ -71,3 +71,30 @@ def test_low_rank_estimate_is_close(kind):
     # Theorem thm:rp: |p_i^2 - p~_i^2| <= eps p_i^2 with a moderate eps here
     rel = np.abs(out["p"] ** 2 - p ** 2) / p ** 2
     assert rel.max() < 0.6
+
+
+def test_srht_padding_equals_zero_padded_matrix():
+    # n = 48 is read as R zero-padded to N = 64: R Pi equals the top n rows of
+    # [R 0; 0 0] Pi_N, so the singular values agree
+    n, N, k, s = 48, 64, 5, 32
+    psi = synth.orthonormal_columns(n, k, 21)
+    p = synth.spectrum_exponential(k, 2.0)
+    R = synth.dense_density(psi, p)
+    Rp = np.zeros((N, N))
+    Rp[:n, :n] = R
+    a = P.estimate_projection(R, k, s, "srht", seed=6)
+    b = P.estimate_projection(Rp, k, s, "srht", seed=6)
+    np.testing.assert_allclose(a["p"], b["p"], rtol=1e-12)
+    assert abs(a["H"] - b["H"]) < 1e-12
+
+
+def test_rank_deficient_tail_is_negligible():
+    # rank 3 < k = 6: the trailing singular values are round-off
+    n, s = 64, 16
+    psi = synth.orthonormal_columns(n, 3, 2)
+    p = np.array([0.5, 0.3, 0.2])
+    R = synth.dense_density(psi, p)
+    out = P.estimate_projection(R, 6, s, "gaussian", seed=3)
+    assert np.all(out["p"][3:] < 1e-14)
+    H = float((p * np.log(1 / p)).sum())
+    assert abs(out["H"] - H) / H < 0.5
