@@ -193,6 +193,41 @@ vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* 
 vne_status vne_lambda_max_static(const vne_matrix* R, const vne_params* p, double* lam_out,
                                  void* stream);
 
+/* vne_entropy_projection.sketch: the random projection Pi of Algorithm alg:EN */
+enum { VNE_SKETCH_GAUSSIAN = 0, VNE_SKETCH_SRHT = 1, VNE_SKETCH_COUNT = 2 };
+
+/* Algorithm alg:EN (Section 5): for R of rank at most k, the k largest
+ * singular values p~_i of R~ = R Pi (Pi n x s) and H~ = sum_i p~_i ln(1/p~_i).
+ *   k            : 1 <= k <= s.
+ *   s            : sketch width, 1 <= s <= 512.
+ *   sketch       : VNE_SKETCH_GAUSSIAN -- i.i.d. N(0,1)/sqrt(s) entries, entry
+ *                  (i, c) from counter c*n + i as for the Gaussian probes;
+ *                  VNE_SKETCH_SRHT -- Algorithm alg:SHD scaled by sqrt(N/s):
+ *                  Pi[i, c] = D_i (-1)^popcount(i & t_c) / sqrt(s) with N the
+ *                  next power of two >= n (R read as zero-padded to N), D_i the
+ *                  top bit of SplitMix64 output i of seed ^ 0xA0761D6478BD642F,
+ *                  t_c = floor(u N), u = (output c of seed ^ 0xE7037ED1A0B428DB
+ *                  >> 11) / 2^53;
+ *                  VNE_SKETCH_COUNT -- Algorithm alg:IS: Pi[i, h(i)] = D_i with
+ *                  h(i) = floor(u s), u from output i of the same index stream.
+ *   krylov_iters : 0 (Algorithm alg:EN as printed); other values return
+ *                  VNE_ERR_UNSUPPORTED.
+ *   precision    : VNE_PREC_F64 or VNE_PREC_F32: arithmetic of Pi and of the
+ *                  product R Pi.  The Gram matrix R~^T R~, its eigenvalues
+ *                  (Householder tridiagonalisation + bisection) and H~ are FP64.
+ *   R            : VNE_DENSE only.
+ *   H_out        : host, 1 double.   p_out : host, k doubles (descending), or NULL.
+ * Singular values come from the eigenvalues of R~^T R~: the top-k values have
+ * full relative accuracy; those below ~1e-8 p~_1 only absolute accuracy. */
+vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k, int32_t s,
+                                  int32_t sketch, int32_t krylov_iters, int32_t precision,
+                                  uint64_t seed, double* H_out, double* p_out, void* stream);
+
+/* The random projection of vne_entropy_projection: out[c*n + i] = Pi[i, c]
+ * (FP64, device, n*s doubles, caller-owned). */
+vne_status vne_sketch_block(vne_handle* h, int64_t n, int32_t s, int32_t sketch, uint64_t seed,
+                            double* out, void* stream);
+
 /* The probe block the estimators draw: out[j*n + i] = g_j[i] (FP64, device,
  * n*s doubles, caller-owned).  Lets callers check the generator. */
 vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, uint64_t seed,

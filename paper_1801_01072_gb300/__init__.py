@@ -10,6 +10,7 @@ is no CPU fallback.
     res = vne.entropy_taylor(R, m=20, s=50, seed=1)             # Algorithm 1a
     both = vne.entropy_both(R, m=40, s=128, precision="bf16")   # shared passes
     lam = vne.lambda_max(R)                                     # Algorithm alg:power
+    pr = vne.entropy_projection(R, k=64, s=256, sketch="gaussian")  # Algorithm alg:EN
 
 ``R`` is a dense (n, n) tensor (row-major) or, with ``layout="dia"``, the
 (D, n) band storage ``vals[d, i] = R[i, i + d]`` of a symmetric banded R.
@@ -27,6 +28,7 @@ from . import _lib
 from ._lib import VneError
 
 __all__ = ["entropy_chebyshev", "entropy_taylor", "entropy_both", "lambda_max", "probe_block",
+           "entropy_projection", "sketch_block", "ProjectionResult",
            "Handle", "Result", "BothResult", "VneError", "suggest_m", "load"]
 
 
@@ -48,6 +50,15 @@ class BothResult:
     u: float
     moments_chebyshev: np.ndarray | None
     moments_taylor: np.ndarray | None
+
+
+@dataclass
+class ProjectionResult:
+    H: float
+    p: np.ndarray  # (k,) descending
+
+
+SKETCH = {"gaussian": 0, "srht": 1, "countsketch": 2}
 
 
 class Handle:
@@ -238,6 +249,35 @@ def probe_block(n: int, s: int, seed: int, probe: str = "rademacher", device: in
     st = h.lib.vne_probe_block(h.h, int(n), int(s), _lib.PROBE[probe], int(seed),
                                C.c_void_p(out.data_ptr()), _stream(device, None))
     h.check(st, "vne_probe_block")
+    return out.t()
+
+
+def entropy_projection(R, k: int, s: int, sketch: str = "gaussian", seed: int = 0,
+                       precision: str = "f64", krylov_iters: int = 0,
+                       stream=None) -> ProjectionResult:
+    """Algorithm alg:EN: the k largest singular values p~ of R Pi and sum p~ ln(1/p~)."""
+    mat, keep, dev = _matrix(R, "dense")
+    h = _handle(dev)
+    H = C.c_double()
+    p = np.zeros(int(k), dtype=np.float64)
+    st = h.lib.vne_entropy_projection(h.h, C.byref(mat), int(k), int(s), SKETCH[sketch],
+                                      int(krylov_iters), _lib.PREC[precision],
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(H), _dptr(p),
+                                      _stream(dev, stream))
+    h.check(st, "vne_entropy_projection")
+    del keep
+    return ProjectionResult(H.value, p)
+
+
+def sketch_block(n: int, s: int, seed: int, sketch: str = "gaussian", device: int = 0):
+    """The random projection Pi as a (n, s) float64 CUDA tensor."""
+    import torch
+
+    h = _handle(device)
+    out = torch.empty((s, n), dtype=torch.float64, device=f"cuda:{device}")
+    st = h.lib.vne_sketch_block(h.h, int(n), int(s), SKETCH[sketch], int(seed),
+                                C.c_void_p(out.data_ptr()), _stream(device, None))
+    h.check(st, "vne_sketch_block")
     return out.t()
 
 

@@ -60,6 +60,11 @@ SIGNATURES = [
     ("vne_lambda_max", C.c_int, [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, C.c_void_p]),
     ("vne_lambda_max_static", C.c_int,
      [C.POINTER(VneMatrix), C.POINTER(VneParams), _D, C.c_void_p]),
+    ("vne_entropy_projection", C.c_int,
+     [_H, C.POINTER(VneMatrix), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+      _D, _D, C.c_void_p]),
+    ("vne_sketch_block", C.c_int,
+     [_H, C.c_int64, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p]),
     ("vne_probe_block", C.c_int,
      [_H, C.c_int64, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p]),
     ("vne_profile_enable", C.c_int, [_H, C.c_int32]),

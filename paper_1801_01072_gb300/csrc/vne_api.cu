@@ -151,6 +151,18 @@ vne_status ensure_ws(vne_handle* h, size_t bytes) {
 
 size_t elt_size(int dtype) { return dtype == VNE_F64 ? 8 : 4; }
 
+// Adds the event pairs recorded during a finished call to the per-kind totals.
+void collect_profile(vne_handle* h) {
+    for (const ProfEvent& pe : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+            h->prof_ms[pe.kind] += ms;
+            h->prof_n[pe.kind] += pe.count;
+        }
+    }
+    h->pending.clear();
+}
+
 vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
     if (!R || !p) return VNE_ERR_INVALID_ARG;
     if (R->n < 1 || !R->data) return VNE_ERR_INVALID_ARG;
@@ -484,14 +496,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         cudaGetLastError();
         return map_err(h, c.err);
     }
-    for (const ProfEvent& pe : h->pending) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
-            h->prof_ms[pe.kind] += ms;
-            h->prof_n[pe.kind] += pe.count;
-        }
-    }
-    h->pending.clear();
+    collect_profile(h);
     const double* hs = h->host_sc;
     uint64_t flags;
     std::memcpy(&flags, &hs[SC_FLAGS], sizeof(flags));
@@ -503,6 +508,89 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     if (out.H_taylor) *out.H_taylor = hs[SC_H_TAYLOR];
     if (out.u) *out.u = hs[SC_U];
     if (out.lam) *out.lam = hs[SC_LAM];
+    return VNE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Random projection (Algorithm alg:EN): sketch -> R Pi -> Gram -> eigenvalues
+// -> top-k singular values and H~.
+// ---------------------------------------------------------------------------
+template <typename T>
+vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int kind,
+                          uint64_t seed, double* H_out, double* p_out, cudaStream_t st) {
+    Call c{h, st};
+    const int64_t n = R.n;
+    const int want = sizeof(T) == 8 ? VNE_F64 : VNE_F32;
+    const int splitk = dense_simt_splitk(n, s, h->sm_count);
+    const int chunks = gram_chunks(n, s, h->sm_count);
+    auto plan = [&](Bump& b, void** Rcopy, T** Rop, T** Pi, T** Zpart, T** Z, double** part,
+                    double** C, double** W, double** de, double** ev, double** out) {
+        *Rcopy = R.memory == VNE_MEM_HOST ? b.take<char>((size_t)n * R.ld * elt_size(R.dtype))
+                                          : nullptr;
+        *Rop = R.dtype != want ? b.take<T>((size_t)n * n) : nullptr;
+        *Pi = b.take<T>((size_t)n * s);
+        *Zpart = b.take<T>((size_t)splitk * s * n);
+        *Z = splitk > 1 ? b.take<T>((size_t)s * n) : *Zpart;
+        *part = b.take<double>((size_t)chunks * s * s);
+        *C = b.take<double>((size_t)s * s);
+        *W = b.take<double>((size_t)s * s);
+        *de = b.take<double>((size_t)2 * s);
+        *ev = b.take<double>((size_t)s);
+        *out = b.take<double>((size_t)k + 1);
+    };
+    void* Rcopy;
+    T *Rop, *Pi, *Zpart, *Z;
+    double *part, *C, *W, *de, *ev, *out;
+    {
+        Bump b0(nullptr);
+        plan(b0, &Rcopy, &Rop, &Pi, &Zpart, &Z, &part, &C, &W, &de, &ev, &out);
+        vne_status vs = ensure_ws(h, b0.off + 4096);
+        if (vs != VNE_OK) return vs;
+        Bump b1(h->ws);
+        plan(b1, &Rcopy, &Rop, &Pi, &Zpart, &Z, &part, &C, &W, &de, &ev, &out);
+    }
+    h->ev_used = 0;
+    h->pending.clear();
+    const void* Rdata = R.data;
+    if (R.memory == VNE_MEM_HOST) {
+        c.chk(cudaMemcpyAsync(Rcopy, R.data, (size_t)n * R.ld * elt_size(R.dtype),
+                              cudaMemcpyHostToDevice, st));
+        Rdata = Rcopy;
+    }
+    const T* Rk = (const T*)Rdata;
+    int64_t ldr = R.ld;
+    if (Rop) {
+        if (sizeof(T) == 8)
+            c.launched(launch_dense_convert_f64(Rdata, R.dtype, n, R.ld, (double*)Rop, st));
+        else
+            c.launched(launch_dense_convert_f32(Rdata, R.dtype, n, R.ld, (float*)Rop, st));
+        Rk = Rop;
+        ldr = n;
+    }
+    if (c.ok()) c.launched(launch_sketch<T>(Pi, n, s, kind, seed, h->sm_count, st));
+    if (c.ok()) {
+        c.prof_begin();
+        c.launched(launch_dense_simt_step<T>(Rk, ldr, n, Pi, Zpart, s, 0, s, splitk, st));
+        c.prof_end(1);
+    }
+    if (c.ok() && splitk > 1)
+        c.launched(launch_split_sum<T>(Zpart, splitk, (int64_t)s * n, Z, h->sm_count, st));
+    if (c.ok()) c.launched(launch_gram<T>(Z, n, s, chunks, part, C, st));
+    if (c.ok()) c.launched(launch_sym_eigvals(C, s, W, de, de + s, ev, st));
+    if (c.ok()) c.launched(launch_proj_combine(ev, k, out, st));
+    std::vector<double> host((size_t)k + 1);
+    if (c.ok())
+        c.chk(cudaMemcpyAsync(host.data(), out, (size_t)(k + 1) * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+    c.chk(cudaStreamSynchronize(st));
+    if (!c.ok()) {
+        cudaGetLastError();
+        return map_err(h, c.err);
+    }
+    collect_profile(h);
+    if (!std::isfinite(host[0])) return VNE_ERR_NONFINITE;
+    *H_out = host[0];
+    if (p_out) std::memcpy(p_out, host.data() + 1, (size_t)k * sizeof(double));
     return VNE_OK;
 }
 
@@ -589,6 +677,38 @@ vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* 
     Outputs o;
     o.lam = lam_out;
     return run(h, R, p, MODE_POWER, o, stream);
+}
+
+vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k, int32_t s,
+                                  int32_t sketch, int32_t krylov_iters, int32_t precision,
+                                  uint64_t seed, double* H_out, double* p_out, void* stream) {
+    if (!h || !R || !H_out || !R->data) return VNE_ERR_INVALID_ARG;
+    if (R->n < 1 || R->ld < R->n) return VNE_ERR_INVALID_ARG;
+    if (R->dtype != VNE_F64 && R->dtype != VNE_F32) return VNE_ERR_INVALID_ARG;
+    if (R->memory != VNE_MEM_DEVICE && R->memory != VNE_MEM_HOST) return VNE_ERR_INVALID_ARG;
+    if (R->layout != VNE_DENSE && R->layout != VNE_DIA) return VNE_ERR_INVALID_ARG;
+    if (s < 1 || k < 1 || k > s) return VNE_ERR_INVALID_ARG;
+    if (sketch < VNE_SKETCH_GAUSSIAN || sketch > VNE_SKETCH_COUNT) return VNE_ERR_INVALID_ARG;
+    if (precision < VNE_PREC_F64 || precision > VNE_PREC_BF16X3 || krylov_iters < 0)
+        return VNE_ERR_INVALID_ARG;
+    if (R->layout != VNE_DENSE || s > 512 || krylov_iters != 0 || precision > VNE_PREC_F32)
+        return VNE_ERR_UNSUPPORTED;
+    if ((int64_t)s * R->n > ((int64_t)1 << 40)) return VNE_ERR_UNSUPPORTED;
+    DeviceGuard guard(h->device);
+    if (precision == VNE_PREC_F64)
+        return run_projection<double>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
+    return run_projection<float>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
+}
+
+vne_status vne_sketch_block(vne_handle* h, int64_t n, int32_t s, int32_t sketch, uint64_t seed,
+                            double* out, void* stream) {
+    if (!h || !out || n < 1 || s < 1) return VNE_ERR_INVALID_ARG;
+    if (sketch < VNE_SKETCH_GAUSSIAN || sketch > VNE_SKETCH_COUNT) return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    cudaError_t e = launch_sketch<double>(out, n, s, sketch, seed, h->sm_count, (cudaStream_t)stream);
+    h->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return map_err(h, e);
 }
 
 vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, uint64_t seed,

@@ -122,6 +122,26 @@ cudaError_t launch_tc_step(const TcStep& a, int sm_count, cudaStream_t st);
 int tc_tile_m();
 int tc_tile_k();
 
+// ---- random projection (vne_proj.cu) ------------------------------------------------
+// Pi stored [s][n]; kind 0 Gaussian, 1 SRHT, 2 input-sparsity (vne.h VNE_SKETCH_*).
+template <typename T>
+cudaError_t launch_sketch(T* Pi, int64_t n, int s, int kind, uint64_t seed, int sm_count,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_split_sum(const T* Zpart, int splitk, int64_t len, T* Z, int sm_count,
+                             cudaStream_t st);
+int gram_chunks(int64_t n, int s, int sm_count);
+// C (s x s, FP64, exactly symmetric) = Z^T Z for Z stored [s][n]; part holds chunks*s*s.
+template <typename T>
+cudaError_t launch_gram(const T* Z, int64_t n, int s, int chunks, double* part, double* C,
+                        cudaStream_t st);
+// Eigenvalues (descending) of a symmetric N x N FP64 matrix, N <= 512; Wg is
+// N*N scratch, d and e N each.
+cudaError_t launch_sym_eigvals(const double* A, int N, double* Wg, double* d, double* e,
+                               double* evals, cudaStream_t st);
+// out[0] = H~, out[1..k] = p~ from the k largest Gram eigenvalues.
+cudaError_t launch_proj_combine(const double* evals, int k, double* out, cudaStream_t st);
+
 // ---- combine (vne_combine.cu) ----------------------------------------------------
 // moments[k][j] for k = 0..m of the Chebyshev columns / Taylor columns, then
 // the FP64 estimates into sc.
