@@ -10,7 +10,8 @@ s = 128 Gaussian probes sharing every pass over R (41 tensor-core steps),
 FP64 combine, and the estimates copied back to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|bf16x3|f64]
-                    [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7]
+                    [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7|
+                                lowrank_n8192_k64]
                     [--impl reference]
 
 Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on the
@@ -84,6 +85,9 @@ def peak_value(d, *keys):
 
 def make_workload(name):
     w = dict(synth.WORKLOADS[name])
+    if w["kind"] == "lowrank":
+        R, p, _ = synth.dense_lowrank(w["n"], w["k"], w["tau"], w["seed"])
+        return w, R, p
     if w["kind"] == "dense":
         if w["spectrum"] == "powerlaw":
             R, p, _ = synth.dense_powerlaw(w["n"], w["k"], w["alpha"], w["floor"], w["seed"])
@@ -190,6 +194,139 @@ def oracle_sample_time(w, R, s_sample):
     return full, desc, threads
 
 
+def oracle_projection_time(w, R):
+    """Time one oracle call of Algorithm alg:EN on the full matrix."""
+    import oracle.projection as OP
+
+    t0 = time.perf_counter()
+    OP.estimate_projection(R, w["k"], w["s"], w["sketch"], seed=w["seed"])
+    t = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count() or 1
+    desc = (f"oracle (NumPy FP64) Algorithm EN on the full n={w['n']} rank-{w['k']} matrix: "
+            f"{w['sketch']} sketch s={w['s']}, R Pi and its SVD, one whole estimate")
+    return t, desc, threads
+
+
+PROJ_METRIC = ("entropies/s (rank-64 n=8192 density matrices through Algorithm EN: Gaussian "
+               "sketch s=256, R Pi, singular values, top-64 entropy)")
+
+
+def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1801_01072_gb300 as vne
+
+    n, k, s = w["n"], w["k"], w["s"]
+    prec = args.precision if args.precision in ("f32", "f64") else "f32"
+    Rd = torch.as_tensor(Rh).to(dev)
+    seed = w["seed"] + 1000 * rank
+
+    def step(R):
+        return vne.entropy_projection(R, k, s, w["sketch"], seed=seed, precision=prec)
+
+    h = vne._handle(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        out = step(Rd)
+    torch.cuda.synchronize()
+    h.profile(True)
+    n_launch0 = h.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step(Rd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    n_launch = h.launch_count() - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = h.profile_read(1)
+    h.profile(False)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    Rpin = torch.as_tensor(Rh).pin_memory()
+    step(Rpin)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 4)
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(Rpin)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) / e2e_steps * 1e3
+
+    rel = None
+    if rank == 0 and prec != "f64" and not args.skip_f64_check:
+        ref = vne.entropy_projection(Rd, k, s, w["sketch"], seed=seed, precision="f64")
+        rel = {"H": abs(out.H - ref.H) / abs(ref.H),
+               "p_max_rel_to_p1": float(np.abs(out.p - ref.p).max() / ref.p[0])}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk, pk_src = peaks()
+    # FP32 (or FP64) SIMT product R Pi: 2 n^2 s flops per launch.  Peak of the
+    # FP32 pipes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (FP64: 1.25 TFLOP/s).
+    flops = 2.0 * n * n * s * args.steps
+    achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == "f32" else 1.25
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "kernel": "k_simt_step", "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
+            "peak_source": "derived: FP32 lanes x 2 x max SM clock" if prec == "f32"
+            else "nominal FP64"}
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        t_cpu, desc, threads = oracle_projection_time(w, Rh)
+        cpu = {"value": 1.0 / t_cpu, "unit": "entropies/s", "cores": threads, "kind": "oracle",
+               "sample": desc}
+    line = {
+        "metric": PROJ_METRIC,
+        "value": world * args.steps / (ms_max / 1e3),
+        "unit": "entropies/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": prec,
+        "data": "synthetic (seeded rank-k density matrices, no dataset)",
+        "config": {"workload": args.workload, "n": n, "k": k, "s": s, "sketch": w["sketch"],
+                   "precision": prec, "input": "R FP64 resident in HBM",
+                   "l2": "inputs larger than L2 (R is %.0f MB)" % (Rh.nbytes / 1e6),
+                   "parallelism": f"independent matrices, {world} GPU(s)"},
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
+                "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": (k + 1) * 8},
+        "gpu_launches": int(n_launch),
+        "phases_ms_per_step": {"product": k_ms / args.steps,
+                               "other": ms_max / args.steps - k_ms / args.steps},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "rel_err_vs_f64": rel,
+        "estimates": {"H": out.H, "H_exact": float(-(p * np.log(p)).sum())},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -209,6 +346,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
 
     w, Rh, p = make_workload(args.workload)
+    if w["kind"] == "lowrank":
+        return run_gpu_projection(args, w, Rh, p, world, rank, local, dev)
     dense = w["kind"] == "dense"
     n, m, s = w["n"], w["m"], w["s"]
     prec = args.precision if dense else "f32"
@@ -387,11 +526,34 @@ def run_gpu(args):
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------
 
+def run_reference_projection(args, w, Rh):
+    times = []
+    for i in range(args.warmup + args.steps):
+        t, desc, threads = oracle_projection_time(w, Rh)
+        if i >= args.warmup:
+            times.append(t)
+    value = len(times) / sum(times)
+    print(json.dumps({
+        "impl": "reference", "metric": PROJ_METRIC, "value": value, "unit": "entropies/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded rank-k density matrices, no dataset)",
+        "config": {"workload": args.workload, "n": w["n"], "k": w["k"], "s": w["s"],
+                   "sketch": w["sketch"]},
+        "cpu_baseline": {"value": value, "unit": "entropies/s", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "entropies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w, Rh, p = make_workload(args.workload)
+    if w["kind"] == "lowrank":
+        return run_reference_projection(args, w, Rh)
     s_sample = args.ref_probes
     times = []
     for i in range(args.warmup + args.steps):
@@ -433,7 +595,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dense_powerlaw_n8192", choices=list(synth.WORKLOADS))
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "f64", "f32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "f64", "f32"],
+                    help="recurrence arithmetic; the projection workload runs f32 unless f64")
     ap.add_argument("--cpu-probes", type=int, default=16)
     ap.add_argument("--ref-probes", type=int, default=4)
     ap.add_argument("--skip-cpu", action="store_true")

@@ -576,7 +576,7 @@ vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int 
     if (c.ok() && splitk > 1)
         c.launched(launch_split_sum<T>(Zpart, splitk, (int64_t)s * n, Z, h->sm_count, st));
     if (c.ok()) c.launched(launch_gram<T>(Z, n, s, chunks, part, C, st));
-    if (c.ok()) c.launched(launch_sym_eigvals(C, s, W, de, de + s, ev, st));
+    if (c.ok()) c.launched(launch_sym_eigvals(C, s, k, W, de, de + s, ev, st));
     if (c.ok()) c.launched(launch_proj_combine(ev, k, out, st));
     std::vector<double> host((size_t)k + 1);
     if (c.ok())

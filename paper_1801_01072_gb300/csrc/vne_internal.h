@@ -135,9 +135,9 @@ int gram_chunks(int64_t n, int s, int sm_count);
 template <typename T>
 cudaError_t launch_gram(const T* Z, int64_t n, int s, int chunks, double* part, double* C,
                         cudaStream_t st);
-// Eigenvalues (descending) of a symmetric N x N FP64 matrix, N <= 512; Wg is
-// N*N scratch, d and e N each.
-cudaError_t launch_sym_eigvals(const double* A, int N, double* Wg, double* d, double* e,
+// The `top` largest eigenvalues (descending, evals[0..top)) of a symmetric
+// N x N FP64 matrix, N <= 512; Wg is N*N scratch, d and e N each.
+cudaError_t launch_sym_eigvals(const double* A, int N, int top, double* Wg, double* d, double* e,
                                double* evals, cudaStream_t st);
 // out[0] = H~, out[1..k] = p~ from the k largest Gram eigenvalues.
 cudaError_t launch_proj_combine(const double* evals, int k, double* out, cudaStream_t st);

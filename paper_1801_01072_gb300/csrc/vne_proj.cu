@@ -3,7 +3,7 @@
 //      Hadamard (Algorithm alg:SHD) or input-sparsity (Algorithm alg:IS),
 //      generated from counters, stored [s][n];
 //   2. R~ = R Pi on the dense SIMT product kernel (vne_dense_simt.cu);
-//   3. the s x s Gram matrix R~^T R~ accumulated in FP64;
+//   3. the s x s Gram matrix R~^T R~ (FP64, or compensated FP32 sums);
 //   4. its eigenvalues (Householder reduction to tridiagonal form, then
 //      Sturm-sequence bisection), i.e. the squared singular values of R~;
 //   5. p~_i = sqrt(lambda_i) for the k largest and H~ = sum p~_i ln(1/p~_i).
@@ -96,25 +96,57 @@ cudaError_t launch_split_sum(const T* Zpart, int splitk, int64_t len, T* Z, int 
 }
 
 // ---------------------------------------------------------------------------
-// Gram matrix C = Z^T Z of Z stored [s][n]: 32 x 32 output tiles, the rows
-// split into `chunks` slices whose FP64 partials are summed in slice order.
-// Entry (a, b) and (b, a) take the same products in the same order, so C is
-// exactly symmetric.
+// Gram matrix C = Z^T Z of Z stored [s][n]: 32 x 32 output tiles of the lower
+// triangle (mirrored on store), the rows split into `chunks` slices whose
+// partials are summed in slice order.  Entries (a, b) and (b, a) of a diagonal
+// tile take the same products in the same order, so C is exactly symmetric.
+// FP64 Z: FP64 fused multiply-adds.  FP32 Z: each product is split exactly
+// into p + e (p = fl(xy), e = fma(x, y, -p)) and summed with Knuth's TwoSum
+// into an FP32 (sum, correction) pair -- the compensated dot product of
+// Ogita, Rump and Oishi (2005) -- which is as accurate as FP64 accumulation
+// while running on the FP32 pipes; the pair is added in FP64 at the end.
 // ---------------------------------------------------------------------------
 constexpr int GR_T = 32, GR_K = 32;
+
+template <typename T> struct GramAcc;
+template <> struct GramAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct GramAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        const float e = __fmaf_rn(x, y, -p);
+        const float t = __fadd_rn(s, p);
+        const float z = __fadd_rn(t, -s);
+        const float err = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -z)), __fadd_rn(p, -z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Z, int64_t n, int s,
                                               int64_t rows_per_chunk, double* __restrict__ part) {
-    __shared__ double As[GR_K][GR_T + 1];
-    __shared__ double Bs[GR_K][GR_T + 1];
+    __shared__ T As[GR_K][GR_T + 1];
+    __shared__ T Bs[GR_K][GR_T + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int a0 = blockIdx.y * GR_T, b0 = blockIdx.x * GR_T;
-    const int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk;
+    // blockIdx.x enumerates the lower-triangle tiles (ta >= tb)
+    int ta = 0, rem = (int)blockIdx.x;
+    while (rem > ta) {
+        rem -= ta + 1;
+        ++ta;
+    }
+    const int tb = rem;
+    const int a0 = ta * GR_T, b0 = tb * GR_T;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
     int64_t r1 = r0 + rows_per_chunk;
     if (r1 > n) r1 = n;
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    GramAcc<T> acc[2][2];
     for (int64_t k0 = r0; k0 < r1; k0 += GR_K) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -122,28 +154,32 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Z, int64_t n
             const int col = e >> 5, kk = e & 31;
             const int64_t r = k0 + kk;
             const int ca = a0 + col, cb = b0 + col;
-            As[kk][col] = (ca < s && r < r1) ? (double)Z[(int64_t)ca * n + r] : 0.0;
-            Bs[kk][col] = (cb < s && r < r1) ? (double)Z[(int64_t)cb * n + r] : 0.0;
+            As[kk][col] = (ca < s && r < r1) ? Z[(int64_t)ca * n + r] : (T)0;
+            Bs[kk][col] = (cb < s && r < r1) ? Z[(int64_t)cb * n + r] : (T)0;
         }
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < GR_K; ++kk) {
-            const double x0 = As[kk][ty * 2], x1 = As[kk][ty * 2 + 1];
-            const double y0 = Bs[kk][tx * 2], y1 = Bs[kk][tx * 2 + 1];
-            acc[0][0] = fma(x0, y0, acc[0][0]);
-            acc[0][1] = fma(x0, y1, acc[0][1]);
-            acc[1][0] = fma(x1, y0, acc[1][0]);
-            acc[1][1] = fma(x1, y1, acc[1][1]);
+            const T x0 = As[kk][ty * 2], x1 = As[kk][ty * 2 + 1];
+            const T y0 = Bs[kk][tx * 2], y1 = Bs[kk][tx * 2 + 1];
+            acc[0][0].add(x0, y0);
+            acc[0][1].add(x0, y1);
+            acc[1][0].add(x1, y0);
+            acc[1][1].add(x1, y1);
         }
         __syncthreads();
     }
-    double* out = part + (int64_t)blockIdx.z * s * s;
+    double* out = part + (int64_t)blockIdx.y * s * s;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int a = a0 + ty * 2 + i, b = b0 + tx * 2 + j;
-            if (a < s && b < s) out[(int64_t)a * s + b] = acc[i][j];
+            if (a < s && b < s) {
+                const double v = acc[i][j].value();
+                out[(int64_t)a * s + b] = v;
+                if (ta != tb) out[(int64_t)b * s + a] = v;
+            }
         }
 }
 
@@ -158,7 +194,8 @@ __global__ void k_sum_chunks(const double* __restrict__ part, int chunks, int64_
 }
 
 int gram_chunks(int64_t n, int s, int sm_count) {
-    const int64_t tiles = (int64_t)((s + GR_T - 1) / GR_T) * ((s + GR_T - 1) / GR_T);
+    const int64_t nt = (s + GR_T - 1) / GR_T;
+    const int64_t tiles = nt * (nt + 1) / 2;
     int64_t chunks = (2 * (int64_t)sm_count + tiles - 1) / tiles;
     const int64_t max_chunks = (n + 255) / 256;
     if (chunks > max_chunks) chunks = max_chunks;
@@ -172,7 +209,8 @@ cudaError_t launch_gram(const T* Z, int64_t n, int s, int chunks, double* part, 
                         cudaStream_t st) {
     int64_t rows = (n + chunks - 1) / chunks;
     rows = (rows + GR_K - 1) / GR_K * GR_K;
-    dim3 grid((unsigned)((s + GR_T - 1) / GR_T), (unsigned)((s + GR_T - 1) / GR_T), (unsigned)chunks);
+    const unsigned nt = (unsigned)((s + GR_T - 1) / GR_T);
+    dim3 grid(nt * (nt + 1) / 2, (unsigned)chunks);
     k_gram<T><<<grid, 256, 0, st>>>(Z, n, s, rows, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -275,69 +313,312 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiag(const double* __restric
     }
 }
 
-// Number of eigenvalues of the tridiagonal (d, e) below x (Sturm sequence of
-// the LDL^T pivots; a pivot of magnitude <= pivmin is replaced by -pivmin).
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, int N, double x,
-                                           double pivmin) {
+// ---------------------------------------------------------------------------
+// The same reduction on a thread-block cluster of C CTAs, the matrix held in
+// distributed shared memory: row r lives in CTA r % C (local row r / C).  Per
+// column k every CTA
+//   1. sends its entries of x = A[k+1:, k] and its part of ||x||^2 to all CTAs;
+//   2. forms v locally, computes p = A_sub v for its own rows and sends p and
+//      its part of v^T p to all CTAs;
+//   3. updates its own rows with w = p - (v^T p) v.
+// Gathered vectors and partial sums are double-buffered by column parity, so
+// the two cluster barriers of a column separate every write from the reads it
+// could overwrite.  Partial sums are added in CTA order, so every CTA takes the
+// same branch and the same scalars.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ uint32_t proj_smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void proj_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+__device__ __forceinline__ uint32_t proj_cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t proj_cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Store v at the address of *local_ptr in the shared memory of CTA `rank`.
+__device__ __forceinline__ void st_peer_f64(const double* local_ptr, uint32_t rank, double v) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(proj_smem_u32(local_ptr)), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+}  // namespace
+
+constexpr int kClusterMax = 16;
+constexpr int kEigWarps = kEigThreads / 32;
+
+__global__ void __launch_bounds__(kEigThreads) k_tridiag_cluster(const double* __restrict__ A, int N,
+                                                                 double* __restrict__ d_out,
+                                                                 double* __restrict__ e_out) {
+    extern __shared__ double Wl[];
+    __shared__ double xb[2][kEigMaxN], pb[2][kEigMaxN];
+    __shared__ double part[2][2][kClusterMax];
+    __shared__ double wsum[2][kEigWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = (int)proj_cluster_rank(), C = (int)proj_cluster_size();
+    const int rows_local = (N - rank + C - 1) / C;
+    // local row lr belongs to warp lr % kEigWarps in every phase, so a warp
+    // only ever reads the rows it wrote itself
+    for (int lr = warp; lr < rows_local; lr += kEigWarps) {
+        const int r = rank + lr * C;
+        for (int j = lane; j < N; j += 32) Wl[(int64_t)lr * N + j] = A[(int64_t)r * N + j];
+    }
+    proj_cluster_sync();
+    for (int k = 0; k + 2 < N; ++k) {
+        const int b = k & 1, m = N - k - 1, o = k + 1;
+        // 1. gather x = A[o:, k] and ||x[1:]||^2
+        double tpart = 0.0;
+        for (int lr = warp; lr < rows_local; lr += kEigWarps) {
+            const int r = rank + lr * C;
+            if (r < o) continue;
+            const double x = Wl[(int64_t)lr * N + k];
+            if (r > o) tpart += x * x;
+            if (lane < C) st_peer_f64(&xb[b][r - o], (uint32_t)lane, x);
+        }
+        if (lane == 0) wsum[0][warp] = tpart;
+        __syncthreads();
+        if (warp == 0) {
+            double t = lane < kEigWarps ? wsum[0][lane] : 0.0;
+            t = warp_sum(t);
+            if (lane < C) st_peer_f64(&part[b][0][rank], (uint32_t)lane, t);
+        }
+        proj_cluster_sync();
+        double tail = 0.0;
+        for (int c = 0; c < C; ++c) tail += part[b][0][c];
+        const double x0 = xb[b][0];
+        if (k % C == rank && tid == 0) d_out[k] = Wl[(int64_t)(k / C) * N + k];
+        if (tail == 0.0) {  // column already reduced: same branch in every CTA
+            if (rank == 0 && tid == 0) e_out[k] = x0;
+            continue;
+        }
+        const double xx = tail + x0 * x0;
+        const double alpha = x0 >= 0.0 ? -sqrt(xx) : sqrt(xx);
+        const double v0 = x0 - alpha;
+        const double scale = 1.0 / sqrt(tail + v0 * v0);
+        // 2. p = A_sub v on own rows (v_j = scale * (j ? x_j : x_0 - alpha)), v^T p
+        double kpart = 0.0;
+        for (int lr = warp; lr < rows_local; lr += kEigWarps) {
+            const int r = rank + lr * C;
+            if (r < o) continue;
+            const double* row = Wl + (int64_t)lr * N + o;
+            double acc = 0.0;
+            for (int j = lane; j < m; j += 32) acc = fma(row[j], (j ? xb[b][j] : v0) * scale, acc);
+            acc = warp_sum(acc);
+            if (lane < C) st_peer_f64(&pb[b][r - o], (uint32_t)lane, acc);
+            const int i = r - o;
+            kpart += (i ? xb[b][i] : v0) * scale * acc;
+        }
+        if (lane == 0) wsum[1][warp] = kpart;
+        __syncthreads();
+        if (warp == 0) {
+            double t = lane < kEigWarps ? wsum[1][lane] : 0.0;
+            t = warp_sum(t);
+            if (lane < C) st_peer_f64(&part[b][1][rank], (uint32_t)lane, t);
+        }
+        proj_cluster_sync();
+        double K = 0.0;
+        for (int c = 0; c < C; ++c) K += part[b][1][c];
+        // 3. own rows -= 2 (v w^T + w v^T), w = p - K v
+        for (int lr = warp; lr < rows_local; lr += kEigWarps) {
+            const int r = rank + lr * C;
+            if (r < o) continue;
+            double* row = Wl + (int64_t)lr * N + o;
+            const int i = r - o;
+            const double vr = (i ? xb[b][i] : v0) * scale;
+            const double wr = pb[b][i] - K * vr;
+            for (int j = lane; j < m; j += 32) {
+                const double vj = (j ? xb[b][j] : v0) * scale;
+                const double wj = pb[b][j] - K * vj;
+                row[j] -= 2.0 * (vr * wj + wr * vj);
+            }
+        }
+        __syncwarp();  // next column's x is read by all lanes of the owning warp
+        if (rank == 0 && tid == 0) e_out[k] = alpha;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (N >= 2) {
+            if ((N - 2) % C == rank) d_out[N - 2] = Wl[(int64_t)((N - 2) / C) * N + (N - 2)];
+            if ((N - 1) % C == rank) e_out[N - 2] = Wl[(int64_t)((N - 1) / C) * N + (N - 2)];
+        }
+        if ((N - 1) % C == rank) {
+            d_out[N - 1] = Wl[(int64_t)((N - 1) / C) * N + (N - 1)];
+            e_out[N - 1] = 0.0;
+        }
+    }
+    proj_cluster_sync();
+}
+
+// Number of eigenvalues of the tridiagonal (d, e) below x: sign changes of
+// the leading principal minors p_i = det(T_i - x I), p_0 = 1,
+//   p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2}
+// (Sturm's theorem), without divisions: FP64 division is many times the cost
+// of a fused multiply-add on this part.  The pair (p_{i-1}, p_i) is rescaled by
+// a power of two (exact) whenever |p_i| leaves [2^-400, 2^400]; a minor that
+// comes out exactly zero is replaced by -2^-60 p_{i-1}, i.e. a tiny negative
+// pivot, the usual convention of the pivot form of the count.
+// e2 holds the squared off-diagonal entries.
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int N, double x) {
     int c = 0;
-    double q = d[0] - x;
-    if (fabs(q) <= pivmin) q = -pivmin;
-    if (q < 0.0) ++c;
-    for (int i = 1; i < N; ++i) {
-        q = d[i] - x - (e[i - 1] * e[i - 1]) / q;
-        if (fabs(q) <= pivmin) q = -pivmin;
-        if (q < 0.0) ++c;
+    double pm2 = 0.0, pm1 = 1.0;
+    for (int i = 0; i < N; ++i) {
+        double p = (d[i] - x) * pm1;
+        if (i > 0) p = fma(-e2[i - 1], pm2, p);
+        long long bits = __double_as_longlong(p);
+        if ((bits << 1) == 0) {  // exact zero
+            p = -pm1 * 0x1.0p-60;
+            bits = __double_as_longlong(p);
+        }
+        c += (int)(((unsigned long long)bits >> 63) ^ ((unsigned long long)__double_as_longlong(pm1) >> 63));
+        const int ex = (int)((bits >> 52) & 0x7FF) - 1023;
+        if (ex > 400 || ex < -400) {
+            const double sc = __longlong_as_double((long long)(1023 - ex) << 52);  // 2^-ex
+            p *= sc;
+            pm1 *= sc;
+        }
+        pm2 = pm1;
+        pm1 = p;
     }
     return c;
 }
 
-// Bisection: thread j finds the j-th smallest eigenvalue and stores it at
-// evals[N-1-j] (descending order).
-__global__ void k_bisect(const double* __restrict__ d_in, const double* __restrict__ e_in, int N,
-                         double* __restrict__ evals) {
-    __shared__ double d[kEigMaxN], e[kEigMaxN];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+// Multisection: each half-warp owns one eigenvalue (ascending rank j >= j0) and
+// splits its bracket [a, b] (count(a) <= j < count(b)) at 16 interior points
+// per round, keeping the sub-interval where the count passes j.  It stops
+// when the bracket is within 16 ulps of the spectrum's scale and stores the
+// midpoint at evals[N-1-j] (descending order).
+constexpr int kMsLanes = 16;
+
+__global__ void __launch_bounds__(32) k_bisect_multi(const double* __restrict__ d_in,
+                                                     const double* __restrict__ e_in, int N,
+                                                     int j0, double* __restrict__ evals) {
+    __shared__ double d[kEigMaxN], e[kEigMaxN], e2[kEigMaxN];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < N; i += 32) {
         d[i] = d_in[i];
         e[i] = e_in[i];
+        e2[i] = e_in[i] * e_in[i];
     }
-    __syncthreads();
-    double lo = d[0], hi = d[0], emax2 = 0.0;
-    for (int i = 0; i < N; ++i) {
+    __syncwarp();
+    double lo = 1e308, hi = -1e308, emax2 = 0.0;
+    for (int i = lane; i < N; i += 32) {
         const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < N ? fabs(e[i]) : 0.0);
         lo = fmin(lo, d[i] - r);
         hi = fmax(hi, d[i] + r);
         if (i + 1 < N) emax2 = fmax(emax2, e[i] * e[i]);
     }
-    const double pivmin = 0x1.0p-1022 * fmax(1.0, emax2);
-    const double pad = 2.2204460492503131e-16 * fmax(fabs(lo), fabs(hi)) + pivmin;
-    lo -= pad;
-    hi += pad;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    double a = lo, b = hi;
-    for (int it = 0; it < 256; ++it) {
-        const double mid = 0.5 * (a + b);
-        if (!(mid > a && mid < b)) break;
-        if (sturm_count(d, e, N, mid, pivmin) >= j + 1) b = mid;
-        else a = mid;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
     }
-    evals[N - 1 - j] = 0.5 * (a + b);
+    const double pivmin = 0x1.0p-1022 * fmax(1.0, emax2);
+    const double scale = fmax(fabs(lo), fabs(hi));
+    const double pad = 2.2204460492503131e-16 * scale + pivmin;
+    const double tol = 16.0 * 2.2204460492503131e-16 * scale + 2.0 * pivmin;
+    const int g = lane / kMsLanes, l = lane % kMsLanes;
+    const int j = j0 + blockIdx.x * (32 / kMsLanes) + g;
+    const bool live = j < N;
+    const unsigned gmask = 0xFFFFu << (g * kMsLanes);
+    double a = lo - pad, b = hi + pad;
+    for (int round = 0; round < 64; ++round) {
+        if (!(b - a > tol)) break;  // uniform within the half-warp
+        const double x = a + (b - a) * ((double)(l + 1) / (double)(kMsLanes + 1));
+        const bool up = live ? sturm_count(d, e2, N, x) >= j + 1 : true;
+        const unsigned bal = (__ballot_sync(gmask, up) & gmask) >> (g * kMsLanes);
+        const int L = bal ? __ffs(bal) - 1 : kMsLanes;  // first point with count > j
+        const double xl = __shfl_sync(gmask, x, g * kMsLanes + (L > 0 ? L - 1 : 0));
+        const double xr = __shfl_sync(gmask, x, g * kMsLanes + (L < kMsLanes ? L : kMsLanes - 1));
+        const double na = L > 0 ? xl : a;
+        const double nb = L < kMsLanes ? xr : b;
+        if (!(na >= a && nb <= b && na < nb)) break;  // no progress at this scale
+        a = na;
+        b = nb;
+    }
+    if (live && l == 0) evals[N - 1 - j] = 0.5 * (a + b);
 }
 
-cudaError_t launch_sym_eigvals(const double* A, int N, double* Wg, double* d, double* e,
+// CTAs of the reduction: about 16 rows each (FP64 work spread over SMs), at
+// most 16 CTAs and 160 KB of rows per CTA.
+int eig_cluster_size(int N) {
+    int C = 1;
+    while (C < kClusterMax && C * 16 < N) C *= 2;
+    if ((int64_t)((N + C - 1) / C) * N * 8 > 160 * 1024) return -1;
+    return C;
+}
+
+cudaError_t launch_sym_eigvals(const double* A, int N, int top, double* Wg, double* d, double* e,
                                double* evals, cudaStream_t st) {
-    if (N < 1 || N > kEigMaxN) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)N * N * sizeof(double);
-    const int use_smem = smem <= 160 * 1024;
-    if (use_smem) {
-        cudaError_t r = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    if (N < 1 || N > kEigMaxN || top < 1 || top > N) return cudaErrorInvalidValue;
+    int C = eig_cluster_size(N);
+    cudaError_t r = cudaSuccess;
+    bool done = false;
+    if (C >= 1) {
+        const size_t smem = (size_t)((N + C - 1) / C) * N * sizeof(double);
+        r = cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (r == cudaSuccess && C > 8)
+            r = cudaFuncSetAttribute(k_tridiag_cluster,
+                                     cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(kEigThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (r == cudaSuccess)
+            r = cudaOccupancyMaxActiveClusters(&clusters, k_tridiag_cluster, &cfg);
+        if (r == cudaSuccess && clusters == 0 && C > 8) {
+            // 16-CTA clusters not schedulable here: 8 CTAs if their rows fit
+            const int C8 = 8;
+            const size_t smem8 = (size_t)((N + C8 - 1) / C8) * N * sizeof(double);
+            if (smem8 <= 160 * 1024) {
+                attr[0].val.clusterDim.x = C8;
+                cfg.gridDim = dim3(C8);
+                cfg.dynamicSmemBytes = smem8;
+                r = cudaFuncSetAttribute(k_tridiag_cluster,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8);
+                if (r == cudaSuccess)
+                    r = cudaOccupancyMaxActiveClusters(&clusters, k_tridiag_cluster, &cfg);
+            }
+        }
+        if (r == cudaSuccess && clusters > 0) {
+            r = cudaLaunchKernelEx(&cfg, k_tridiag_cluster, A, N, d, e);
+            if (r != cudaSuccess) return r;
+            done = true;
+        } else {
+            cudaGetLastError();  // fall back to the one-CTA kernel
+        }
+    }
+    if (!done) {
+        const size_t smem = (size_t)N * N * sizeof(double);
+        const int use_smem = smem <= 160 * 1024;
+        if (use_smem) {
+            r = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (r != cudaSuccess) return r;
+        }
+        k_tridiag<<<1, kEigThreads, use_smem ? smem : 0, st>>>(A, N, Wg, use_smem, d, e);
+        r = cudaGetLastError();
         if (r != cudaSuccess) return r;
     }
-    k_tridiag<<<1, kEigThreads, use_smem ? smem : 0, st>>>(A, N, Wg, use_smem, d, e);
-    cudaError_t r = cudaGetLastError();
-    if (r != cudaSuccess) return r;
-    k_bisect<<<(N + 31) / 32, 32, 0, st>>>(d, e, N, evals);
+    // only the `top` largest eigenvalues: ascending ranks N-top .. N-1
+    k_bisect_multi<<<(top + 1) / 2, 32, 0, st>>>(d, e, N, N - top, evals);
     return cudaGetLastError();
 }
 
