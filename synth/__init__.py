@@ -32,6 +32,9 @@ __all__ = [
     "dense_powerlaw",
     "orthonormal_columns",
     "dense_lowrank",
+    "training_spectrum",
+    "learned_sample_params",
+    "mlp_init",
     "band_diag_dominant",
     "band_poisson",
     "dia_to_dense",
@@ -110,6 +113,48 @@ def dense_lowrank(n: int = 8192, k: int = 64, tau: float = 16.0, seed: int = 4):
     psi = orthonormal_columns(n, k, seed)
     p = spectrum_exponential(k, tau)
     return dense_density(psi, p), p, psi
+
+
+def training_spectrum(kind: int, n: int, a: float, ktop: int, floor: float) -> np.ndarray:
+    """Spectra of the learned correction's training set, unit trace, i = 1..n:
+    kind 0: p_i ~ exp(-(i-1)/a); kind 1: p_i ~ i^-a for i <= ktop, floor beyond."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    if kind == 0:
+        q = np.exp(-(i - 1.0) / a)
+    else:
+        q = np.where(i <= ktop, i ** -a, floor)
+    return q / q.sum()
+
+
+def learned_sample_params(count: int, seed: int, n_lo: int = 1024, n_hi: int = 4096) -> dict:
+    """Seeded parameters of `count` training spectra: half exponential with
+    a = tau ~ U(10, n/4), half power law with a = alpha ~ U(1.1, 2.0),
+    ktop ~ U(n/8, n/2) and a floor log-uniform in [1e-10, 1e-6]; n
+    log-uniform in [n_lo, n_hi]; u = c * p_1 with c ~ U(1.0, 1.1); one probe
+    seed per spectrum.  Arrays are int32 / float32 / uint64."""
+    r = np.random.default_rng(seed)
+    n = np.exp(r.uniform(np.log(n_lo), np.log(n_hi), count)).astype(np.int32)
+    kind = (np.arange(count) % 2).astype(np.int32)
+    tau = r.uniform(10.0, n / 4.0)
+    alpha = r.uniform(1.1, 2.0, count)
+    a = np.where(kind == 0, tau, alpha).astype(np.float32)
+    ktop = r.uniform(n / 8.0, n / 2.0).astype(np.int32)
+    floor = np.exp(r.uniform(np.log(1e-10), np.log(1e-6), count)).astype(np.float32)
+    c = r.uniform(1.0, 1.1, count).astype(np.float32)
+    seeds = r.integers(1, 2 ** 62, count, dtype=np.int64).astype(np.uint64)
+    return dict(kind=kind, n=n, a=a, ktop=ktop, floor=floor, c=c, seed=seeds)
+
+
+def mlp_init(seed: int, layers=((19, 128), (128, 128), (128, 128), (128, 1))) -> np.ndarray:
+    """Initial parameters of the correction network, one flat vector
+    [W1 (out x in, row-major), b1, W2, b2, ...]: U(-1/sqrt(in), 1/sqrt(in))."""
+    r = np.random.default_rng(seed)
+    parts = []
+    for i, o in layers:
+        lim = 1.0 / np.sqrt(i)
+        parts.append(r.uniform(-lim, lim, o * i))
+        parts.append(r.uniform(-lim, lim, o))
+    return np.concatenate(parts)
 
 
 def band_diag_dominant(n: int, half_bw: int = 16, offdiag_scale: float = 0.02,
