@@ -223,6 +223,76 @@ vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k,
                                   int32_t sketch, int32_t krylov_iters, int32_t precision,
                                   uint64_t seed, double* H_out, double* p_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned moment correction (an extension of Algorithm 1b; the paper has no
+ * learned component).  The Chebyshev estimate of degree m = 16 carries the
+ * truncation error of f_16 (Lemma lem:prior).  A network maps 19 features of
+ * the estimate -- tot_k / (s n) for k = 0..15 with tot_k = sum_j mu_{k,j} the
+ * probe totals of the moments, ln(n)/10, ln(lambda~)/10 and ln(u)/10 -- to
+ * c = 100 (H - H_16) / (n u), and the corrected estimate is H_16 + c n u / 100.
+ * (With p = u y the truncation error of f_m is u e_m(y), e_m that of y ln y
+ * on [0, 1], so c is a mean over the spectral distribution of y.)
+ * Network: 19 -> 128 -> 128 -> 128 -> 1, GELU(x) = x Phi(x) on the hidden
+ * layers, linear output, FP32.  Parameters are one flat device array of
+ * VNE_MLP_N_PARAMS floats: [W1 (128 x 19, row-major), b1 (128), W2 (128 x 128),
+ * b2, W3 (128 x 128), b3, W4 (1 x 128), b4 (1)].  Feature rows are
+ * VNE_MLP_N_IN floats.  All pointers below are DEVICE pointers unless marked
+ * host.
+ * ------------------------------------------------------------------------- */
+#define VNE_MLP_N_IN 19
+#define VNE_MLP_N_MOMENTS 16
+#define VNE_MLP_N_HIDDEN 128
+#define VNE_MLP_N_PARAMS 35713
+#define VNE_MLP_DEGREE 16
+
+/* Training data without forming R: for `count` spectra p (index b), with
+ *   kind[b] 0: p_i ~ exp(-(i-1)/a[b]); 1: p_i ~ i^-a[b] for i <= ktop[b],
+ *   floor[b] beyond (i = 1..n[b], unit trace, n[b] >= 2),
+ * u = c[b] * p_1 and lambda~ = p_1, draws the probe totals of Algorithm 1b for
+ * R = Psi diag(p) Psi^T with Haar Psi and s Gaussian probes -- sum_j mu_{k,j}
+ * = sum_i w_i T_k(2 p_i / u - 1), w_i = sum_j z_ij^2, z_ij the Gaussian probe
+ * value (i, j) of seeds[b] -- for k = 0..m (15 <= m <= 64), and writes
+ * features[b] (19 floats), target[b] = 100 (H(p) - H_m) / (n u) (float), the exact
+ * entropy H_exact[b], the estimate H_low[b] = H_m and, if totals != NULL,
+ * totals[b*(m+1) + k].  Arithmetic: FP32 draws and polynomials, FP64 sums. */
+vne_status vne_spectral_samples(vne_handle* h, int32_t count, const int32_t* kind,
+                                const int32_t* n, const float* a, const int32_t* ktop,
+                                const float* floor, const float* c, const uint64_t* seeds,
+                                int32_t m, int32_t s, float* features, float* target,
+                                double* H_exact, double* H_low, double* totals, void* stream);
+
+/* y[b] = net(X[b]) for b < batch (X: batch x 19 floats, y: batch floats). */
+vne_status vne_mlp_forward(vne_handle* h, const float* params, const float* X, int32_t batch,
+                           float* y, void* stream);
+
+/* Mean squared error of net(X) against target (batch rows) and its gradient
+ * (grad: VNE_MLP_N_PARAMS floats, same layout as params); loss_out is host. */
+vne_status vne_mlp_gradient(vne_handle* h, const float* params, const float* X,
+                            const float* target, int32_t batch, float* grad, double* loss_out,
+                            void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1) on
+ * the batch of rows idx_i = (a * ((first + i) mod rows) + c) mod rows, i < batch,
+ * of X / target (rows rows), where a (coprime to rows) and c come from
+ * perm_seed: `first` = e * rows + (offset in epoch e) walks a fixed
+ * permutation.  params, adam_m, adam_v: VNE_MLP_N_PARAMS floats each (Adam
+ * moments start at zero).  loss_out: host, or NULL (then the call does not
+ * synchronise the stream). */
+vne_status vne_mlp_train_step(vne_handle* h, float* params, float* adam_m, float* adam_v,
+                              int32_t step, float lr, const float* X, const float* target,
+                              int64_t rows, int32_t batch, int64_t first, uint64_t perm_seed,
+                              double* loss_out, void* stream);
+
+/* Algorithm 1b with Gaussian probes at degree p->m (VNE_MLP_DEGREE, the
+ * degree the network is trained for; >= 15 required) followed by the learned
+ * correction: H_out = H_m + (n u / 100) net(features).  H_plain_out (host, or
+ * NULL) receives H_m itself -- the uncorrected estimate, which is also the
+ * fallback when no trained network is at hand.  Other arguments as for
+ * vne_entropy_chebyshev; params is the trained network (device). */
+vne_status vne_entropy_chebyshev_learned(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                                         const float* params, double* H_out,
+                                         double* H_plain_out, double* u_out, void* stream);
+
 /* The random projection of vne_entropy_projection: out[c*n + i] = Pi[i, c]
  * (FP64, device, n*s doubles, caller-owned). */
 vne_status vne_sketch_block(vne_handle* h, int64_t n, int32_t s, int32_t sketch, uint64_t seed,

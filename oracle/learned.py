@@ -18,7 +18,12 @@ function has a pin in tests/test_oracle_learned.py):
   alone, with z the Gaussian probe block of `seed` (counter j*n + i).
 * ``features`` -- the 19 network inputs: tot_k / (s n) for k = 0..15,
   ln(n)/10, ln(lambda~)/10, ln(u)/10.
-* ``target`` -- (H(p) - H_16) / ln n, the correction the network learns.
+* ``target`` -- 100 (H(p) - H_16) / (n u), the correction the network
+  learns.  With p_i = u y_i, h(p) - f_m(p) = u e_m(y) where e_m is the error
+  of the degree-m Chebyshev truncation of y ln y on [0, 1] (the term y ln u is
+  linear and expanded exactly), so H - H_m = -u sum_i e_m(y_i) + probe noise:
+  divided by n u it is a mean over the spectral distribution of y, which the
+  moment features tot_k / (s n) describe, whatever n is.
 * the network: 19 -> 128 -> 128 -> 128 -> 1, GELU(x) = x Phi(x) (exact, erf)
   on the hidden layers, linear output; parameters are one flat vector
   [W1 (128x19 row-major), b1, W2 (128x128), b2, W3 (128x128), b3, W4 (1x128), b4];
@@ -72,8 +77,11 @@ def entropy(p: np.ndarray) -> float:
     return float(-(q * np.log(q)).sum())
 
 
-def target(p: np.ndarray, H_low: float) -> float:
-    return (entropy(p) - H_low) / np.log(p.size)
+TARGET_SCALE = 100.0
+
+
+def target(p: np.ndarray, H_low: float, u: float) -> float:
+    return TARGET_SCALE * (entropy(p) - H_low) / (p.size * u)
 
 
 # --------------------------------------------------------------------------

@@ -63,6 +63,17 @@ SIGNATURES = [
     ("vne_entropy_projection", C.c_int,
      [_H, C.POINTER(VneMatrix), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
       _D, _D, C.c_void_p]),
+    ("vne_entropy_chebyshev_learned", C.c_int,
+     [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), C.c_void_p, _D, _D, _D, C.c_void_p]),
+    ("vne_spectral_samples", C.c_int,
+     [_H, C.c_int32] + [C.c_void_p] * 7 + [C.c_int32, C.c_int32] + [C.c_void_p] * 5
+     + [C.c_void_p]),
+    ("vne_mlp_forward", C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("vne_mlp_gradient", C.c_int,
+     [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, _D, C.c_void_p]),
+    ("vne_mlp_train_step", C.c_int,
+     [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p, C.c_void_p,
+      C.c_int64, C.c_int32, C.c_int64, C.c_uint64, _D, C.c_void_p]),
     ("vne_sketch_block", C.c_int,
      [_H, C.c_int64, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p]),
     ("vne_probe_block", C.c_int,

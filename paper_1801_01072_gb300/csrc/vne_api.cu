@@ -50,6 +50,8 @@ struct Outputs {
     double* mom_taylor = nullptr;
     double* u = nullptr;
     double* lam = nullptr;
+    const float* mlp = nullptr;      // trained correction network (device), or NULL
+    double* H_learned = nullptr;
 };
 
 struct DeviceGuard {
@@ -259,8 +261,10 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     auto plan = [&](Bump& b, void** Rcopy, void** Rop, __nv_bfloat16** Rhi, __nv_bfloat16** Rlo,
                     double** sc, double** ppart, unsigned int** counter, void** x0, void** x1,
                     void** G, uint64_t** bits, void** Yb0, void** Yb1, void** Yb2, void** Zpart,
-                    __nv_bfloat16** Sh, double** part, double** mom_c, double** mom_t) {
+                    __nv_bfloat16** Sh, double** part, double** mom_c, double** mom_t,
+                    float** mws) {
         *sc = b.take<double>(SC_COUNT);
+        *mws = out.mlp ? b.take<float>(64 + mlp_workspace_floats(1)) : nullptr;
         *counter = b.take<unsigned int>(64);
         *ppart = b.take<double>((size_t)std::max(power_blocks, 256) * 3 * q);
         *Rcopy = nullptr;
@@ -300,17 +304,18 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     void *Rcopy, *Rop, *x0, *x1, *G, *Yb0, *Yb1, *Yb2, *Zpart;
     __nv_bfloat16 *Rhi, *Rlo, *Sh;
     double *sc, *ppart, *part, *mom_c, *mom_t;
+    float* mws;
     unsigned int* counter;
     uint64_t* bits;
     {
         Bump b0(nullptr);
         plan(b0, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
-             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t);
+             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
         vs = ensure_ws(h, b0.off + 4096);
         if (vs != VNE_OK) return vs;
         Bump b1(h->ws);
         plan(b1, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
-             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t);
+             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
     }
     h->ev_used = 0;
     h->pending.clear();
@@ -477,6 +482,11 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         if (c.ok())
             c.launched(launch_combine(P, s, m, has_cheb ? 0 : -1, has_tay ? (has_cheb ? s : 0) : -1,
                                       mom_c, mom_t, sc, c.st));
+        if (c.ok() && out.mlp) {
+            int cnt = 0;
+            c.chk(launch_learned(mom_c, m, s, n, sc, out.mlp, mws, &cnt, c.st));
+            h->launches += cnt;
+        }
     }
 
     // ---- results ----
@@ -508,6 +518,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     if (out.H_taylor) *out.H_taylor = hs[SC_H_TAYLOR];
     if (out.u) *out.u = hs[SC_U];
     if (out.lam) *out.lam = hs[SC_LAM];
+    if (out.H_learned) *out.H_learned = hs[SC_H_LEARNED];
     return VNE_OK;
 }
 
@@ -698,6 +709,119 @@ vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k,
     if (precision == VNE_PREC_F64)
         return run_projection<double>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
     return run_projection<float>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
+}
+
+vne_status vne_entropy_chebyshev_learned(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                                         const float* params, double* H_out,
+                                         double* H_plain_out, double* u_out, void* stream) {
+    if (!H_out || !params || !p) return VNE_ERR_INVALID_ARG;
+    if (p->m < VNE_MLP_N_MOMENTS - 1 || p->probe != VNE_GAUSSIAN) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.H_cheb = H_plain_out;
+    o.u = u_out;
+    o.mlp = params;
+    o.H_learned = H_out;
+    return run(h, R, p, MODE_CHEB, o, stream);
+}
+
+vne_status vne_spectral_samples(vne_handle* h, int32_t count, const int32_t* kind,
+                                const int32_t* n, const float* a, const int32_t* ktop,
+                                const float* floor, const float* c, const uint64_t* seeds,
+                                int32_t m, int32_t s, float* features, float* target,
+                                double* H_exact, double* H_low, double* totals, void* stream) {
+    if (!h || count < 1 || s < 1 || !kind || !n || !a || !ktop || !floor || !c || !seeds ||
+        !features || !target || !H_exact || !H_low)
+        return VNE_ERR_INVALID_ARG;
+    if (m < VNE_MLP_N_MOMENTS - 1 || m > 64) return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    cudaError_t e = launch_spectral_sample(count, kind, n, a, ktop, floor, c, seeds, m, s, features,
+                                           target, H_exact, H_low, totals, (cudaStream_t)stream);
+    h->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return map_err(h, e);
+}
+
+namespace {
+// workspace of the network calls: activations, row indices, gradient, loss
+struct MlpWs {
+    float* act;
+    int* idx;
+    float* grad;
+    double* loss;
+};
+vne_status mlp_ws(vne_handle* h, int B, MlpWs* w) {
+    auto plan = [&](Bump& b) {
+        w->act = b.take<float>(mlp_workspace_floats(B));
+        w->idx = b.take<int>((size_t)B);
+        w->grad = b.take<float>(VNE_MLP_N_PARAMS);
+        w->loss = b.take<double>(1);
+    };
+    Bump b0(nullptr);
+    plan(b0);
+    vne_status vs = ensure_ws(h, b0.off + 4096);
+    if (vs != VNE_OK) return vs;
+    Bump b1(h->ws);
+    plan(b1);
+    return VNE_OK;
+}
+}  // namespace
+
+vne_status vne_mlp_forward(vne_handle* h, const float* params, const float* X, int32_t batch,
+                           float* y, void* stream) {
+    if (!h || !params || !X || !y || batch < 1) return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    MlpWs w;
+    vne_status vs = mlp_ws(h, batch, &w);
+    if (vs != VNE_OK) return vs;
+    int cnt = 0;
+    cudaError_t e = mlp_forward(params, X, batch, y, w.act, &cnt, (cudaStream_t)stream);
+    h->launches += cnt;
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return map_err(h, e);
+}
+
+vne_status vne_mlp_gradient(vne_handle* h, const float* params, const float* X,
+                            const float* target, int32_t batch, float* grad, double* loss_out,
+                            void* stream) {
+    if (!h || !params || !X || !target || !grad || batch < 1) return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    MlpWs w;
+    vne_status vs = mlp_ws(h, batch, &w);
+    if (vs != VNE_OK) return vs;
+    int cnt = 0;
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = mlp_loss_grad(params, X, target, nullptr, batch, grad, w.loss, w.act, &cnt, st);
+    h->launches += cnt;
+    double loss = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, w.loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && loss_out) *loss_out = loss;
+    return map_err(h, e);
+}
+
+vne_status vne_mlp_train_step(vne_handle* h, float* params, float* adam_m, float* adam_v,
+                              int32_t step, float lr, const float* X, const float* target,
+                              int64_t rows, int32_t batch, int64_t first, uint64_t perm_seed,
+                              double* loss_out, void* stream) {
+    if (!h || !params || !adam_m || !adam_v || !X || !target || step < 1 || rows < 1 ||
+        batch < 1 || first < 0 || !(lr > 0.f))
+        return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    MlpWs w;
+    vne_status vs = mlp_ws(h, batch, &w);
+    if (vs != VNE_OK) return vs;
+    int cnt = 0;
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = mlp_train_step(params, adam_m, adam_v, step, lr, X, target, rows, batch, first,
+                                   perm_seed, w.idx, w.grad, w.loss, w.act, &cnt, st);
+    h->launches += cnt;
+    if (e == cudaSuccess && loss_out) {
+        double loss = 0.0;
+        e = cudaMemcpyAsync(&loss, w.loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) *loss_out = loss;
+    }
+    return map_err(h, e);
 }
 
 vne_status vne_sketch_block(vne_handle* h, int64_t n, int32_t s, int32_t sketch, uint64_t seed,

@@ -60,6 +60,7 @@ enum ScalarSlot {
     SC_H_CHEB = 3,   // Chebyshev estimate
     SC_H_TAYLOR = 4, // Taylor estimate
     SC_FLAGS = 5,    // error bits (stored as a double-sized slot, read as uint64)
+    SC_H_LEARNED = 6, // Chebyshev estimate plus the learned correction
     SC_NORM = 8,     // power method: 3*q running sums (||y||^2, x.y, x.x) per trial
     SC_COUNT = 8 + 3 * 64
 };

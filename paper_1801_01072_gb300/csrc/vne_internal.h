@@ -142,6 +142,25 @@ cudaError_t launch_sym_eigvals(const double* A, int N, int top, double* Wg, doub
 // out[0] = H~, out[1..k] = p~ from the k largest Gram eigenvalues.
 cudaError_t launch_proj_combine(const double* evals, int k, double* out, cudaStream_t st);
 
+// ---- learned correction (vne_mlp.cu) ------------------------------------------------
+cudaError_t launch_spectral_sample(int count, const int* kind, const int* n, const float* a,
+                                   const int* ktop, const float* floor, const float* c,
+                                   const uint64_t* seeds, int m, int s, float* feat, float* target,
+                                   double* H_exact, double* H_low, double* totals,
+                                   cudaStream_t st);
+size_t mlp_workspace_floats(int B);
+cudaError_t mlp_forward(const float* th, const float* X, int B, float* y, float* ws, int* launches,
+                        cudaStream_t st);
+cudaError_t mlp_loss_grad(const float* th, const float* X, const float* t, const int* idx, int B,
+                          float* grad, double* loss, float* ws, int* launches, cudaStream_t st);
+cudaError_t mlp_train_step(float* th, float* am, float* av, int step, float lr, const float* X,
+                           const float* t, int64_t rows, int B, int64_t first, uint64_t perm_seed,
+                           int* idx, float* grad, double* loss, float* ws, int* launches,
+                           cudaStream_t st);
+// ws: 64 + mlp_workspace_floats(1) floats
+cudaError_t launch_learned(const double* mom, int m, int s, int64_t n, double* sc,
+                           const float* params, float* ws, int* launches, cudaStream_t st);
+
 // ---- combine (vne_combine.cu) ----------------------------------------------------
 // moments[k][j] for k = 0..m of the Chebyshev columns / Taylor columns, then
 // the FP64 estimates into sc.

@@ -38,7 +38,21 @@ def test_target_of_uniform_spectrum():
     n = 128
     p = np.full(n, 1.0 / n)
     assert abs(L.entropy(p) - np.log(n)) < 1e-13
-    assert abs(L.target(p, np.log(n) - 0.5) - 0.5 / np.log(n)) < 1e-13
+    assert abs(L.target(p, np.log(n) - 0.5, 2.0 / n) - 100 * 0.5 / 2.0) < 1e-11
+
+
+def test_target_is_the_truncation_error_over_n_u():
+    # with w_i = s exactly, H - H_m = -u sum_i e_m(p_i / u): the target is
+    # -100 * mean_i e_m(y_i) for any n with the same distribution of y
+    m, s = 16, 4
+    for n in (256, 4096):
+        y = (np.arange(n) + 0.5) / n  # the same distribution of y = p/u at both sizes
+        p = y / y.sum()
+        u = p.max() / y.max()
+        tot = s * np.polynomial.chebyshev.chebvander(2 * p / u - 1, m).sum(axis=0)
+        t = L.target(p, L.chebyshev_from_totals(tot, u, s), u)
+        e = y * np.log(y) - O.cheb_fm(y, 1.0, m)
+        assert abs(t - (-100.0 * e.mean())) < 1e-9 * max(1.0, abs(t))
 
 
 def test_gelu_values():
