@@ -11,7 +11,7 @@ FP64 combine, and the estimates copied back to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|bf16x3|f64]
                     [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7|
-                                lowrank_n8192_k64]
+                                lowrank_n8192_k64|learned_n8192]
                     [--impl reference]
 
 Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on the
@@ -85,6 +85,9 @@ def peak_value(d, *keys):
 
 def make_workload(name):
     w = dict(synth.WORKLOADS[name])
+    if w["kind"] == "learned":
+        R, p, _ = synth.dense_powerlaw(w["n"], w["k"], w["alpha"], w["floor"], w["seed"])
+        return w, R, p
     if w["kind"] == "lowrank":
         R, p, _ = synth.dense_lowrank(w["n"], w["k"], w["tau"], w["seed"])
         return w, R, p
@@ -180,6 +183,10 @@ def oracle_sample_time(w, R, s_sample):
     O.chebyshev_moments(Rop, G, u, m)
     if w["kind"] == "dense":
         O.taylor_terms(Rop, G, u, m)
+    if w["kind"] == "dense_cheb":
+        import oracle.learned as OL
+        theta = synth.mlp_init(1)
+        OL.forward(theta, np.zeros((1, OL.N_IN)))
     t2 = time.perf_counter()
     full = (t1 - t0) + (t2 - t1) * (s / s_sample)
     try:
@@ -187,7 +194,8 @@ def oracle_sample_time(w, R, s_sample):
         threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
     except Exception:
         threads = os.cpu_count() or 1
-    est = "Chebyshev + Taylor" if w["kind"] == "dense" else "Chebyshev"
+    est = {"dense": "Chebyshev + Taylor", "dense_cheb": "Chebyshev + network forward"}.get(
+        w["kind"], "Chebyshev")
     desc = (f"oracle (NumPy FP64) on the full n={n} matrix: {w['power_iters']} power-method "
             f"products + {est} recurrences, m={m}, on {s_sample} of the s={s} probes, "
             f"time scaled by s/{s_sample} for the recurrence part")
@@ -327,6 +335,131 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
         dist.destroy_process_group()
 
 
+LEARNED_METRIC = ("entropies/s (n=8192 density matrices through power method + Chebyshev m=16 "
+                  "on BF16 tensor cores, s=128 Gaussian probes, + learned correction)")
+
+
+def run_gpu_learned(args, w, Rh, p, world, rank, local, dev):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1801_01072_gb300 as vne
+    from paper_1801_01072_gb300 import learned
+
+    n, m, s = w["n"], w["m"], w["s"]
+    prec = args.precision if args.precision in ("bf16", "bf16x3", "f64", "f32") else "bf16"
+    Rd = torch.as_tensor(Rh).to(dev)
+    seed = w["seed"] + 1000 * rank
+    H_exact = float(-(p[p > 0] * np.log(p[p > 0])).sum())
+    # training (outside the timed region): sampled spectra, the library's kernels
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    data = learned.spectral_samples(synth.learned_sample_params(w["train_count"], 1), s=s,
+                                    device=local)
+    theta0 = torch.tensor(synth.mlp_init(1), dtype=torch.float32).to(dev)
+    theta, hist = learned.train(theta0, data["features"], data["target"],
+                                epochs=w["train_epochs"], batch=1024, lr=2e-3, report_every=1000)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del data
+
+    def step(R):
+        return learned.entropy_chebyshev_learned(R, theta, s=s, seed=seed, precision=prec,
+                                                 power_iters=w["power_iters"])
+
+    h = vne._handle(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        out = step(Rd)
+    torch.cuda.synchronize()
+    h.profile(True)
+    n_launch0 = h.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step(Rd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    n_launch = h.launch_count() - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = h.profile_read(0 if prec in ("bf16", "bf16x3") else 1)
+    h.profile(False)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    Rpin = torch.as_tensor(Rh).pin_memory()
+    step(Rpin)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 4)
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(Rpin)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) / e2e_steps * 1e3
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # the plain full-degree estimator on the same GPU: FP64, degree m_ref
+    torch.cuda.synchronize()
+    f0 = time.perf_counter()
+    ref = vne.entropy_chebyshev(Rd, w["m_ref"], s, seed=seed, probe="gaussian", precision="f64",
+                                power_iters=w["power_iters"], u_scale=1.05)
+    torch.cuda.synchronize()
+    f64_ms = (time.perf_counter() - f0) * 1e3
+    pk, pk_src = peaks()
+    flops = 2.0 * n * n * s * m * args.steps
+    achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+    peak = peak_value(pk, "bf16_tflops_sustained", "bf16_tflops") if prec.startswith("bf16") else None
+    roof = {"bound": "tensor" if peak else "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if (achieved and peak) else None,
+            "traffic": None, "kernel": "k_tc_step" if peak else "k_simt_step", "launches": k_n,
+            "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
+            "peak_source": pk_src + (" bf16 sustained" if peak else "")}
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        t_cpu, desc, threads = oracle_sample_time(dict(w, kind="dense_cheb"), Rh, args.cpu_probes)
+        cpu = {"value": 1.0 / t_cpu, "unit": "entropies/s", "cores": threads, "kind": "oracle",
+               "sample": desc}
+    value = world * args.steps / (ms_max / 1e3)
+    line = {
+        "metric": LEARNED_METRIC, "value": value, "unit": "entropies/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+        "data": "synthetic (seeded density matrix and sampled training spectra, no dataset)",
+        "config": {"workload": args.workload, "n": n, "m": m, "s": s, "probe": "gaussian",
+                   "power_iters": w["power_iters"], "precision": prec, "u_scale": 1.05,
+                   "input": "R FP64 resident in HBM",
+                   "l2": "inputs larger than L2 (R is %.0f MB)" % (Rh.nbytes / 1e6),
+                   "parallelism": f"independent matrices, {world} GPU(s)"},
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
+                "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": 200 * 8},
+        "gpu_launches": int(n_launch),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "training": {"spectra": w["train_count"], "epochs": w["train_epochs"],
+                     "seconds_incl_sampling": train_s, "final_loss": hist[-1][1] if hist else None},
+        "vs_plain_fp64": {"m": w["m_ref"], "ms": f64_ms, "speedup": f64_ms / (ms_max / args.steps),
+                          "rel_err_exact_plain_fp64": abs(ref.H - H_exact) / H_exact},
+        "estimates": {"H_learned": out.H, "H_plain_m16": out.H_plain, "H_exact": H_exact,
+                      "rel_err_exact_learned": abs(out.H - H_exact) / H_exact,
+                      "rel_err_exact_plain_m16": abs(out.H_plain - H_exact) / H_exact,
+                      "u": out.u},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -348,6 +481,8 @@ def run_gpu(args):
     w, Rh, p = make_workload(args.workload)
     if w["kind"] == "lowrank":
         return run_gpu_projection(args, w, Rh, p, world, rank, local, dev)
+    if w["kind"] == "learned":
+        return run_gpu_learned(args, w, Rh, p, world, rank, local, dev)
     dense = w["kind"] == "dense"
     n, m, s = w["n"], w["m"], w["s"]
     prec = args.precision if dense else "f32"
@@ -554,6 +689,8 @@ def run_reference(args):
     w, Rh, p = make_workload(args.workload)
     if w["kind"] == "lowrank":
         return run_reference_projection(args, w, Rh)
+    if w["kind"] == "learned":
+        w = dict(w, kind="dense_cheb")
     s_sample = args.ref_probes
     times = []
     for i in range(args.warmup + args.steps):
@@ -564,7 +701,8 @@ def run_reference(args):
     value = len(times) / tot
     line = {
         "impl": "reference",
-        "metric": "entropies/s (density matrices through power method + Chebyshev m=40 + "
+        "metric": LEARNED_METRIC if w["kind"] == "dense_cheb" else
+                  "entropies/s (density matrices through power method + Chebyshev m=40 + "
                   "Taylor m=40, s=128) at <=1e-3 rel. error vs the FP64 path on the same GPU"
                   if w["kind"] == "dense" else "entropies/s (banded Chebyshev m=30, s=64)",
         "value": value,

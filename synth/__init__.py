@@ -212,6 +212,12 @@ WORKLOADS = {
                                  probe="gaussian", power_iters=30),
     "band33_n1e7": dict(kind="band", n=10_000_000, half_bw=16, offdiag_scale=0.02,
                         seed=3, m=30, s=64, probe="rademacher", power_iters=30),
+    # the dense n = 8192 matrix through the degree-16 estimator plus the learned
+    # correction (trained on 100k sampled spectra, n = 1024..4096), against
+    # the plain degree-64 estimator
+    "learned_n8192": dict(kind="learned", n=8192, spectrum="powerlaw", k=2048, alpha=1.5,
+                          floor=1e-9, seed=2, m=16, s=128, probe="gaussian", power_iters=30,
+                          train_count=100000, train_epochs=20, m_ref=64),
     # rank-64 mixture for the random-projection estimator (Algorithm alg:EN)
     "lowrank_n8192_k64": dict(kind="lowrank", n=8192, k=64, tau=16.0, seed=4, s=256,
                               sketch="gaussian"),
