@@ -62,9 +62,10 @@ def mlp_forward(theta, X):
     import torch
 
     dev = X.device.index
+    X = X.contiguous()  # held until the call returns
     y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
     h = _handle(dev)
-    h.check(h.lib.vne_mlp_forward(h.h, _p(theta), _p(X.contiguous()), X.shape[0], _p(y),
+    h.check(h.lib.vne_mlp_forward(h.h, _p(theta), _p(X), X.shape[0], _p(y),
                                   _stream(dev, None)), "vne_mlp_forward")
     return y
 
@@ -73,12 +74,12 @@ def mlp_gradient(theta, X, target):
     import torch
 
     dev = X.device.index
+    X, target = X.contiguous(), target.contiguous()  # held until the call returns
     g = torch.empty(N_PARAMS, dtype=torch.float32, device=X.device)
     loss = C.c_double()
     h = _handle(dev)
-    h.check(h.lib.vne_mlp_gradient(h.h, _p(theta), _p(X.contiguous()), _p(target.contiguous()),
-                                   X.shape[0], _p(g), C.byref(loss), _stream(dev, None)),
-            "vne_mlp_gradient")
+    h.check(h.lib.vne_mlp_gradient(h.h, _p(theta), _p(X), _p(target), X.shape[0], _p(g),
+                                   C.byref(loss), _stream(dev, None)), "vne_mlp_gradient")
     return loss.value, g
 
 
@@ -91,6 +92,7 @@ def train(theta0, X, target, epochs: int = 20, batch: int = 1024, lr: float = 1e
 
     dev = X.device.index
     theta = theta0.detach().to(torch.float32).contiguous().clone()
+    X, target = X.contiguous(), target.contiguous()
     m = torch.zeros_like(theta)
     v = torch.zeros_like(theta)
     rows = X.shape[0]
