@@ -292,8 +292,10 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
     flops = 2.0 * n * n * s * args.steps
     achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
     peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == "f32" else 1.25
+    traffic = profiled_traffic("k_simt_step_f32_lowrank_n8192_k64.md", "vne_dense_simt.cu") \
+        if (prec == "f32" and args.workload == "lowrank_n8192_k64") else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
             "kernel": "k_simt_step", "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
             "peak_source": "derived: FP32 lanes x 2 x max SM clock" if prec == "f32"
             else "nominal FP64"}
