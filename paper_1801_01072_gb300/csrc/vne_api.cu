@@ -240,7 +240,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     int rows_per_tile0 = 256;
     if (mode != MODE_POWER) {
         if (dense && !tc) {
-            splitk = dense_simt_splitk(n, S, h->sm_count);
+            splitk = dense_simt_splitk(n, S, h->sm_count, f64 ? 8 : 4);
             ntiles = ntiles0 = (int)((n + 255) / 256);
         } else if (tc) {
             rows_per_tile0 = tc_tile_m();
@@ -532,7 +532,7 @@ vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int 
     Call c{h, st};
     const int64_t n = R.n;
     const int want = sizeof(T) == 8 ? VNE_F64 : VNE_F32;
-    const int splitk = dense_simt_splitk(n, s, h->sm_count);
+    const int splitk = dense_simt_splitk(n, s, h->sm_count, (int)sizeof(T));
     const int chunks = gram_chunks(n, s, h->sm_count);
     auto plan = [&](Bump& b, void** Rcopy, T** Rop, T** Pi, T** Zpart, T** Z, double** part,
                     double** C, double** W, double** de, double** ev, double** out) {

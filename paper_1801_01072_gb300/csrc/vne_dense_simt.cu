@@ -4,7 +4,7 @@
 // reference the mixed-precision tensor-core path is measured against.
 //
 // Layout: R row-major (ld), Y column blocks [S][n] (probe c contiguous).
-// Step kernel: 32 x 32 output tile, K split into `splitk` slices so that
+// FP64 step kernel: 32 x 32 output tile, K split into `splitk` slices so that
 // small problems still fill the GPU; partial products go to Zpart[split][S][n]
 // and the epilogue kernel sums them in split order (deterministic).
 #include "vne_common.cuh"
@@ -61,8 +61,93 @@ __global__ void __launch_bounds__(256) k_simt_step(const T* __restrict__ R, int6
         }
 }
 
-int dense_simt_splitk(int64_t n, int ncols, int sm_count) {
-    const int64_t tiles = ((n + SB_M - 1) / SB_M) * ((ncols + SB_N - 1) / SB_N);
+// FP32 step: 128 x 64 output tile, 8 x 4 outputs per thread from a
+// register tile (two float4 loads of R's column slice and one of Y's per k),
+// K staged 16 at a time.  blockIdx.x runs over the column tiles, so the CTAs
+// that share a 128-row block of R are launched together and R is fetched from
+// HBM about once (the other column tiles hit in L2).
+constexpr int FB_M = 128, FB_N = 64, FB_K = 16;
+
+__global__ void __launch_bounds__(256) k_simt_step_f32(const float* __restrict__ R, int64_t ld,
+                                                       int64_t n, const float* __restrict__ Y,
+                                                       float* __restrict__ Zpart, int S, int col0,
+                                                       int ncols, int64_t kchunk, int vec) {
+    __shared__ __align__(16) float As[FB_K][FB_M + 4];
+    __shared__ __align__(16) float Bs[FB_K][FB_N + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int c0 = col0 + blockIdx.x * FB_N;
+    const int64_t i0 = (int64_t)blockIdx.y * FB_M;
+    const int cend = col0 + ncols;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    int64_t ke = kb + kchunk;
+    if (ke > n) ke = n;
+    float acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const int ar = tid >> 1, ak = (tid & 1) * 8;   // A: row, first k of 8
+    const int bc = tid >> 2, bk = (tid & 3) * 4;   // B: column, first k of 4
+    const int64_t arow = i0 + ar;
+    const int bcol = c0 + bc;
+    for (int64_t k0 = kb; k0 < ke; k0 += FB_K) {
+        float a[8], bv[4];
+        if (vec && arow < n && k0 + ak + 8 <= ke) {
+            const float4 x = *reinterpret_cast<const float4*>(R + arow * ld + k0 + ak);
+            const float4 y = *reinterpret_cast<const float4*>(R + arow * ld + k0 + ak + 4);
+            a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+            a[4] = y.x; a[5] = y.y; a[6] = y.z; a[7] = y.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t k = k0 + ak + q;
+                a[q] = (arow < n && k < ke) ? R[arow * ld + k] : 0.f;
+            }
+        }
+        if (vec && bcol < cend && k0 + bk + 4 <= ke) {
+            const float4 y = *reinterpret_cast<const float4*>(Y + (int64_t)bcol * n + k0 + bk);
+            bv[0] = y.x; bv[1] = y.y; bv[2] = y.z; bv[3] = y.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t k = k0 + bk + q;
+                bv[q] = (bcol < cend && k < ke) ? Y[(int64_t)bcol * n + k] : 0.f;
+            }
+        }
+        __syncthreads();  // the previous slice has been consumed
+#pragma unroll
+        for (int q = 0; q < 8; ++q) As[ak + q][ar] = a[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Bs[bk + q][bc] = bv[q];
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < FB_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bw[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bw[c], acc[r][c]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int64_t i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        if (i >= n) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int col = c0 + tx * 4 + c;
+            if (col < cend) Zpart[((int64_t)blockIdx.z * S + col) * n + i] = acc[r][c];
+        }
+    }
+}
+
+int dense_simt_splitk(int64_t n, int ncols, int sm_count, int elt_bytes) {
+    const int64_t tm = elt_bytes == 4 ? FB_M : SB_M, tn = elt_bytes == 4 ? FB_N : SB_N;
+    const int64_t tiles = ((n + tm - 1) / tm) * ((ncols + tn - 1) / tn);
     const int64_t kblocks = (n + SB_K - 1) / SB_K;
     int64_t split = 1;
     while (tiles * split < 2 * (int64_t)sm_count && split * 2 <= kblocks && split < 16) split *= 2;
@@ -74,6 +159,16 @@ cudaError_t launch_dense_simt_step(const T* R, int64_t ld, int64_t n, const T* Y
                                    int S, int col0, int ncols, int splitk, cudaStream_t st) {
     const int64_t kblocks = (n + SB_K - 1) / SB_K;
     const int64_t kchunk = ((kblocks + splitk - 1) / splitk) * SB_K;
+    if (sizeof(T) == 4) {
+        const int vec = (ld % 4 == 0) && (n % 4 == 0) &&
+                        (reinterpret_cast<uintptr_t>(R) % 16 == 0) &&
+                        (reinterpret_cast<uintptr_t>(Yprev) % 16 == 0);
+        dim3 grid((unsigned)((ncols + FB_N - 1) / FB_N), (unsigned)((n + FB_M - 1) / FB_M),
+                  (unsigned)splitk);
+        k_simt_step_f32<<<grid, 256, 0, st>>>((const float*)R, ld, n, (const float*)Yprev,
+                                              (float*)Zpart, S, col0, ncols, kchunk, vec);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)((n + SB_M - 1) / SB_M), (unsigned)((ncols + SB_N - 1) / SB_N),
               (unsigned)splitk);
     k_simt_step<T><<<grid, 256, 0, st>>>(R, ld, n, Yprev, Zpart, S, col0, ncols, kchunk);

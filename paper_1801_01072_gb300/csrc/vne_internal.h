@@ -88,7 +88,7 @@ cudaError_t launch_dense_simt_epilogue(const T* Zpart, int splitk, const T* G, c
                                        const T* Yprev2, T* Ynew, int64_t n, int S, int s,
                                        StepCols cols, const double* sc, Partials P, int t,
                                        cudaStream_t st);
-int dense_simt_splitk(int64_t n, int ncols, int sm_count);
+int dense_simt_splitk(int64_t n, int ncols, int sm_count, int elt_bytes);
 
 // ---- banded recurrence (vne_dia.cu) --------------------------------------------
 template <typename T>

@@ -359,9 +359,10 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiag_cluster(const double* _
                                                                  double* __restrict__ d_out,
                                                                  double* __restrict__ e_out) {
     extern __shared__ double Wl[];
-    __shared__ double xb[2][kEigMaxN], pb[2][kEigMaxN];
+    __shared__ double xb[2][kEigMaxN], pb[2][kEigMaxN], vb[kEigMaxN], wb[kEigMaxN];
     __shared__ double part[2][2][kClusterMax];
     __shared__ double wsum[2][kEigWarps];
+    __shared__ double scal[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rank = (int)proj_cluster_rank(), C = (int)proj_cluster_size();
     const int rows_local = (N - rank + C - 1) / C;
@@ -391,30 +392,44 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiag_cluster(const double* _
             if (lane < C) st_peer_f64(&part[b][0][rank], (uint32_t)lane, t);
         }
         proj_cluster_sync();
-        double tail = 0.0;
-        for (int c = 0; c < C; ++c) tail += part[b][0][c];
-        const double x0 = xb[b][0];
-        if (k % C == rank && tid == 0) d_out[k] = Wl[(int64_t)(k / C) * N + k];
-        if (tail == 0.0) {  // column already reduced: same branch in every CTA
-            if (rank == 0 && tid == 0) e_out[k] = x0;
-            continue;
+        // the scalars of the column, once per CTA (FP64 instructions are
+        // expensive on this part: one thread computes, the block reads)
+        if (tid == 0) {
+            double tail = 0.0;
+            for (int c = 0; c < C; ++c) tail += part[b][0][c];
+            const double x0 = xb[b][0];
+            if (k % C == rank) d_out[k] = Wl[(int64_t)(k / C) * N + k];
+            double alpha = x0, v0 = 0.0, scale = 0.0;
+            if (tail != 0.0) {
+                const double xx = tail + x0 * x0;
+                alpha = x0 >= 0.0 ? -sqrt(xx) : sqrt(xx);
+                v0 = x0 - alpha;
+                scale = 1.0 / sqrt(tail + v0 * v0);
+            }
+            if (rank == 0) e_out[k] = alpha;
+            scal[0] = tail;
+            scal[1] = v0 * scale;
+            scal[2] = scale;
         }
-        const double xx = tail + x0 * x0;
-        const double alpha = x0 >= 0.0 ? -sqrt(xx) : sqrt(xx);
-        const double v0 = x0 - alpha;
-        const double scale = 1.0 / sqrt(tail + v0 * v0);
-        // 2. p = A_sub v on own rows (v_j = scale * (j ? x_j : x_0 - alpha)), v^T p
+        __syncthreads();
+        if (scal[0] == 0.0) continue;  // column already reduced: same branch in every CTA
+        // v once per column (every CTA keeps the whole vector)
+        {
+            const double scale = scal[2], v0s = scal[1];
+            for (int j = tid; j < m; j += blockDim.x) vb[j] = j ? xb[b][j] * scale : v0s;
+        }
+        __syncthreads();
+        // 2. p = A_sub v on own rows, v^T p
         double kpart = 0.0;
         for (int lr = warp; lr < rows_local; lr += kEigWarps) {
             const int r = rank + lr * C;
             if (r < o) continue;
             const double* row = Wl + (int64_t)lr * N + o;
             double acc = 0.0;
-            for (int j = lane; j < m; j += 32) acc = fma(row[j], (j ? xb[b][j] : v0) * scale, acc);
+            for (int j = lane; j < m; j += 32) acc = fma(row[j], vb[j], acc);
             acc = warp_sum(acc);
             if (lane < C) st_peer_f64(&pb[b][r - o], (uint32_t)lane, acc);
-            const int i = r - o;
-            kpart += (i ? xb[b][i] : v0) * scale * acc;
+            kpart += vb[r - o] * acc;
         }
         if (lane == 0) wsum[1][warp] = kpart;
         __syncthreads();
@@ -424,24 +439,28 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiag_cluster(const double* _
             if (lane < C) st_peer_f64(&part[b][1][rank], (uint32_t)lane, t);
         }
         proj_cluster_sync();
-        double K = 0.0;
-        for (int c = 0; c < C; ++c) K += part[b][1][c];
-        // 3. own rows -= 2 (v w^T + w v^T), w = p - K v
+        if (tid == 0) {
+            double K = 0.0;
+            for (int c = 0; c < C; ++c) K += part[b][1][c];
+            scal[3] = -K;
+        }
+        __syncthreads();
+        // w = p - K v, stored scaled by -2 so the update is two fused multiply-adds
+        {
+            const double mK = scal[3];
+            for (int j = tid; j < m; j += blockDim.x) wb[j] = -2.0 * fma(mK, vb[j], pb[b][j]);
+        }
+        __syncthreads();
+        // 3. own rows -= 2 (v w^T + w v^T)
         for (int lr = warp; lr < rows_local; lr += kEigWarps) {
             const int r = rank + lr * C;
             if (r < o) continue;
             double* row = Wl + (int64_t)lr * N + o;
             const int i = r - o;
-            const double vr = (i ? xb[b][i] : v0) * scale;
-            const double wr = pb[b][i] - K * vr;
-            for (int j = lane; j < m; j += 32) {
-                const double vj = (j ? xb[b][j] : v0) * scale;
-                const double wj = pb[b][j] - K * vj;
-                row[j] -= 2.0 * (vr * wj + wr * vj);
-            }
+            const double vr = vb[i], wr2 = wb[i];
+            for (int j = lane; j < m; j += 32) row[j] = fma(vr, wb[j], fma(wr2, vb[j], row[j]));
         }
         __syncwarp();  // next column's x is read by all lanes of the owning warp
-        if (rank == 0 && tid == 0) e_out[k] = alpha;
     }
     __syncthreads();
     if (tid == 0) {
@@ -490,12 +509,12 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
     return c;
 }
 
-// Multisection: each half-warp owns one eigenvalue (ascending rank j >= j0) and
-// splits its bracket [a, b] (count(a) <= j < count(b)) at 16 interior points
+// Multisection: each group of kMsLanes lanes owns one eigenvalue (ascending
+// rank j >= j0) and splits its bracket [a, b] (count(a) <= j < count(b)) at kMsLanes interior points
 // per round, keeping the sub-interval where the count passes j.  It stops
 // when the bracket is within 16 ulps of the spectrum's scale and stores the
 // midpoint at evals[N-1-j] (descending order).
-constexpr int kMsLanes = 16;
+constexpr int kMsLanes = 32;
 
 __global__ void __launch_bounds__(32) k_bisect_multi(const double* __restrict__ d_in,
                                                      const double* __restrict__ e_in, int N,
@@ -528,7 +547,8 @@ __global__ void __launch_bounds__(32) k_bisect_multi(const double* __restrict__ 
     const int g = lane / kMsLanes, l = lane % kMsLanes;
     const int j = j0 + blockIdx.x * (32 / kMsLanes) + g;
     const bool live = j < N;
-    const unsigned gmask = 0xFFFFu << (g * kMsLanes);
+    const unsigned gmask =
+        kMsLanes == 32 ? 0xFFFFFFFFu : (((1u << (kMsLanes & 31)) - 1u) << (g * kMsLanes));
     double a = lo - pad, b = hi + pad;
     for (int round = 0; round < 64; ++round) {
         if (!(b - a > tol)) break;  // uniform within the half-warp
@@ -618,7 +638,8 @@ cudaError_t launch_sym_eigvals(const double* A, int N, int top, double* Wg, doub
         if (r != cudaSuccess) return r;
     }
     // only the `top` largest eigenvalues: ascending ranks N-top .. N-1
-    k_bisect_multi<<<(top + 1) / 2, 32, 0, st>>>(d, e, N, N - top, evals);
+    k_bisect_multi<<<(top + 32 / kMsLanes - 1) / (32 / kMsLanes), 32, 0, st>>>(d, e, N, N - top,
+                                                                             evals);
     return cudaGetLastError();
 }
 
