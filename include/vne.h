@@ -67,7 +67,7 @@ enum { VNE_RADEMACHER = 0, VNE_GAUSSIAN = 1 };
 /* vne_matrix.memory */
 enum { VNE_MEM_DEVICE = 0, VNE_MEM_HOST = 1 };
 /* vne_suggest_m.method */
-enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1 };
+enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1, VNE_METHOD_BOTH = 2 };
 
 /* The density matrix R (eq. R1).
  *   n        : order of R (n >= 1).
@@ -154,6 +154,22 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
                             double* H_cheb, double* H_taylor,
                             double* moments_cheb, double* moments_taylor,
                             double* u_out, void* stream);
+
+/* Many density matrices of uneven sizes in one call (Algorithms 1a/1b with
+ * alg:power, applied to each).  Rs[i] (DEVICE memory, any layout and dtype a
+ * single call accepts) is estimated with the same parameters p; method is
+ * VNE_METHOD_CHEBYSHEV, VNE_METHOD_TAYLOR or VNE_METHOD_BOTH.  The matrices
+ * run concurrently on 8 streams of the handle, each with its own slice of a
+ * batch workspace.  use_graph != 0 captures the whole batch once as a CUDA
+ * graph and replays it while the matrices (pointers, sizes, layouts), p and
+ * method stay the same -- one graph launch per batch; a change recaptures.
+ * H_cheb / H_taylor / u_out: host arrays of count doubles (those of the
+ * estimators not run may be NULL; u_out may be NULL).  Returns the first
+ * failing status; a matrix that failed gets NaN.  Results equal the single
+ * calls' exactly.  Synchronises `stream`. */
+vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t count,
+                               const vne_params* p, int32_t method, int32_t use_graph,
+                               double* H_cheb, double* H_taylor, double* u_out, void* stream);
 
 /* Algorithm alg:power: p1~ = max_j x_t^T R x_t / x_t^T x_t over q = power_trials
  * start vectors in {+1,-1}^n after t = power_iters products (each iterate is

@@ -28,7 +28,7 @@ from . import _lib
 from ._lib import VneError
 
 __all__ = ["entropy_chebyshev", "entropy_taylor", "entropy_both", "lambda_max", "probe_block",
-           "entropy_projection", "sketch_block", "ProjectionResult",
+           "entropy_projection", "sketch_block", "ProjectionResult", "entropy_batched",
            "Handle", "Result", "BothResult", "VneError", "suggest_m", "load"]
 
 
@@ -223,6 +223,39 @@ def entropy_both(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
     h.check(st, "vne_entropy_both")
     del keep
     return BothResult(Hc.value, Ht.value, uo.value, mc, mt)
+
+
+def entropy_batched(Rs, m: int, s: int, seed: int = 0, probe: str = "rademacher",
+                    precision: str = "f64", method: str = "chebyshev", use_graph: bool = True,
+                    power_iters: int = 30, power_trials: int = 1, u_scale: float = 1.0,
+                    u: float | None = None, layouts=None, stream=None):
+    """Many density matrices (CUDA tensors, uneven sizes) in one call, run
+    concurrently and, with use_graph, replayed from one captured CUDA graph.
+    Returns (H_chebyshev, H_taylor, u) as float64 arrays (None for an
+    estimator not run)."""
+    layouts = layouts or ["dense"] * len(Rs)
+    mats, keep, dev = [], [], None
+    for R, lay in zip(Rs, layouts):
+        mat, k, d = _matrix(R, lay)
+        if not R.is_cuda:
+            raise ValueError("entropy_batched takes device tensors")
+        mats.append(mat)
+        keep.append(k)
+        dev = d if dev is None else dev
+    arr = (_lib.VneMatrix * len(mats))(*mats)
+    h = _handle(dev)
+    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, False)
+    meth = {"taylor": 0, "chebyshev": 1, "both": 2}[method]
+    n = len(mats)
+    hc = np.full(n, np.nan) if meth in (1, 2) else None
+    ht = np.full(n, np.nan) if meth in (0, 2) else None
+    uo = np.zeros(n)
+    st = h.lib.vne_entropy_batched(h.h, C.cast(arr, C.c_void_p), n, C.byref(p), meth,
+                                   1 if use_graph else 0, _dptr(hc), _dptr(ht), _dptr(uo),
+                                   _stream(dev, stream))
+    h.check(st, "vne_entropy_batched")
+    del keep
+    return hc, ht, uo
 
 
 def lambda_max(R, power_iters: int = 30, power_trials: int = 1, seed: int = 0,

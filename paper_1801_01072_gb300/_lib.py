@@ -57,6 +57,9 @@ SIGNATURES = [
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, _D, _D, C.c_void_p]),
     ("vne_entropy_both", C.c_int,
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, _D, _D, _D, _D, C.c_void_p]),
+    ("vne_entropy_batched", C.c_int,
+     [_H, C.c_void_p, C.c_int32, C.POINTER(VneParams), C.c_int32, C.c_int32, _D, _D, _D,
+      C.c_void_p]),
     ("vne_lambda_max", C.c_int, [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, C.c_void_p]),
     ("vne_lambda_max_static", C.c_int,
      [C.POINTER(VneMatrix), C.POINTER(VneParams), _D, C.c_void_p]),

@@ -37,6 +37,15 @@ struct vne_handle {
     size_t ev_used = 0;
     std::vector<ProfEvent> pending;
     int64_t launches = 0;
+    // batched calls
+    char* bws = nullptr;
+    size_t bws_bytes = 0;
+    double* bhost = nullptr;
+    size_t bhost_count = 0;
+    std::vector<cudaStream_t> bstreams;
+    std::vector<cudaEvent_t> bevents;  // [0] fork, [1] done, [2 + k] join of stream k
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_key = 0;
 };
 
 namespace {
@@ -52,6 +61,12 @@ struct Outputs {
     double* lam = nullptr;
     const float* mlp = nullptr;      // trained correction network (device), or NULL
     double* H_learned = nullptr;
+    // batched calls: measure the workspace only, or enqueue into a given
+    // workspace and pinned host slot without synchronising
+    int measure = 0;
+    size_t* measured = nullptr;
+    char* ws = nullptr;
+    double* host_slot = nullptr;
 };
 
 struct DeviceGuard {
@@ -163,6 +178,17 @@ void collect_profile(vne_handle* h) {
         }
     }
     h->pending.clear();
+}
+
+// Status of a finished call from its scalar block (copied to the host).
+vne_status slot_status(const double* hs, int check_trace) {
+    uint64_t flags;
+    std::memcpy(&flags, &hs[SC_FLAGS], sizeof(flags));
+    if (check_trace && !(std::fabs(hs[SC_TRACE] - 1.0) <= 1e-6)) return VNE_ERR_NOT_UNIT_TRACE;
+    if (flags & FLAG_TIMEOUT) return VNE_ERR_TIMEOUT;
+    if (flags & FLAG_BAD_INTERVAL) return VNE_ERR_BAD_INTERVAL;
+    if (flags & FLAG_NONFINITE) return VNE_ERR_NONFINITE;
+    return VNE_OK;
 }
 
 vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
@@ -311,9 +337,17 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         Bump b0(nullptr);
         plan(b0, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
              &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
-        vs = ensure_ws(h, b0.off + 4096);
-        if (vs != VNE_OK) return vs;
-        Bump b1(h->ws);
+        if (out.measure) {
+            *out.measured = b0.off + 4096;
+            return VNE_OK;
+        }
+        char* base = out.ws;
+        if (!base) {
+            vs = ensure_ws(h, b0.off + 4096);
+            if (vs != VNE_OK) return vs;
+            base = h->ws;
+        }
+        Bump b1(base);
         plan(b1, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
              &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
     }
@@ -490,8 +524,13 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     }
 
     // ---- results ----
-    if (c.ok()) c.chk(cudaMemcpyAsync(h->host_sc, sc, SC_COUNT * sizeof(double),
+    double* host_slot = out.host_slot ? out.host_slot : h->host_sc;
+    if (c.ok()) c.chk(cudaMemcpyAsync(host_slot, sc, SC_COUNT * sizeof(double),
                                       cudaMemcpyDeviceToHost, c.st));
+    if (out.host_slot) {  // batched: the caller synchronises and reads the slot
+        if (!c.ok()) return map_err(h, c.err);
+        return VNE_OK;
+    }
     if (c.ok() && out.mom_cheb && has_cheb)
         c.chk(cudaMemcpyAsync(out.mom_cheb, mom_c, (size_t)(m + 1) * s * sizeof(double),
                               cudaMemcpyDeviceToHost, c.st));
@@ -508,12 +547,8 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     }
     collect_profile(h);
     const double* hs = h->host_sc;
-    uint64_t flags;
-    std::memcpy(&flags, &hs[SC_FLAGS], sizeof(flags));
-    if (p->check_trace && !(std::fabs(hs[SC_TRACE] - 1.0) <= 1e-6)) return VNE_ERR_NOT_UNIT_TRACE;
-    if (flags & FLAG_TIMEOUT) return VNE_ERR_TIMEOUT;
-    if (flags & FLAG_BAD_INTERVAL) return VNE_ERR_BAD_INTERVAL;
-    if (flags & FLAG_NONFINITE) return VNE_ERR_NONFINITE;
+    vne_status fs = slot_status(hs, p->check_trace);
+    if (fs != VNE_OK) return fs;
     if (out.H_cheb) *out.H_cheb = hs[SC_H_CHEB];
     if (out.H_taylor) *out.H_taylor = hs[SC_H_TAYLOR];
     if (out.u) *out.u = hs[SC_U];
@@ -644,6 +679,11 @@ void vne_destroy(vne_handle* h) {
     cudaDeviceSynchronize();
     if (h->ws) cudaFree(h->ws);
     if (h->host_sc) cudaFreeHost(h->host_sc);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (cudaStream_t st : h->bstreams) cudaStreamDestroy(st);
+    for (cudaEvent_t e : h->bevents) cudaEventDestroy(e);
+    if (h->bws) cudaFree(h->bws);
+    if (h->bhost) cudaFreeHost(h->bhost);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
 }
@@ -679,6 +719,192 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
     o.mom_taylor = moments_taylor;
     o.u = u_out;
     return run(h, R, p, MODE_BOTH, o, stream);
+}
+
+namespace {
+uint64_t mix(uint64_t hsh, uint64_t v) { return splitmix_out(hsh ^ v, 0x51ull); }
+
+vne_status batch_resources(vne_handle* h, size_t ws_bytes, size_t count) {
+    const int K = 8;
+    while ((int)h->bstreams.size() < K) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return VNE_ERR_CUDA;
+        }
+        h->bstreams.push_back(st);
+    }
+    while ((int)h->bevents.size() < K + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return VNE_ERR_CUDA;
+        }
+        h->bevents.push_back(e);
+    }
+    if (ws_bytes > h->bws_bytes || count > h->bhost_count) {
+        cudaDeviceSynchronize();
+        if (h->graph) {  // the graph holds the old addresses
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+    }
+    if (ws_bytes > h->bws_bytes) {
+        if (h->bws) cudaFree(h->bws);
+        h->bws = nullptr;
+        h->bws_bytes = 0;
+        if (cudaMalloc((void**)&h->bws, ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            h->bws = nullptr;
+            return VNE_ERR_OOM;
+        }
+        h->bws_bytes = ws_bytes;
+    }
+    if (count > h->bhost_count) {
+        if (h->bhost) cudaFreeHost(h->bhost);
+        h->bhost = nullptr;
+        h->bhost_count = 0;
+        if (cudaMallocHost((void**)&h->bhost, count * SC_COUNT * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            h->bhost = nullptr;
+            return VNE_ERR_OOM;
+        }
+        h->bhost_count = count;
+    }
+    return VNE_OK;
+}
+}  // namespace
+
+vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t count,
+                               const vne_params* p, int32_t method, int32_t use_graph,
+                               double* H_cheb, double* H_taylor, double* u_out, void* stream) {
+    if (!h || !Rs || !p || count < 1) return VNE_ERR_INVALID_ARG;
+    if (method != VNE_METHOD_TAYLOR && method != VNE_METHOD_CHEBYSHEV && method != VNE_METHOD_BOTH)
+        return VNE_ERR_INVALID_ARG;
+    const int mode = method == VNE_METHOD_TAYLOR ? MODE_TAYLOR
+                     : method == VNE_METHOD_CHEBYSHEV ? MODE_CHEB : MODE_BOTH;
+    if ((mode & MODE_CHEB) && !H_cheb) return VNE_ERR_INVALID_ARG;
+    if ((mode & MODE_TAYLOR) && !H_taylor) return VNE_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (Rs[i].memory != VNE_MEM_DEVICE) return VNE_ERR_UNSUPPORTED;
+    DeviceGuard guard(h->device);
+    // workspace of every matrix (the same plan as a single call)
+    std::vector<size_t> off((size_t)count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        Outputs o;
+        o.measure = 1;
+        size_t bytes = 0;
+        o.measured = &bytes;
+        vne_status vs = run(h, &Rs[i], p, mode, o, nullptr);
+        if (vs != VNE_OK) return vs;
+        off[i + 1] = off[i] + round_up((int64_t)bytes, 256);
+    }
+    vne_status vs = batch_resources(h, off[count], (size_t)count);
+    if (vs != VNE_OK) return vs;
+    const int K = 8;
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t origin = h->bstreams[0];
+    const int saved_prof = h->prof_on;
+    h->prof_on = 0;
+    // every matrix on one of the K streams, forked from and joined into origin
+    auto enqueue = [&]() -> vne_status {
+        cudaError_t e = cudaEventRecord(h->bevents[0], origin);
+        for (int k = 1; k < K && e == cudaSuccess; ++k)
+            e = cudaStreamWaitEvent(h->bstreams[k], h->bevents[0], 0);
+        if (e != cudaSuccess) return map_err(h, e);
+        for (int i = 0; i < count; ++i) {
+            Outputs o;
+            o.ws = h->bws + off[i];
+            o.host_slot = h->bhost + (size_t)i * SC_COUNT;
+            vne_status r = run(h, &Rs[i], p, mode, o, h->bstreams[i % K]);
+            if (r != VNE_OK) return r;
+        }
+        for (int k = 1; k < K && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(h->bevents[2 + k], h->bstreams[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, h->bevents[2 + k], 0);
+        }
+        return map_err(h, e);
+    };
+    cudaError_t e = cudaEventRecord(h->bevents[1], user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, h->bevents[1], 0);
+    if (e != cudaSuccess) {
+        h->prof_on = saved_prof;
+        return map_err(h, e);
+    }
+    if (use_graph) {
+        uint64_t key = mix(0x9E3779B97F4A7C15ull, (uint64_t)count);
+        for (int i = 0; i < count; ++i) {
+            key = mix(key, (uint64_t)Rs[i].n);
+            key = mix(key, (uint64_t)(uintptr_t)Rs[i].data);
+            key = mix(key, (uint64_t)Rs[i].ld);
+            key = mix(key, ((uint64_t)Rs[i].layout << 32) ^ ((uint64_t)Rs[i].dtype << 16) ^
+                               (uint64_t)Rs[i].n_diags);
+        }
+        const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
+        for (size_t b = 0; b < sizeof(vne_params); ++b) key = mix(key, pb[b] + (b << 8));
+        key = mix(key, (uint64_t)method);
+        key = mix(key, (uint64_t)(uintptr_t)h->bws);
+        key = mix(key, (uint64_t)(uintptr_t)h->bhost);
+        if (!h->graph || key != h->graph_key) {
+            if (h->graph) {
+                cudaGraphExecDestroy(h->graph);
+                h->graph = nullptr;
+            }
+            e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                h->prof_on = saved_prof;
+                return map_err(h, e);
+            }
+            vne_status r = enqueue();
+            cudaGraph_t g = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(origin, &g);
+            if (r != VNE_OK || ee != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                h->prof_on = saved_prof;
+                return r != VNE_OK ? r : map_err(h, ee);
+            }
+            ee = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ee != cudaSuccess) {
+                h->graph = nullptr;
+                h->prof_on = saved_prof;
+                return map_err(h, ee);
+            }
+            h->graph_key = key;
+        }
+        e = cudaGraphLaunch(h->graph, origin);
+        if (e != cudaSuccess) {
+            h->prof_on = saved_prof;
+            return map_err(h, e);
+        }
+    } else {
+        vne_status r = enqueue();
+        if (r != VNE_OK) {
+            h->prof_on = saved_prof;
+            cudaStreamSynchronize(origin);
+            return r;
+        }
+    }
+    h->prof_on = saved_prof;
+    e = cudaEventRecord(h->bevents[1], origin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->bevents[1], 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(user);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return map_err(h, e);
+    }
+    vne_status first = VNE_OK;
+    for (int i = 0; i < count; ++i) {
+        const double* hs = h->bhost + (size_t)i * SC_COUNT;
+        vne_status fs = slot_status(hs, p->check_trace);
+        if (fs != VNE_OK && first == VNE_OK) first = fs;
+        const double nan = std::nan("");
+        if (H_cheb && (mode & MODE_CHEB)) H_cheb[i] = fs == VNE_OK ? hs[SC_H_CHEB] : nan;
+        if (H_taylor && (mode & MODE_TAYLOR)) H_taylor[i] = fs == VNE_OK ? hs[SC_H_TAYLOR] : nan;
+        if (u_out) u_out[i] = hs[SC_U];
+    }
+    return first;
 }
 
 vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,

@@ -1,0 +1,78 @@
+"""Batched estimates of uneven matrices (one call, concurrent streams, CUDA
+graph replay) against the single calls and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+vne = pytest.importorskip("paper_1801_01072_gb300")
+
+
+def mats(sizes, seed0=0):
+    out = []
+    for i, n in enumerate(sizes):
+        R, p, _ = synth.dense_exp(n, max(4.0, n / 10), seed=seed0 + i)
+        out.append((torch.tensor(R).cuda(), R, p))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("precision,method", [("f64", "both"), ("bf16", "chebyshev"),
+                                              ("f32", "taylor")])
+def test_batched_equals_single_calls(use_graph, precision, method):
+    sizes = [64, 200, 333, 97, 512, 130, 256, 40, 300, 150]
+    ms = mats(sizes)
+    m, s, seed = 12, 16, 9
+    hc, ht, u = vne.entropy_batched([t for t, _, _ in ms], m, s, seed=seed, probe="gaussian",
+                                    precision=precision, method=method, use_graph=use_graph)
+    kw = dict(seed=seed, probe="gaussian", precision=precision)
+    for i, (t, R, p) in enumerate(ms):
+        # the same estimator set as the batch (the fused column count decides
+        # the tiling, hence the rounding order)
+        if method == "both":
+            one = vne.entropy_both(t, m, s, **kw)
+            assert (hc[i], ht[i], u[i]) == (one.H_chebyshev, one.H_taylor, one.u), i
+        elif method == "chebyshev":
+            one = vne.entropy_chebyshev(t, m, s, **kw)
+            assert (hc[i], u[i]) == (one.H, one.u), (i, hc[i], one.H)
+        else:
+            one = vne.entropy_taylor(t, m, s, **kw)
+            assert (ht[i], u[i]) == (one.H, one.u), (i, ht[i], one.H)
+    if precision == "f64":
+        for i, (t, R, p) in enumerate(ms[:3]):
+            ref = O.estimate(R, "chebyshev", m, s, seed, "gaussian", power_iters=30)
+            assert abs(hc[i] - ref["H"]) <= 1e-10 * abs(ref["H"])
+
+
+def test_graph_replay_and_recapture():
+    ms = mats([128, 256, 77], seed0=20)
+    ts = [t for t, _, _ in ms]
+    a = vne.entropy_batched(ts, 10, 8, seed=3, precision="bf16")[0]
+    b = vne.entropy_batched(ts, 10, 8, seed=3, precision="bf16")[0]   # replay
+    assert np.array_equal(a, b)
+    c = vne.entropy_batched(ts, 10, 8, seed=4, precision="bf16")[0]   # new key: recapture
+    d = vne.entropy_batched(ts, 10, 8, seed=4, precision="bf16", use_graph=False)[0]
+    assert np.array_equal(c, d) and not np.array_equal(a, c)
+    # different matrices with the same shapes: recaptured, not stale
+    ms2 = mats([128, 256, 77], seed0=40)
+    e = vne.entropy_batched([t for t, _, _ in ms2], 10, 8, seed=3, precision="bf16")[0]
+    f = [vne.entropy_chebyshev(t, 10, 8, seed=3, precision="bf16").H for t, _, _ in ms2]
+    assert np.array_equal(e, np.array(f))
+
+
+def test_batched_mixed_layouts_and_errors():
+    n = 3000
+    vals = synth.band_diag_dominant(n, 16, 0.02, seed=2, dtype=np.float64)
+    band = torch.tensor(vals).cuda()
+    dense, _, _ = mats([180])[0]
+    hc, _, _ = vne.entropy_batched([dense, band], 8, 6, seed=1, precision="f64",
+                                   layouts=["dense", "dia"])
+    one = vne.entropy_chebyshev(band, 8, 6, seed=1, precision="f64", layout="dia")
+    assert hc[1] == one.H
+    with pytest.raises(vne.VneError):
+        vne.entropy_batched([dense, band], 8, 6, seed=1, precision="bf16",
+                            layouts=["dense", "dia"])   # banded BF16 is not supported
