@@ -11,7 +11,7 @@ FP64 combine, and the estimates copied back to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|bf16x3|f64]
                     [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7|
-                                lowrank_n8192_k64|learned_n8192]
+                                lowrank_n8192_k64|learned_n8192|batched256]
                     [--impl reference]
 
 Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on the
@@ -85,6 +85,8 @@ def peak_value(d, *keys):
 
 def make_workload(name):
     w = dict(synth.WORKLOADS[name])
+    if w["kind"] == "batched":
+        return w, synth.batched_specs(w["count"], w["seed"], w["n_lo"], w["n_hi"]), None
     if w["kind"] == "learned":
         R, p, _ = synth.dense_powerlaw(w["n"], w["k"], w["alpha"], w["floor"], w["seed"])
         return w, R, p
@@ -462,6 +464,169 @@ def run_gpu_learned(args, w, Rh, p, world, rank, local, dev):
         dist.destroy_process_group()
 
 
+BATCH_METRIC = ("entropies/s (256 dense density matrices, n log-uniform in [256, 4096], "
+                "power method + Chebyshev m=24 on BF16 tensor cores, s=32, one batched call)")
+
+
+def batch_matrices(specs, dev):
+    """R_b = Q diag(p) Q^T with Q the (sign-fixed) QR factor of a seeded
+    Gaussian matrix, built on the GPU (FP32 QR, FP64 result)."""
+    import torch
+
+    mats = []
+    for n, p, seed in specs:
+        g = torch.Generator(device=dev).manual_seed(seed)
+        A = torch.randn(n, n, generator=g, device=dev, dtype=torch.float32)
+        Q, Rr = torch.linalg.qr(A)
+        Q = (Q * torch.sign(torch.diagonal(Rr))[None, :]).double()
+        R = (Q * torch.tensor(p, device=dev)[None, :]) @ Q.T
+        mats.append((0.5 * (R + R.T)).contiguous())
+    return mats
+
+
+def run_gpu_batched(args, w, specs, world, rank, local, dev):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1801_01072_gb300 as vne
+
+    m, s = w["m"], w["s"]
+    prec = args.precision if args.precision in ("bf16", "bf16x3", "f64", "f32") else "bf16"
+    seed = w["seed"] + 1000 * rank
+    t0 = time.perf_counter()
+    mats = batch_matrices(specs, dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    # autotune the tensor-core tile per size bucket (the largest matrix of each)
+    tuned = {}
+    if prec.startswith("bf16"):
+        buckets = {}
+        for i, (n, _, _) in enumerate(specs):
+            b = int(np.ceil(np.log2(max(1, -(-n // 128)))))
+            if b not in buckets or n > specs[buckets[b]][0]:
+                buckets[b] = i
+        for b, i in sorted(buckets.items()):
+            shape, us = vne.autotune(mats[i], m, s, precision=prec, method="chebyshev",
+                                     seed=seed, probe=w["probe"], power_iters=w["power_iters"])
+            tuned[str(specs[i][0])] = {"shape": list(shape), "us_per_step": us}
+
+    def step():
+        return vne.entropy_batched(mats, m, s, seed=seed, probe=w["probe"], precision=prec,
+                                   method="chebyshev", use_graph=True,
+                                   power_iters=w["power_iters"])
+
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize()
+    h = vne._handle(local)
+    n_launch0 = h.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    # the same matrices one call at a time (no batching, no graph)
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    single = [vne.entropy_chebyshev(R, m, s, seed=seed, probe=w["probe"], precision=prec,
+                                    power_iters=w["power_iters"]).H for R in mats]
+    torch.cuda.synchronize()
+    single_ms = (time.perf_counter() - s0) * 1e3
+    # end to end: the matrices copied from pinned host memory inside the step
+    host = [R.cpu().pin_memory() for R in mats]
+    h2d = int(sum(x.numel() * 8 for x in host))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(2):
+        for dst, src in zip(mats, host):
+            dst.copy_(src, non_blocking=True)
+        step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) / 2 * 1e3
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    H_exact = np.array([float(-(p * np.log(p)).sum()) for _, p, _ in specs])
+    rel = np.abs(out[0] - H_exact) / H_exact
+    flops = sum(2.0 * n * n * s * m for n, _, _ in specs)
+    pk, pk_src = peaks()
+    peak = peak_value(pk, "bf16_tflops_sustained", "bf16_tflops") if prec.startswith("bf16") else None
+    achieved = flops / (ms_max / args.steps / 1e3) / 1e12
+    roof = {"bound": "tensor" if peak else "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+            "kernel": "whole batch (recurrence flops over the whole step, lower bound for k_tc_step)",
+            "peak_source": pk_src + (" bf16 sustained" if peak else "")}
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        import oracle as O
+        from oracle import rng
+        idx = list(range(0, len(specs), max(1, len(specs) // 4)))[:4]
+        c0 = time.perf_counter()
+        tot_full = 0.0
+        for i in idx:
+            n, p, sd = specs[i]
+            R = mats[i].cpu().numpy()
+            lam, _ = O.power_method(R, rng.power_start(n, 1, seed), w["power_iters"])
+            ta = time.perf_counter()
+            G = rng.probes(n, s, seed, w["probe"])[:, :4]
+            O.chebyshev_moments(R, G, O.interval_u(lam, 1.0), m)
+            tb = time.perf_counter()
+            tot_full += (ta - c0) + (tb - ta) * s / 4
+            c0 = time.perf_counter()
+        per = tot_full / len(idx)
+        try:
+            from threadpoolctl import threadpool_info
+            threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+        except Exception:
+            threads = os.cpu_count() or 1
+        cpu = {"value": 1.0 / per, "unit": "entropies/s", "cores": threads, "kind": "oracle",
+               "sample": f"oracle (NumPy FP64) on {len(idx)} of the {len(specs)} matrices: power "
+                         f"method + Chebyshev m={m} on 4 of the s={s} probes, recurrence time "
+                         f"scaled by s/4, mean per matrix"}
+    line = {
+        "metric": BATCH_METRIC, "value": world * len(specs) * args.steps / (ms_max / 1e3),
+        "unit": "entropies/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec,
+        "data": "synthetic (seeded uneven density matrices built on the GPU, no dataset)",
+        "config": {"workload": args.workload, "count": len(specs), "n_range": [w["n_lo"], w["n_hi"]],
+                   "n_total": int(sum(n for n, _, _ in specs)), "m": m, "s": s,
+                   "probe": w["probe"], "power_iters": w["power_iters"], "precision": prec,
+                   "input": "FP64 matrices resident in HBM (%.1f GB)" % (h2d / 1e9),
+                   "l2": "inputs larger than L2", "graph": "one CUDA graph launch per step",
+                   "parallelism": f"8 streams inside the graph, {world} GPU(s)"},
+        "e2e": {"value": world * len(specs) * 1e3 / e2e_ms, "unit": "entropies/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(specs) * 200 * 8},
+        "gpu_launches": int(h.launch_count() - n_launch0),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "vs_single_calls": {"ms": single_ms, "speedup": single_ms / (ms_max / args.steps)},
+        "autotuned": tuned,
+        "matrix_generation_s": gen_s,
+        "estimates": {"rel_err_exact_mean": float(rel.mean()), "rel_err_exact_max": float(rel.max()),
+                      "same_as_single_calls": bool(np.array_equal(out[0], np.array(single)))},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -485,6 +650,8 @@ def run_gpu(args):
         return run_gpu_projection(args, w, Rh, p, world, rank, local, dev)
     if w["kind"] == "learned":
         return run_gpu_learned(args, w, Rh, p, world, rank, local, dev)
+    if w["kind"] == "batched":
+        return run_gpu_batched(args, w, Rh, world, rank, local, dev)
     dense = w["kind"] == "dense"
     n, m, s = w["n"], w["m"], w["s"]
     prec = args.precision if dense else "f32"
@@ -684,11 +851,55 @@ def run_reference_projection(args, w, Rh):
                 "d2h_bytes_per_step": 0}}))
 
 
+def run_reference_batched(args, w, specs):
+    import oracle as O
+    from oracle import rng
+
+    idx = list(range(0, len(specs), max(1, len(specs) // 4)))[:4]
+    mats = [synth.dense_density(synth.haar_orthogonal(specs[i][0], specs[i][2]), specs[i][1])
+            for i in idx]
+    times = []
+    for it in range(args.warmup + args.steps):
+        tot = 0.0
+        for R, i in zip(mats, idx):
+            n = specs[i][0]
+            t0 = time.perf_counter()
+            lam, _ = O.power_method(R, rng.power_start(n, 1, w["seed"]), w["power_iters"])
+            t1 = time.perf_counter()
+            G = rng.probes(n, w["s"], w["seed"], w["probe"])[:, :4]
+            O.chebyshev_moments(R, G, O.interval_u(lam, 1.0), w["m"])
+            tot += (t1 - t0) + (time.perf_counter() - t1) * w["s"] / 4
+        if it >= args.warmup:
+            times.append(tot / len(idx))
+    value = len(times) / sum(times)
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count() or 1
+    desc = (f"oracle (NumPy FP64) on {len(idx)} of the {len(specs)} matrices: power method + "
+            f"Chebyshev m={w['m']} on 4 of the s={w['s']} probes, recurrence scaled by s/4, "
+            f"mean time per matrix")
+    print(json.dumps({
+        "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": "entropies/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded uneven density matrices, no dataset)",
+        "config": {"workload": args.workload, "count": len(specs), "m": w["m"], "s": w["s"]},
+        "cpu_baseline": {"value": value, "unit": "entropies/s", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "entropies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w, Rh, p = make_workload(args.workload)
+    if w["kind"] == "batched":
+        return run_reference_batched(args, w, Rh)
     if w["kind"] == "lowrank":
         return run_reference_projection(args, w, Rh)
     if w["kind"] == "learned":

@@ -171,6 +171,20 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
                                const vne_params* p, int32_t method, int32_t use_graph,
                                double* H_cheb, double* H_taylor, double* u_out, void* stream);
 
+/* Autotuner of the tensor-core step (BF16 / BF16X3 dense paths; not in the
+ * paper).  Times every candidate tile shape -- BN probe columns per CTA (the
+ * widest MMA, half of it, 128), clusters of 1 or 2 CTAs along M or N, and the
+ * K split over a CTA pair -- on full estimator calls of R with p and method
+ * (CUDA events around the tensor-core steps), and keeps the fastest for the
+ * size bucket of R (ceil log2 of its 128-row tiles) and of the step's column
+ * count.  The choice is process-wide and applies to later calls (single and
+ * batched) whose sizes fall in the same buckets; the environment variable
+ * VNE_TC_TILE="BN,CM,CN[,ksplit]" still overrides it.
+ *   shape_out: host, 4 ints (BN, CM, CN, ksplit) or NULL;
+ *   us_out:    host, the chosen shape's microseconds per step, or NULL. */
+vne_status vne_tc_autotune(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                           int32_t method, int32_t* shape_out, double* us_out, void* stream);
+
 /* Algorithm alg:power: p1~ = max_j x_t^T R x_t / x_t^T x_t over q = power_trials
  * start vectors in {+1,-1}^n after t = power_iters products (each iterate is
  * divided by its 2-norm, which leaves the Rayleigh quotient unchanged).  The

@@ -28,7 +28,7 @@ from . import _lib
 from ._lib import VneError
 
 __all__ = ["entropy_chebyshev", "entropy_taylor", "entropy_both", "lambda_max", "probe_block",
-           "entropy_projection", "sketch_block", "ProjectionResult", "entropy_batched",
+           "entropy_projection", "sketch_block", "ProjectionResult", "entropy_batched", "autotune",
            "Handle", "Result", "BothResult", "VneError", "suggest_m", "load"]
 
 
@@ -256,6 +256,23 @@ def entropy_batched(Rs, m: int, s: int, seed: int = 0, probe: str = "rademacher"
     h.check(st, "vne_entropy_batched")
     del keep
     return hc, ht, uo
+
+
+def autotune(R, m: int, s: int, precision: str = "bf16", method: str = "chebyshev",
+             seed: int = 0, probe: str = "gaussian", power_iters: int = 30, stream=None):
+    """Time the tensor-core tile shapes on R and keep the fastest for R's size
+    bucket.  Returns ((BN, CM, CN, ksplit), microseconds per step)."""
+    mat, keep, dev = _matrix(R, "dense")
+    h = _handle(dev)
+    p = _params(m, s, seed, probe, precision, power_iters, 1, 1.0, None, False)
+    shape = (C.c_int32 * 4)()
+    us = C.c_double()
+    meth = {"taylor": 0, "chebyshev": 1, "both": 2}[method]
+    st = h.lib.vne_tc_autotune(h.h, C.byref(mat), C.byref(p), meth, C.cast(shape, C.c_void_p),
+                               C.byref(us), _stream(dev, stream))
+    h.check(st, "vne_tc_autotune")
+    del keep
+    return tuple(shape), us.value
 
 
 def lambda_max(R, power_iters: int = 30, power_trials: int = 1, seed: int = 0,

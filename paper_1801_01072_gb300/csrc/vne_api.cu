@@ -907,6 +907,57 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     return first;
 }
 
+vne_status vne_tc_autotune(vne_handle* h, const vne_matrix* R, const vne_params* p,
+                           int32_t method, int32_t* shape_out, double* us_out, void* stream) {
+    if (!h || !R || !p) return VNE_ERR_INVALID_ARG;
+    if (R->layout != VNE_DENSE || p->precision < VNE_PREC_BF16) return VNE_ERR_UNSUPPORTED;
+    if (method != VNE_METHOD_TAYLOR && method != VNE_METHOD_CHEBYSHEV && method != VNE_METHOD_BOTH)
+        return VNE_ERR_INVALID_ARG;
+    const int mode = method == VNE_METHOD_TAYLOR ? MODE_TAYLOR
+                     : method == VNE_METHOD_CHEBYSHEV ? MODE_CHEB : MODE_BOTH;
+    const int S = mode == MODE_BOTH ? 2 * p->s : p->s;
+    int cand[16][4];
+    const int cnt = tc_candidates(R->n, S, cand, 16);
+    if (cnt < 1) return VNE_ERR_UNSUPPORTED;
+    const int saved_prof = h->prof_on;
+    h->prof_on = 1;
+    int best = -1;
+    double best_us = 0.0;
+    vne_status st = VNE_OK;
+    for (int i = 0; i < cnt && st == VNE_OK; ++i) {
+        tc_set_tuned(R->n, S, cand[i][0], cand[i][1], cand[i][2], cand[i][3]);
+        Outputs o;
+        double H = 0.0, H2 = 0.0;
+        o.H_cheb = &H;
+        o.H_taylor = &H2;
+        st = run(h, R, p, mode, o, stream);  // warm-up (tensor maps, caches)
+        if (st != VNE_OK) break;
+        h->prof_ms[0] = 0.0;
+        h->prof_n[0] = 0;
+        st = run(h, R, p, mode, o, stream);
+        if (st != VNE_OK) break;
+        const double us = h->prof_n[0] > 0 ? h->prof_ms[0] * 1e3 / (double)h->prof_n[0] : 1e30;
+        if (best < 0 || us < best_us) {
+            best = i;
+            best_us = us;
+        }
+    }
+    h->prof_on = saved_prof;
+    for (int k = 0; k < 4; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+    }
+    if (st != VNE_OK || best < 0) {
+        tc_set_tuned(R->n, S, 0, 0, 0, 0);
+        return st != VNE_OK ? st : VNE_ERR_UNSUPPORTED;
+    }
+    tc_set_tuned(R->n, S, cand[best][0], cand[best][1], cand[best][2], cand[best][3]);
+    if (shape_out)
+        for (int k = 0; k < 4; ++k) shape_out[k] = cand[best][k];
+    if (us_out) *us_out = best_us;
+    return VNE_OK;
+}
+
 vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,
                           double* lam_out, void* stream) {
     if (!lam_out) return VNE_ERR_INVALID_ARG;

@@ -119,6 +119,9 @@ struct TcStep {
     int t;
 };
 cudaError_t launch_tc_step(const TcStep& a, int sm_count, cudaStream_t st);
+// autotuner: set (BN = 0 clears) the shape of n x ncols steps; candidates
+int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit);
+int tc_candidates(int64_t n, int ncols, int (*out)[4], int max);
 int tc_tile_m();
 int tc_tile_k();
 

@@ -28,6 +28,8 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <algorithm>
+
 #include "vne_common.cuh"
 #include "vne_internal.h"
 #include "vne_ptx.cuh"
@@ -610,8 +612,77 @@ static int pick_cluster(int tiles, int want) {
     return c < 1 ? 1 : c;
 }
 
+static bool shape_ok(const TcShape& t, int ncols, int mtiles, int nkb) {
+    if (!(t.BN >= 32 && t.BN <= 256 && t.BN % 32 == 0 && t.CM >= 1 && t.CN >= 1 &&
+          t.CM * t.CN <= 8 && (t.BN / t.CM) % 8 == 0 && (TC_BM / t.CN) % 8 == 0))
+        return false;
+    if (!(t.ksplit == 1 || (t.ksplit == 2 && t.CM == 1 && t.CN == 1 && t.BN % 64 == 0 && nkb >= 2)))
+        return false;
+    const int ntn = (ncols + t.BN - 1) / t.BN;
+    return mtiles % t.CM == 0 && ntn % t.CN == 0;
+}
+
+// Shapes chosen by the autotuner, per bucket of row tiles (ceil log2) and of
+// step columns (<= 32, 64, 128, 256, 512, more); process-wide.
+struct TunedShape {
+    int valid;
+    TcShape sh;
+};
+static TunedShape g_tuned[16][6];
+
+static int rows_bucket(int mtiles) {
+    int b = 0;
+    while ((1 << b) < mtiles && b < 15) ++b;
+    return b;
+}
+static int cols_bucket(int ncols) {
+    return ncols <= 32 ? 0 : ncols <= 64 ? 1 : ncols <= 128 ? 2 : ncols <= 256 ? 3
+                                                            : ncols <= 512 ? 4 : 5;
+}
+
+int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit) {
+    const int mtiles = (int)((n + TC_BM - 1) / TC_BM);
+    TunedShape& e = g_tuned[rows_bucket(mtiles)][cols_bucket(ncols)];
+    if (BN == 0) {
+        e.valid = 0;
+        return 0;
+    }
+    TcShape t{BN, (ncols + BN - 1) / BN, CM, CN, ksplit};
+    const int nkb = (int)((n + TC_BK - 1) / TC_BK);
+    if (!shape_ok(t, ncols, mtiles, nkb)) return -1;
+    e.sh = t;
+    e.valid = 1;
+    return 0;
+}
+
+// Candidate shapes for n x ncols steps: column tiles of one or two MMAs'
+// width, clusters of 1, 2 (along M or N), K split over a CTA pair.
+int tc_candidates(int64_t n, int ncols, int (*out)[4], int max) {
+    const int mtiles = (int)((n + TC_BM - 1) / TC_BM);
+    const int nkb = (int)((n + TC_BK - 1) / TC_BK);
+    const int wide = std::min(256, (ncols + 31) / 32 * 32);
+    const int bns[3] = {wide, std::max(32, (wide / 2 + 31) / 32 * 32), 128};
+    const int cl[4][3] = {{1, 1, 1}, {1, 1, 2}, {2, 1, 1}, {1, 2, 1}};
+    int cnt = 0;
+    for (int bi = 0; bi < 3; ++bi) {
+        if (bi > 0 && bns[bi] == bns[0]) continue;
+        if (bi == 2 && bns[2] == bns[1]) continue;
+        for (int ci = 0; ci < 4 && cnt < max; ++ci) {
+            TcShape t{bns[bi], (ncols + bns[bi] - 1) / bns[bi], cl[ci][0], cl[ci][1], cl[ci][2]};
+            if (!shape_ok(t, ncols, mtiles, nkb)) continue;
+            out[cnt][0] = t.BN;
+            out[cnt][1] = t.CM;
+            out[cnt][2] = t.CN;
+            out[cnt][3] = t.ksplit;
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
 // Default: the widest tile (BN up to 256 columns, the largest N of one MMA);
-// when that leaves most SMs idle, a CTA pair splits K (ksplit = 2).
+// when that leaves most SMs idle, a CTA pair splits K (ksplit = 2).  A shape
+// set by the autotuner for this bucket comes first; VNE_TC_TILE overrides both.
 static TcShape choose_shape(int ncols, int mtiles, int nkb, int sm_count) {
     TcShape sh;
     const int ntn = (ncols + 255) / 256;
@@ -630,11 +701,15 @@ static TcShape choose_shape(int ncols, int mtiles, int nkb, int sm_count) {
             if (got < 4) o_ks = 1;
         }
     }
-    if (o_bn >= 32 && o_bn <= 256 && o_bn % 32 == 0 && o_cm >= 1 && o_cn >= 1 &&
-        o_cm * o_cn <= 8 && (o_bn / o_cm) % 8 == 0 && (TC_BM / o_cn) % 8 == 0 &&
-        (o_ks == 1 || (o_ks == 2 && o_cm == 1 && o_cn == 1 && o_bn % 64 == 0 && nkb >= 2))) {
+    const TunedShape& tu = g_tuned[rows_bucket(mtiles)][cols_bucket(ncols)];
+    if (tu.valid) {
+        TcShape t = tu.sh;
+        t.ntn = (ncols + t.BN - 1) / t.BN;
+        if (shape_ok(t, ncols, mtiles, nkb)) sh = t;
+    }
+    if (o_bn > 0) {
         TcShape t{o_bn, (ncols + o_bn - 1) / o_bn, o_cm, o_cn, o_ks};
-        if (mtiles % t.CM == 0 && t.ntn % t.CN == 0) sh = t;
+        if (shape_ok(t, ncols, mtiles, nkb)) sh = t;
     }
     return sh;
 }

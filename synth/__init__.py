@@ -32,6 +32,7 @@ __all__ = [
     "dense_powerlaw",
     "orthonormal_columns",
     "dense_lowrank",
+    "batched_specs",
     "training_spectrum",
     "learned_sample_params",
     "mlp_init",
@@ -113,6 +114,19 @@ def dense_lowrank(n: int = 8192, k: int = 64, tau: float = 16.0, seed: int = 4):
     psi = orthonormal_columns(n, k, seed)
     p = spectrum_exponential(k, tau)
     return dense_density(psi, p), p, psi
+
+
+def batched_specs(count: int, seed: int, n_lo: int = 256, n_hi: int = 4096):
+    """Sizes and spectra of a batch of uneven dense density matrices: n
+    log-uniform in [n_lo, n_hi], p_i ~ exp(-i/tau) with tau ~ U(10, n/4), and a
+    seed for each matrix's Haar eigenvectors.  Returns a list of (n, p, seed)."""
+    r = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(np.exp(r.uniform(np.log(n_lo), np.log(n_hi))))
+        tau = r.uniform(10.0, n / 4.0)
+        out.append((n, spectrum_exponential(n, tau), int(r.integers(1, 2 ** 31))))
+    return out
 
 
 def training_spectrum(kind: int, n: int, a: float, ktop: int, floor: float) -> np.ndarray:
@@ -218,6 +232,9 @@ WORKLOADS = {
     "learned_n8192": dict(kind="learned", n=8192, spectrum="powerlaw", k=2048, alpha=1.5,
                           floor=1e-9, seed=2, m=16, s=128, probe="gaussian", power_iters=30,
                           train_count=100000, train_epochs=20, m_ref=64),
+    # 256 uneven dense matrices in one batched call (one CUDA graph launch)
+    "batched256": dict(kind="batched", count=256, n_lo=256, n_hi=4096, seed=5, m=24, s=32,
+                       probe="gaussian", power_iters=30),
     # rank-64 mixture for the random-projection estimator (Algorithm alg:EN)
     "lowrank_n8192_k64": dict(kind="lowrank", n=8192, k=64, tau=16.0, seed=4, s=256,
                               sketch="gaussian"),

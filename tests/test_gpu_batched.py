@@ -76,3 +76,15 @@ def test_batched_mixed_layouts_and_errors():
     with pytest.raises(vne.VneError):
         vne.entropy_batched([dense, band], 8, 6, seed=1, precision="bf16",
                             layouts=["dense", "dia"])   # banded BF16 is not supported
+
+
+def test_autotune_picks_a_candidate_and_results_hold():
+    t, R, p = mats([1024], seed0=60)[0]
+    shape, us = vne.autotune(t, 10, 32, precision="bf16", method="chebyshev", seed=2)
+    BN, CM, CN, ks = shape
+    assert BN % 32 == 0 and 32 <= BN <= 256 and CM * CN <= 8 and ks in (1, 2) and us > 0
+    res = vne.entropy_chebyshev(t, 10, 32, seed=2, probe="gaussian", precision="bf16")
+    from oracle import rng
+    G = rng.probes(1024, 32, 2, "gaussian")
+    ref = O.chebyshev_estimate_from_moments(O.chebyshev_moments(R, G, res.u, 10), res.u)
+    assert abs(res.H - ref) <= 1e-3 * abs(ref)
