@@ -32,6 +32,7 @@ __all__ = [
     "dense_powerlaw",
     "orthonormal_columns",
     "dense_lowrank",
+    "hermitian_density",
     "batched_specs",
     "training_spectrum",
     "learned_sample_params",
@@ -114,6 +115,18 @@ def dense_lowrank(n: int = 8192, k: int = 64, tau: float = 16.0, seed: int = 4):
     psi = orthonormal_columns(n, k, seed)
     p = spectrum_exponential(k, tau)
     return dense_density(psi, p), p, psi
+
+
+def hermitian_density(n: int, p: np.ndarray, seed: int) -> np.ndarray:
+    """Complex Hermitian density matrix R = U diag(p) U^H, U the sign-fixed Q of
+    a seeded complex Ginibre matrix (Haar unitary); complex128, row-major."""
+    r = np.random.default_rng(seed)
+    a = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) / np.sqrt(2.0)
+    q, rr = np.linalg.qr(a)
+    d = np.diag(rr)
+    q = q * (d / np.abs(d))[None, :]
+    R = (q * np.asarray(p, dtype=np.float64)[None, :]) @ q.conj().T
+    return np.ascontiguousarray(0.5 * (R + R.conj().T))
 
 
 def batched_specs(count: int, seed: int, n_lo: int = 256, n_hi: int = 4096):
