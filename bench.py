@@ -11,7 +11,7 @@ FP64 combine, and the estimates copied back to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|bf16x3|f64]
                     [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7|
-                                lowrank_n8192_k64|learned_n8192|batched256]
+                                lowrank_n8192_k64|learned_n8192|batched256|hermitian_n5000]
                     [--impl reference]
 
 Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on the
@@ -85,6 +85,8 @@ def peak_value(d, *keys):
 
 def make_workload(name):
     w = dict(synth.WORKLOADS[name])
+    if w["kind"] == "hermitian":
+        return w, None, synth.spectrum_exponential(w["n"], w["tau"])
     if w["kind"] == "batched":
         return w, synth.batched_specs(w["count"], w["seed"], w["n_lo"], w["n_hi"]), None
     if w["kind"] == "learned":
@@ -634,6 +636,144 @@ def run_gpu_batched(args, w, specs, world, rank, local, dev):
         dist.destroy_process_group()
 
 
+HERM_METRIC = ("entropies/s (5000 x 5000 complex Hermitian density matrices, Algorithms "
+               "alg1a_complex + alg1b_complex, m=10, s=100, u=1, BF16 tensor cores)")
+
+
+def hermitian_matrix(w, dev):
+    """R = U diag(p) U^H with U the (phase-fixed) QR factor of a seeded complex
+    Gaussian matrix, built on the GPU (complex64 QR, complex128 result)."""
+    import torch
+
+    n = w["n"]
+    p = synth.spectrum_exponential(n, w["tau"])
+    g = torch.Generator(device=dev).manual_seed(w["seed"])
+    A = torch.complex(torch.randn(n, n, generator=g, device=dev),
+                      torch.randn(n, n, generator=g, device=dev))
+    Q, Rr = torch.linalg.qr(A)
+    d = torch.diagonal(Rr)
+    Q = (Q * (d / d.abs())[None, :]).to(torch.complex128)
+    R = (Q * torch.tensor(p, device=dev, dtype=torch.float64)[None, :]) @ Q.conj().T
+    return (0.5 * (R + R.conj().T)).contiguous(), p
+
+
+def run_gpu_hermitian(args, w, p, world, rank, local, dev):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1801_01072_gb300 as vne
+
+    n, m, s = w["n"], w["m"], w["s"]
+    prec = args.precision if args.precision in ("bf16", "bf16x3", "f64", "f32") else "bf16"
+    Rd, p = hermitian_matrix(w, dev)
+    seed = w["seed"] + 1000 * rank
+
+    def step(R):
+        return vne.entropy_both(R, m, s, seed=seed, probe="gaussian", precision=prec)
+
+    h = vne._handle(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        out = step(Rd)
+    torch.cuda.synchronize()
+    h.profile(True)
+    n_launch0 = h.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step(Rd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    n_launch = h.launch_count() - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    tc = prec.startswith("bf16")
+    k_ms, k_n = h.profile_read(0 if tc else 1)
+    h.profile(False)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    Rpin = Rd.cpu().pin_memory()
+    step(Rpin)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 4)
+    for _ in range(e2e_steps):
+        step(Rpin)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) / e2e_steps * 1e3
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    rel = None
+    if prec != "f64" and not args.skip_f64_check:
+        ref = vne.entropy_both(Rd, m, s, seed=seed, probe="gaussian", precision="f64")
+        rel = {"chebyshev": abs(out.H_chebyshev - ref.H_chebyshev) / abs(ref.H_chebyshev),
+               "taylor": abs(out.H_taylor - ref.H_taylor) / abs(ref.H_taylor)}
+    H_exact = float(-(p * np.log(p)).sum())
+    pk, pk_src = peaks()
+    # the embedding is 2n x 2n: 2 (2n)^2 flops per probe column and step
+    cols = 2 * s * m + s
+    flops = 2.0 * (2 * n) ** 2 * cols * args.steps
+    achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
+    peak = peak_value(pk, "bf16_tflops_sustained", "bf16_tflops") if tc else None
+    roof = {"bound": "tensor" if tc else "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if (achieved and peak) else None,
+            "traffic": None, "kernel": "k_tc_step" if tc else "k_simt_step", "launches": k_n,
+            "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
+            "peak_source": pk_src + (" bf16 sustained" if tc else "")}
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        import oracle.hermitian as OH
+        from oracle import rng
+        Rh = Rd.cpu().numpy()
+        sp = 4
+        G = rng.gaussian(n, s, seed)[:, :sp]
+        c0 = time.perf_counter()
+        OH.chebyshev_moments_complex(Rh, G, 1.0, m)
+        OH.taylor_terms_complex(Rh, G, 1.0, m)
+        t_cpu = (time.perf_counter() - c0) * s / sp
+        try:
+            from threadpoolctl import threadpool_info
+            threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+        except Exception:
+            threads = os.cpu_count() or 1
+        cpu = {"value": 1.0 / t_cpu, "unit": "entropies/s", "cores": threads, "kind": "oracle",
+               "sample": f"oracle (NumPy complex128) Chebyshev + Taylor recurrences m={m} on "
+                         f"{sp} of the s={s} probes of the full matrix, scaled by s/{sp}"}
+    line = {
+        "metric": HERM_METRIC, "value": world * args.steps / (ms_max / 1e3),
+        "unit": "entropies/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec,
+        "data": "synthetic (seeded complex density matrix built on the GPU, no dataset)",
+        "config": {"workload": args.workload, "n": n, "m": m, "s": s, "probe": "gaussian",
+                   "u": 1.0, "precision": prec, "input": "R complex128 resident in HBM (%.0f MB)"
+                   % (n * n * 16 / 1e6), "l2": "inputs larger than L2",
+                   "parallelism": f"independent matrices, {world} GPU(s)"},
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
+                "h2d_bytes_per_step": n * n * 16, "d2h_bytes_per_step": 200 * 8},
+        "gpu_launches": int(n_launch),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "rel_err_vs_f64": rel,
+        "estimates": {"H_chebyshev": out.H_chebyshev, "H_taylor": out.H_taylor,
+                      "H_exact": H_exact},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -659,6 +799,8 @@ def run_gpu(args):
         return run_gpu_learned(args, w, Rh, p, world, rank, local, dev)
     if w["kind"] == "batched":
         return run_gpu_batched(args, w, Rh, world, rank, local, dev)
+    if w["kind"] == "hermitian":
+        return run_gpu_hermitian(args, w, p, world, rank, local, dev)
     dense = w["kind"] == "dense"
     n, m, s = w["n"], w["m"], w["s"]
     prec = args.precision if dense else "f32"
@@ -900,6 +1042,42 @@ def run_reference_batched(args, w, specs):
                 "d2h_bytes_per_step": 0}}))
 
 
+def run_reference_hermitian(args, w, p):
+    import oracle.hermitian as OH
+    from oracle import rng
+
+    n, m, s = w["n"], w["m"], w["s"]
+    R = synth.hermitian_density(n, p, w["seed"])
+    sp = 2
+    G = rng.gaussian(n, s, w["seed"])[:, :sp]
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        OH.chebyshev_moments_complex(R, G, 1.0, m)
+        OH.taylor_terms_complex(R, G, 1.0, m)
+        if it >= args.warmup:
+            times.append((time.perf_counter() - t0) * s / sp)
+    value = len(times) / sum(times)
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count() or 1
+    desc = (f"oracle (NumPy complex128) Chebyshev + Taylor recurrences m={m} on {sp} of the "
+            f"s={s} probes of the full n={n} matrix, scaled by s/{sp}")
+    print(json.dumps({
+        "impl": "reference", "metric": HERM_METRIC, "value": value, "unit": "entropies/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded complex density matrix, no dataset)",
+        "config": {"workload": args.workload, "n": n, "m": m, "s": s, "u": 1.0},
+        "cpu_baseline": {"value": value, "unit": "entropies/s", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "entropies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -907,6 +1085,8 @@ def run_reference(args):
     w, Rh, p = make_workload(args.workload)
     if w["kind"] == "batched":
         return run_reference_batched(args, w, Rh)
+    if w["kind"] == "hermitian":
+        return run_reference_hermitian(args, w, p)
     if w["kind"] == "lowrank":
         return run_reference_projection(args, w, Rh)
     if w["kind"] == "learned":

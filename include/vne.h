@@ -51,8 +51,10 @@ typedef enum vne_status {
 
 /* vne_matrix.layout */
 enum { VNE_DENSE = 0, VNE_DIA = 1 };
-/* vne_matrix.dtype: storage type of the matrix entries */
-enum { VNE_F64 = 0, VNE_F32 = 1 };
+/* vne_matrix.dtype: storage type of the matrix entries.  The complex types
+ * hold a Hermitian R (Section 4) as interleaved (real, imaginary) pairs, dense
+ * layout only; ld counts complex entries. */
+enum { VNE_F64 = 0, VNE_F32 = 1, VNE_C128 = 2, VNE_C64 = 3 };
 /* vne_params.precision: arithmetic of the R.Y products of the recurrence
  *   F64     : FP64 operands, FP64 accumulation (dense and banded)
  *   F32     : FP32 operands, FP32 accumulation (dense and banded)
@@ -77,7 +79,13 @@ enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1, VNE_METHOD_BOTH = 2 };
  *                           0..n_diags-1, entry R[i, i+d] at data[d*ld + i] for
  *                           i < n-d (the rest of each row is ignored); the lower
  *                           triangle is implied by symmetry.  ld >= n.
- *   dtype    : VNE_F64 or VNE_F32.
+ *   dtype    : VNE_F64 or VNE_F32; VNE_C128 / VNE_C64 for a complex Hermitian R
+ *              (dense).  A Hermitian R = B + iC runs Algorithms alg1a_complex /
+ *              alg1b_complex (Section 4): real probes g_j, estimates of
+ *              g^T Re[f(R)] g, and u = 1 (the printed bound) unless u_override
+ *              is given; the products act on the real 2n x 2n embedding
+ *              [[B, -C], [C, B]] with probes [g_j; 0], which gives the same
+ *              quadratic forms.  check_trace tests sum_i Re R_ii.
  *   data     : pointer to the entries (device, or host if memory == VNE_MEM_HOST).
  *   memory   : VNE_MEM_DEVICE or VNE_MEM_HOST. */
 typedef struct vne_matrix {

@@ -12,7 +12,8 @@ is no CPU fallback.
     lam = vne.lambda_max(R)                                     # Algorithm alg:power
     pr = vne.entropy_projection(R, k=64, s=256, sketch="gaussian")  # Algorithm alg:EN
 
-``R`` is a dense (n, n) tensor (row-major) or, with ``layout="dia"``, the
+``R`` is a dense (n, n) tensor (row-major; complex128/complex64 for a
+Hermitian R, Section 4) or, with ``layout="dia"``, the
 (D, n) band storage ``vals[d, i] = R[i, i + d]`` of a symmetric banded R.
 It may live on the GPU (device pointer) or in host memory (the call then
 copies it itself).
@@ -122,8 +123,8 @@ def _matrix(R, layout: str):
         R = torch.as_tensor(np.ascontiguousarray(R))
     if R.dim() != 2:
         raise ValueError("R must be 2-D")
-    if R.dtype not in (torch.float64, torch.float32):
-        raise ValueError("R must be float64 or float32")
+    if R.dtype not in (torch.float64, torch.float32, torch.complex128, torch.complex64):
+        raise ValueError("R must be float64, float32, complex128 or complex64")
     if R.stride(1) != 1:
         R = R.contiguous()
     mat = _lib.VneMatrix()
@@ -139,7 +140,8 @@ def _matrix(R, layout: str):
         mat.n_diags = R.shape[0]
     else:
         raise ValueError(layout)
-    mat.dtype = _lib.F64 if R.dtype == torch.float64 else _lib.F32
+    mat.dtype = {torch.float64: _lib.F64, torch.float32: _lib.F32, torch.complex128: _lib.C128,
+                 torch.complex64: _lib.C64}[R.dtype]
     mat.data = R.data_ptr()
     mat.ld = R.stride(0)
     mat.memory = _lib.MEM_DEVICE if R.is_cuda else _lib.MEM_HOST

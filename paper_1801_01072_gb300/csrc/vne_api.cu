@@ -166,7 +166,10 @@ vne_status ensure_ws(vne_handle* h, size_t bytes) {
     return VNE_OK;
 }
 
-size_t elt_size(int dtype) { return dtype == VNE_F64 ? 8 : 4; }
+size_t elt_size(int dtype) {
+    return dtype == VNE_C128 ? 16 : (dtype == VNE_F64 || dtype == VNE_C64) ? 8 : 4;
+}
+bool is_complex(int dtype) { return dtype == VNE_C128 || dtype == VNE_C64; }
 
 // Adds the event pairs recorded during a finished call to the per-kind totals.
 void collect_profile(vne_handle* h) {
@@ -195,9 +198,11 @@ vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
     if (!R || !p) return VNE_ERR_INVALID_ARG;
     if (R->n < 1 || !R->data) return VNE_ERR_INVALID_ARG;
     if (R->layout != VNE_DENSE && R->layout != VNE_DIA) return VNE_ERR_INVALID_ARG;
-    if (R->dtype != VNE_F64 && R->dtype != VNE_F32) return VNE_ERR_INVALID_ARG;
+    if (R->dtype != VNE_F64 && R->dtype != VNE_F32 && !is_complex(R->dtype))
+        return VNE_ERR_INVALID_ARG;
     if (R->memory != VNE_MEM_DEVICE && R->memory != VNE_MEM_HOST) return VNE_ERR_INVALID_ARG;
     if (R->ld < R->n) return VNE_ERR_INVALID_ARG;
+    if (is_complex(R->dtype) && R->layout != VNE_DENSE) return VNE_ERR_UNSUPPORTED;
     if (R->layout == VNE_DIA) {
         if (R->n_diags < 1) return VNE_ERR_INVALID_ARG;
         if (dia_supported_halfbw(R->n_diags) < 0) return VNE_ERR_UNSUPPORTED;
@@ -241,7 +246,10 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     Call c{h, (cudaStream_t)stream};
 
     const vne_matrix R = *Rin;
-    const int64_t n = R.n;
+    // A Hermitian R (complex dtype, Section 4) runs as its real 2n x 2n
+    // embedding [[B, -C], [C, B]] with probes [g; 0] and u = 1 unless given.
+    const bool cplx = is_complex(R.dtype);
+    const int64_t n = cplx ? 2 * R.n : R.n;
     const bool dense = R.layout == VNE_DENSE;
     const int prec = p->precision;
     const bool tc = dense && prec >= VNE_PREC_BF16;
@@ -253,7 +261,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     const int m = mode == MODE_POWER ? 0 : p->m;
     const int S = mode == MODE_BOTH ? 2 * s : s;
     const int q = p->power_trials < 1 ? 1 : p->power_trials;
-    const bool do_power = !(p->u_override > 0.0);
+    const bool do_power = !(p->u_override > 0.0) && (!cplx || mode == MODE_POWER);
     const double u_scale = p->u_scale > 0.0 ? p->u_scale : 1.0;
     const int T_steps = mode == MODE_POWER ? 0 : (has_tay ? m + 1 : m);
     const int D = dense ? 0 : R.n_diags;
@@ -295,7 +303,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         *ppart = b.take<double>((size_t)std::max(power_blocks, 256) * 3 * q);
         *Rcopy = nullptr;
         if (R.memory == VNE_MEM_HOST)
-            *Rcopy = b.take<char>((size_t)(dense ? n : D) * R.ld * elt_size(R.dtype));
+            *Rcopy = b.take<char>((size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype));
         *Rop = nullptr;
         *Rhi = *Rlo = nullptr;
         if (tc) {
@@ -304,6 +312,9 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         } else {
             const int want = f64 ? VNE_F64 : VNE_F32;
             if (R.dtype != want) *Rop = b.take<char>((size_t)(dense ? n * n : (int64_t)D * n) * vt);
+        }
+        if (tc && cplx) {  // the embedding, FP32, before the bf16 split
+            *Rop = b.take<char>((size_t)n * n * 4);
         }
         const size_t xs = tc ? 4 : vt;
         *x0 = b.take<char>((size_t)n * q * xs);
@@ -360,16 +371,24 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     // ---- matrix to the device, trace check ----
     const void* Rdata = R.data;
     if (R.memory == VNE_MEM_HOST) {
-        const size_t bytes = (size_t)(dense ? n : D) * R.ld * elt_size(R.dtype);
+        const size_t bytes = (size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype);
         c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
         Rdata = Rcopy;
     }
-    if (p->check_trace) c.launched(launch_trace(Rdata, R.layout, R.dtype, n, R.ld, ppart, counter, sc, c.st));
+    if (p->check_trace)
+        c.launched(launch_trace(Rdata, R.layout, R.dtype, R.n, R.ld, ppart, counter, sc, c.st));
 
     // ---- operands ----
     const void* Rk = Rdata;  // operand of the SIMT / DIA / power kernels
     int64_t ldr = R.ld;
-    if (tc) {
+    if (cplx) {
+        const int edt = (f64 && !tc) ? VNE_F64 : VNE_F32;
+        c.launched(launch_hermitian_embed(Rdata, R.dtype, R.n, R.ld, Rop, edt, c.st));
+        Rk = Rop;
+        ldr = n;
+        if (tc)
+            c.launched(launch_dense_convert_bf16(Rop, VNE_F32, n, n, Rhi, Rlo, rows_pad, ldk, c.st));
+    } else if (tc) {
         c.launched(launch_dense_convert_bf16(Rdata, R.dtype, n, R.ld, Rhi, Rlo, rows_pad, ldk, c.st));
     } else if (Rop) {
         if (dense) {
@@ -404,7 +423,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             std::swap(xa, xb);
         }
     } else {
-        c.launched(launch_set_u(sc, p->u_override, c.st));
+        c.launched(launch_set_u(sc, p->u_override > 0.0 ? p->u_override : 1.0, c.st));
     }
 
     // ---- probes, recurrence, combine ----
@@ -422,11 +441,13 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         if (dense) {
             if (f64)
                 c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, nullptr, 0,
-                                                     n, S, s, p->probe, p->seed, P, 256, c.st));
+                                                     n, S, s, p->probe, p->seed, P, 256, c.st,
+                                                     R.n));
             else
                 c.launched(launch_dense_init<float>((float*)G, (float*)Yb0, sh_hi[0],
                                                     x3 ? sh_lo[0] : nullptr, ldk, n, S, s,
-                                                    p->probe, p->seed, P, rows_per_tile0, c.st));
+                                                    p->probe, p->seed, P, rows_per_tile0, c.st,
+                                                    R.n));
         } else {
             const int Wd = (s + 63) / 64;
             if (f64)

@@ -36,10 +36,12 @@ struct StepCols {
 cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint64_t seed,
                                    cudaStream_t st);
 // Dense layout [column][row] with row stride n (master) / ldk (bf16 shadows).
+// Rows i < probe_n draw counter j*probe_n + i; rows probe_n <= i < n are zero
+// (the lower half of the probes [g; 0] of a Hermitian embedding).
 template <typename T>
 cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                              int rows_per_tile, cudaStream_t st);
+                              int rows_per_tile, cudaStream_t st, int64_t probe_n);
 // Banded layout [row][column] (row stride S).  Rademacher probes are packed
 // as bits (bit j%64 of word j/64 of row i set when g_j[i] = -1; W words per
 // row); Gaussian probes are stored as values G[i*s + j].
@@ -58,6 +60,10 @@ cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n,
                                       int64_t ldk, cudaStream_t st);
 cudaError_t launch_dia_convert(const void* src, int src_dtype, int64_t n, int64_t ld, int D,
                                void* dst, int dst_dtype, cudaStream_t st);
+// [[B, -C], [C, B]] of the Hermitian R = B + iC (complex dtype 2 or 3, n x n,
+// ld complex elements) into dst (2n x 2n, ld 2n, FP64 if dst_dtype 0 else FP32)
+cudaError_t launch_hermitian_embed(const void* src, int cdtype, int64_t n, int64_t ld, void* dst,
+                                   int dst_dtype, cudaStream_t st);
 cudaError_t launch_trace(const void* R, int layout, int dtype, int64_t n, int64_t ld,
                          double* partial, unsigned int* counter, double* sc, cudaStream_t st);
 cudaError_t launch_set_u(double* sc, double u, cudaStream_t st);

@@ -5,8 +5,41 @@
 
 namespace vne {
 
+// dtype 0 FP64, 1 FP32, 2 complex FP64, 3 complex FP32 (interleaved): the
+// real part of entry idx.
 __device__ __forceinline__ double load_entry(const void* src, int dtype, int64_t idx) {
-    return dtype == 0 ? ((const double*)src)[idx] : (double)((const float*)src)[idx];
+    switch (dtype) {
+        case 0: return ((const double*)src)[idx];
+        case 1: return (double)((const float*)src)[idx];
+        case 2: return ((const double*)src)[2 * idx];
+        default: return (double)((const float*)src)[2 * idx];
+    }
+}
+
+// Real symmetric embedding of a Hermitian R = B + iC (Section 4): the 2n x 2n
+// matrix [[B, -C], [C, B]] (row-major, ld 2n).  For real g,
+// [g; 0]^T f([[B, -C], [C, B]]) [g; 0] = g^T Re[f(R)] g for every polynomial f.
+template <typename TO>
+__global__ void k_hermitian_embed(const void* src, int cdtype, int64_t n, int64_t ld, TO* dst) {
+    const int64_t total = n * n;
+    const int64_t n2 = 2 * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n, k = e - i * n;
+        const int64_t idx = i * ld + k;
+        double b, c;
+        if (cdtype == 2) {
+            b = ((const double*)src)[2 * idx];
+            c = ((const double*)src)[2 * idx + 1];
+        } else {
+            b = (double)((const float*)src)[2 * idx];
+            c = (double)((const float*)src)[2 * idx + 1];
+        }
+        dst[i * n2 + k] = (TO)b;
+        dst[i * n2 + n + k] = (TO)(-c);
+        dst[(n + i) * n2 + k] = (TO)c;
+        dst[(n + i) * n2 + n + k] = (TO)b;
+    }
 }
 
 template <typename TO>
@@ -24,6 +57,15 @@ static int grid_for(int64_t total) {
     if (b > 152 * 32) b = 152 * 32;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+cudaError_t launch_hermitian_embed(const void* src, int cdtype, int64_t n, int64_t ld, void* dst,
+                                   int dst_dtype, cudaStream_t st) {
+    if (dst_dtype == 0)
+        k_hermitian_embed<double><<<grid_for(n * n), 256, 0, st>>>(src, cdtype, n, ld, (double*)dst);
+    else
+        k_hermitian_embed<float><<<grid_for(n * n), 256, 0, st>>>(src, cdtype, n, ld, (float*)dst);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dense_convert_f64(const void* src, int src_dtype, int64_t n, int64_t ld,

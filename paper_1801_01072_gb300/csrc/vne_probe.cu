@@ -31,15 +31,18 @@ cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint
 // partials sum_i g_j[i]^2 of each row tile.
 template <typename T>
 __global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
-                             int64_t n, int S, int s, int kind, uint64_t seed, Partials P) {
+                             int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
+                             int64_t probe_n) {
     __shared__ double sh[32];
     const int j = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double g = 0.0;
     if (i < n) {
-        const uint64_t e = (uint64_t)j * (uint64_t)n + (uint64_t)i;
-        if (sizeof(T) == 4 && kind == 1) g = (double)gaussian_f32(seed, e);
-        else g = probe_value(kind, seed, e);
+        if (i < probe_n) {
+            const uint64_t e = (uint64_t)j * (uint64_t)probe_n + (uint64_t)i;
+            if (sizeof(T) == 4 && kind == 1) g = (double)gaussian_f32(seed, e);
+            else g = probe_value(kind, seed, e);
+        }
         const T gt = (T)g;
         G[(int64_t)j * n + i] = gt;
         for (int c = j; c < S; c += s) {
@@ -66,17 +69,18 @@ __global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo
 template <typename T>
 cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                              int rows_per_tile, cudaStream_t st) {
+                              int rows_per_tile, cudaStream_t st, int64_t probe_n) {
     dim3 grid((unsigned)((n + rows_per_tile - 1) / rows_per_tile), (unsigned)s);
-    k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, Yhi, Ylo, ldk, n, S, s, kind, seed, P);
+    k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, Yhi, Ylo, ldk, n, S, s, kind, seed, P,
+                                                    probe_n);
     return cudaGetLastError();
 }
 template cudaError_t launch_dense_init<double>(double*, double*, __nv_bfloat16*, __nv_bfloat16*,
                                                int64_t, int64_t, int, int, int, uint64_t, Partials,
-                                               int, cudaStream_t);
+                                               int, cudaStream_t, int64_t);
 template cudaError_t launch_dense_init<float>(float*, float*, __nv_bfloat16*, __nv_bfloat16*,
                                               int64_t, int64_t, int, int, int, uint64_t, Partials,
-                                              int, cudaStream_t);
+                                              int, cudaStream_t, int64_t);
 
 // Banded layout: a block of 8 warps owns a tile of rows_per_tile rows; each
 // warp walks rows w, w+8, ... of the tile and lane l covers probes l, l+32, ...

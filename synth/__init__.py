@@ -245,6 +245,11 @@ WORKLOADS = {
     "learned_n8192": dict(kind="learned", n=8192, spectrum="powerlaw", k=2048, alpha=1.5,
                           floor=1e-9, seed=2, m=16, s=128, probe="gaussian", power_iters=30,
                           train_count=100000, train_epochs=20, m_ref=64),
+    # a random 5000 x 5000 complex density matrix (Section 6, Hermitian case):
+    # Haar eigenvectors, p_i ~ exp(-i/500); Taylor m = 10 and Chebyshev m = 10,
+    # s = 100 real Gaussian probes, u = 1
+    "hermitian_n5000": dict(kind="hermitian", n=5000, tau=500.0, seed=6, m=10, s=100,
+                            probe="gaussian"),
     # 256 uneven dense matrices in one batched call (one CUDA graph launch)
     "batched256": dict(kind="batched", count=256, n_lo=256, n_hi=4096, seed=5, m=24, s=32,
                        probe="gaussian", power_iters=30),
