@@ -247,7 +247,7 @@ WORKLOADS = {
                           train_count=100000, train_epochs=20, m_ref=64),
     # a random 5000 x 5000 complex density matrix (Section 6, Hermitian case):
     # Haar eigenvectors, p_i ~ exp(-i/500); Taylor m = 10 and Chebyshev m = 10,
-    # s = 100 real Gaussian probes, u = 1
+    # s = 100 real Gaussian probes, u from the power method
     "hermitian_n5000": dict(kind="hermitian", n=5000, tau=500.0, seed=6, m=10, s=100,
                             probe="gaussian"),
     # 256 uneven dense matrices in one batched call (one CUDA graph launch)

