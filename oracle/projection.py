@@ -86,3 +86,65 @@ def estimate_projection(R: np.ndarray, k: int, s: int, kind: str, seed: int) -> 
     pos = p[p > 0]
     H = float((pos * np.log(1.0 / pos)).sum())
     return dict(H=H, p=p, sketch=Pi)
+
+
+# --------------------------------------------------------------------------
+# Block Krylov extension (not in the paper; the random-projection path of the
+# batched workload: block b, q iterations, top-k Ritz values and a tail)
+# --------------------------------------------------------------------------
+
+def rank_revealing_basis(V: np.ndarray, lam_ref: float, drop: float) -> np.ndarray:
+    """Orthonormal basis of the columns of V through the eigendecomposition
+    of V^T V = U diag(l) U^T: Q = V U_kept diag(l_kept)^-1/2, keeping l_i >
+    drop * lam_ref (lam_ref: the largest Gram eigenvalue of the first block,
+    so directions at round-off level are dropped).  Dropped columns are zero."""
+    l, U = np.linalg.eigh(V.T @ V)
+    keep = l > drop * lam_ref
+    M = np.zeros_like(U)
+    M[:, keep] = U[:, keep] / np.sqrt(l[keep])
+    return V @ M
+
+
+def block_krylov_ritz(R: np.ndarray, b: int, q: int, kind: str, seed: int,
+                      drop: float = 1e-12) -> np.ndarray:
+    """Ritz values (descending) of R on K = span[Q_0 .. Q_{q-1}] with
+    V_0 = R Pi, V_j = R Q_{j-1}, each V_j orthogonalised against the earlier
+    blocks (two passes of block Gram-Schmidt) and then made orthonormal by
+    rank_revealing_basis; T = K^T R K."""
+    R = np.asarray(R, dtype=np.float64)
+    n = R.shape[0]
+    Pi = sketch(n, b, kind, seed)
+    V = R @ Pi
+    blocks, lam_ref = [], None
+    for j in range(q):
+        if j > 0:
+            V = R @ blocks[-1]
+            K = np.concatenate(blocks, axis=1)
+            for _ in range(2):
+                V = V - K @ (K.T @ V)
+        if lam_ref is None:
+            lam_ref = float(np.linalg.eigvalsh(V.T @ V).max())
+        blocks.append(rank_revealing_basis(V, lam_ref, drop))
+    K = np.concatenate(blocks, axis=1)
+    T = K.T @ (R @ K)
+    T = 0.5 * (T + T.T)
+    return np.sort(np.linalg.eigvalsh(T))[::-1]
+
+
+def krylov_entropy(theta: np.ndarray, k: int, n: int) -> float:
+    """sum over the k largest Ritz values of t ln(1/t), plus the tail: the
+    remaining trace 1 - sum_k theta_i spread evenly over the other n - k
+    eigenvalues (reading of the tail estimate; tr R = 1)."""
+    top = theta[:k]
+    pos = top[top > 0]
+    H = float((pos * np.log(1.0 / pos)).sum())
+    rest = 1.0 - float(top.sum())
+    if rest > 0 and n > k:
+        H += rest * np.log((n - k) / rest)
+    return H
+
+
+def estimate_block_krylov(R, k: int, b: int, q: int, kind: str, seed: int,
+                          drop: float = 1e-12) -> dict:
+    theta = block_krylov_ritz(R, b, q, kind, seed, drop)
+    return dict(H=krylov_entropy(theta, k, np.asarray(R).shape[0]), theta=theta[:k])

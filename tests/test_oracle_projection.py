@@ -98,3 +98,49 @@ def test_rank_deficient_tail_is_negligible():
     assert np.all(out["p"][3:] < 1e-14)
     H = float((p * np.log(1 / p)).sum())
     assert abs(out["H"] - H) / H < 0.5
+
+
+def test_rank_revealing_basis_is_orthonormal_on_the_kept_span():
+    r = np.random.default_rng(0)
+    V = r.standard_normal((60, 5)) @ r.standard_normal((5, 8))   # rank 5, 8 columns
+    Q = P.rank_revealing_basis(V, np.linalg.eigvalsh(V.T @ V).max(), 1e-12)
+    kept = np.linalg.norm(Q, axis=0) > 0.5
+    assert kept.sum() == 5
+    np.testing.assert_allclose(Q[:, kept].T @ Q[:, kept], np.eye(5), atol=1e-12)
+    # same span as V
+    proj = Q @ Q.T
+    np.testing.assert_allclose(proj @ V, V, atol=1e-10)
+
+
+def test_krylov_recovers_a_rank_k_spectrum_exactly():
+    # the first block already spans range(R) (rank 6 <= b = 8): the Ritz
+    # values are the eigenvalues, later blocks are round-off and dropped
+    n, k = 120, 6
+    psi = synth.orthonormal_columns(n, k, 5)
+    p = synth.spectrum_exponential(k, 2.0)
+    R = synth.dense_density(psi, p)
+    out = P.estimate_block_krylov(R, k, 8, 3, "gaussian", seed=1)
+    np.testing.assert_allclose(out["theta"], p, rtol=1e-11)
+    H = float((p * np.log(1 / p)).sum())
+    assert abs(out["H"] - H) < 1e-11          # tail: 1 - sum p = 0
+
+
+def test_krylov_full_space_gives_exact_entropy():
+    # q b >= n: K spans the whole space, T has R's spectrum, and the tail
+    # formula is exact for a flat remainder
+    n = 24
+    R, p, _ = synth.dense_exp(n, 5.0, seed=3)
+    theta = P.block_krylov_ritz(R, 8, 3, "gaussian", seed=2)
+    np.testing.assert_allclose(theta, np.sort(p)[::-1], atol=1e-12)
+    assert abs(P.krylov_entropy(theta, n, n) - float(-(p * np.log(p)).sum())) < 1e-12
+    flat = np.full(30, 1 / 30)
+    assert abs(P.krylov_entropy(flat[:10], 10, 30) - np.log(30)) < 1e-12
+
+
+def test_krylov_ritz_values_interlace_from_below():
+    # Ritz values never exceed the corresponding eigenvalues (Cauchy interlacing)
+    n = 200
+    R, p, _ = synth.dense_exp(n, 30.0, seed=4)
+    theta = P.block_krylov_ritz(R, 8, 3, "srht", seed=3)
+    ps = np.sort(p)[::-1]
+    assert np.all(theta[:24] <= ps[:24] + 1e-14)
