@@ -248,8 +248,18 @@ enum { VNE_SKETCH_GAUSSIAN = 0, VNE_SKETCH_SRHT = 1, VNE_SKETCH_COUNT = 2 };
  *                  >> 11) / 2^53;
  *                  VNE_SKETCH_COUNT -- Algorithm alg:IS: Pi[i, h(i)] = D_i with
  *                  h(i) = floor(u s), u from output i of the same index stream.
- *   krylov_iters : 0 (Algorithm alg:EN as printed); other values return
- *                  VNE_ERR_UNSUPPORTED.
+ *   krylov_iters : 0 -- Algorithm alg:EN as printed (1 <= k <= s).
+ *                  q >= 1 -- the block-Krylov extension (not in the paper): the
+ *                  block size is b = s (<= 64, q*b <= 512, k <= q*b); V_0 = R Pi,
+ *                  V_j = R Q_(j-1); each V_j is orthogonalised against the
+ *                  earlier blocks (two passes of block Gram-Schmidt) and made
+ *                  orthonormal through the eigendecomposition of its Gram
+ *                  matrix (Jacobi), dropping directions with Gram eigenvalue
+ *                  below 1e-12 (FP64) / 1e-6 (FP32) of the first block's
+ *                  largest; the k largest eigenvalues theta of T = K^T R K
+ *                  (K = [Q_0 .. Q_(q-1)]) give H~ = sum theta ln(1/theta)
+ *                  plus the tail t ln((n-k)/t), t = 1 - sum theta (the rest
+ *                  of the unit trace spread evenly); p_out gets theta.
  *   precision    : VNE_PREC_F64 or VNE_PREC_F32: arithmetic of Pi and of the
  *                  product R Pi.  The Gram matrix R~^T R~, its eigenvalues
  *                  (Householder tridiagonalisation + bisection) and H~ are FP64.

@@ -5,6 +5,7 @@
 // Every arithmetic step is a kernel of this library; the host only sequences.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -661,6 +662,121 @@ vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int 
     return VNE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Block Krylov extension of the projection path (not in the paper).
+// ---------------------------------------------------------------------------
+template <typename T>
+vne_status run_krylov(vne_handle* h, const vne_matrix& R, int k, int b, int q, int kind,
+                      uint64_t seed, double* H_out, double* p_out, cudaStream_t st) {
+    Call c{h, st};
+    const int64_t n = R.n;
+    const int want = sizeof(T) == 8 ? VNE_F64 : VNE_F32;
+    const int N = q * b;
+    const int splitk = dense_simt_splitk(n, b, h->sm_count, (int)sizeof(T));
+    const int chunks = gram_chunks(n, std::max(N, b), h->sm_count);
+    const double drop = sizeof(T) == 8 ? 1e-12 : 1e-6;
+    auto plan = [&](Bump& bp, void** Rcopy, T** Rop, T** Pi, T** V, T** Zpart, T** K, T** W,
+                    double** part, double** C, double** G, double** lam, double** U, double** M,
+                    double** Tm, double** Wg, double** de, double** ev, double** out,
+                    double** lref) {
+        *Rcopy = R.memory == VNE_MEM_HOST ? bp.take<char>((size_t)n * R.ld * elt_size(R.dtype))
+                                          : nullptr;
+        *Rop = R.dtype != want ? bp.take<T>((size_t)n * n) : nullptr;
+        *Pi = bp.take<T>((size_t)n * b);
+        *V = bp.take<T>((size_t)n * b);
+        *Zpart = bp.take<T>((size_t)splitk * b * n);
+        *K = bp.take<T>((size_t)N * n);
+        *W = bp.take<T>((size_t)N * n);
+        *part = bp.take<double>((size_t)chunks * N * N);
+        *C = bp.take<double>((size_t)N * b);
+        *G = bp.take<double>((size_t)b * b);
+        *lam = bp.take<double>((size_t)b);
+        *U = bp.take<double>((size_t)b * b);
+        *M = bp.take<double>((size_t)b * b);
+        *Tm = bp.take<double>((size_t)N * N);
+        *Wg = bp.take<double>((size_t)N * N);
+        *de = bp.take<double>((size_t)2 * N);
+        *ev = bp.take<double>((size_t)N);
+        *out = bp.take<double>((size_t)k + 1);
+        *lref = bp.take<double>(1);
+    };
+    void* Rcopy;
+    T *Rop, *Pi, *V, *Zpart, *K, *W;
+    double *part, *C, *G, *lam, *U, *M, *Tm, *Wg, *de, *ev, *out, *lref;
+    {
+        Bump b0(nullptr);
+        plan(b0, &Rcopy, &Rop, &Pi, &V, &Zpart, &K, &W, &part, &C, &G, &lam, &U, &M, &Tm, &Wg,
+             &de, &ev, &out, &lref);
+        vne_status vs = ensure_ws(h, b0.off + 4096);
+        if (vs != VNE_OK) return vs;
+        Bump b1(h->ws);
+        plan(b1, &Rcopy, &Rop, &Pi, &V, &Zpart, &K, &W, &part, &C, &G, &lam, &U, &M, &Tm, &Wg,
+             &de, &ev, &out, &lref);
+    }
+    h->ev_used = 0;
+    h->pending.clear();
+    const void* Rdata = R.data;
+    if (R.memory == VNE_MEM_HOST) {
+        c.chk(cudaMemcpyAsync(Rcopy, R.data, (size_t)n * R.ld * elt_size(R.dtype),
+                              cudaMemcpyHostToDevice, st));
+        Rdata = Rcopy;
+    }
+    const T* Rk = (const T*)Rdata;
+    int64_t ldr = R.ld;
+    if (Rop) {
+        if (sizeof(T) == 8)
+            c.launched(launch_dense_convert_f64(Rdata, R.dtype, n, R.ld, (double*)Rop, st));
+        else
+            c.launched(launch_dense_convert_f32(Rdata, R.dtype, n, R.ld, (float*)Rop, st));
+        Rk = Rop;
+        ldr = n;
+    }
+    // dst = R X (X stored [b][n])
+    auto product = [&](const T* X, T* dst) {
+        if (!c.ok()) return;
+        c.prof_begin();
+        c.launched(launch_dense_simt_step<T>(Rk, ldr, n, X, Zpart, b, 0, b, splitk, st));
+        c.prof_end(1);
+        if (c.ok()) c.launched(launch_split_sum<T>(Zpart, splitk, (int64_t)b * n, dst, h->sm_count, st));
+    };
+    if (c.ok()) c.launched(launch_sketch<T>(Pi, n, b, kind, seed, h->sm_count, st));
+    product(Pi, V);
+    for (int j = 0; j < q && c.ok(); ++j) {
+        T* Kj = K + (size_t)j * b * n;
+        if (j > 0) {
+            c.chk(cudaMemcpyAsync(V, W + (size_t)(j - 1) * b * n, (size_t)b * n * sizeof(T),
+                                  cudaMemcpyDeviceToDevice, st));
+            for (int pass = 0; pass < 2 && c.ok(); ++pass) {
+                c.launched(launch_xgram<T>(K, j * b, V, b, n, chunks, part, C, st));
+                if (c.ok()) c.launched(launch_ts_mm<T>(K, j * b, C, b, -1.0, V, V, n, st));
+            }
+        }
+        if (c.ok()) c.launched(launch_gram<T>(V, n, b, chunks, part, G, st));
+        if (c.ok()) c.launched(launch_jacobi<T>(G, b, lam, U, st));
+        if (c.ok()) c.launched(launch_basis_coeffs(lam, U, b, lref, j == 0, drop, M, st));
+        if (c.ok()) c.launched(launch_ts_mm<T>(V, b, M, b, 1.0, nullptr, Kj, n, st));
+        product(Kj, W + (size_t)j * b * n);
+    }
+    if (c.ok()) c.launched(launch_xgram<T>(K, N, W, N, n, chunks, part, Tm, st));
+    if (c.ok()) c.launched(launch_symmetrize(Tm, N, st));
+    if (c.ok()) c.launched(launch_sym_eigvals(Tm, N, k, Wg, de, de + N, ev, st));
+    if (c.ok()) c.launched(launch_krylov_combine(ev, k, n, out, st));
+    std::vector<double> host((size_t)k + 1);
+    if (c.ok())
+        c.chk(cudaMemcpyAsync(host.data(), out, (size_t)(k + 1) * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+    c.chk(cudaStreamSynchronize(st));
+    if (!c.ok()) {
+        cudaGetLastError();
+        return map_err(h, c.err);
+    }
+    collect_profile(h);
+    if (!std::isfinite(host[0])) return VNE_ERR_NONFINITE;
+    *H_out = host[0];
+    if (p_out) std::memcpy(p_out, host.data() + 1, (size_t)k * sizeof(double));
+    return VNE_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -996,14 +1112,25 @@ vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k,
     if (R->dtype != VNE_F64 && R->dtype != VNE_F32) return VNE_ERR_INVALID_ARG;
     if (R->memory != VNE_MEM_DEVICE && R->memory != VNE_MEM_HOST) return VNE_ERR_INVALID_ARG;
     if (R->layout != VNE_DENSE && R->layout != VNE_DIA) return VNE_ERR_INVALID_ARG;
-    if (s < 1 || k < 1 || k > s) return VNE_ERR_INVALID_ARG;
+    if (s < 1 || k < 1 || (krylov_iters <= 0 && k > s)) return VNE_ERR_INVALID_ARG;
     if (sketch < VNE_SKETCH_GAUSSIAN || sketch > VNE_SKETCH_COUNT) return VNE_ERR_INVALID_ARG;
     if (precision < VNE_PREC_F64 || precision > VNE_PREC_BF16X3 || krylov_iters < 0)
         return VNE_ERR_INVALID_ARG;
-    if (R->layout != VNE_DENSE || s > 512 || krylov_iters != 0 || precision > VNE_PREC_F32)
+    if (R->layout != VNE_DENSE || s > 512 || precision > VNE_PREC_F32 || is_complex(R->dtype))
         return VNE_ERR_UNSUPPORTED;
     if ((int64_t)s * R->n > ((int64_t)1 << 40)) return VNE_ERR_UNSUPPORTED;
+    if (krylov_iters > 0) {
+        if (s > 64 || (int64_t)krylov_iters * s > 512) return VNE_ERR_UNSUPPORTED;
+        if (k > krylov_iters * s) return VNE_ERR_INVALID_ARG;
+    }
     DeviceGuard guard(h->device);
+    if (krylov_iters > 0) {
+        if (precision == VNE_PREC_F64)
+            return run_krylov<double>(h, *R, k, s, krylov_iters, sketch, seed, H_out, p_out,
+                                      (cudaStream_t)stream);
+        return run_krylov<float>(h, *R, k, s, krylov_iters, sketch, seed, H_out, p_out,
+                                 (cudaStream_t)stream);
+    }
     if (precision == VNE_PREC_F64)
         return run_projection<double>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
     return run_projection<float>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);

@@ -150,6 +150,20 @@ cudaError_t launch_sym_eigvals(const double* A, int N, int top, double* Wg, doub
                                double* evals, cudaStream_t st);
 // out[0] = H~, out[1..k] = p~ from the k largest Gram eigenvalues.
 cudaError_t launch_proj_combine(const double* evals, int k, double* out, cudaStream_t st);
+// block Krylov pieces
+template <typename T>
+cudaError_t launch_xgram(const T* A, int ra, const T* B, int rb, int64_t n, int chunks,
+                         double* part, double* C, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ts_mm(const T* A, int ra, const double* M, int rc, double scale, const T* In,
+                         T* Out, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_jacobi(const double* G, int b, double* lam, double* U, cudaStream_t st);
+cudaError_t launch_basis_coeffs(const double* lam, const double* U, int b, double* lam_ref,
+                                int first, double drop, double* M, cudaStream_t st);
+cudaError_t launch_symmetrize(double* T, int N, cudaStream_t st);
+cudaError_t launch_krylov_combine(const double* ev, int k, int64_t n, double* out,
+                                  cudaStream_t st);
 
 // ---- learned correction (vne_mlp.cu) ------------------------------------------------
 cudaError_t launch_spectral_sample(int count, const int* kind, const int* n, const float* a,

@@ -661,6 +661,337 @@ cudaError_t launch_proj_combine(const double* evals, int k, double* out, cudaStr
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Block Krylov extension (the batched workload's projection path; not in the
+// paper): V_0 = R Pi, V_j = R Q_{j-1}; each V_j is orthogonalised against the
+// earlier blocks (two passes of block Gram-Schmidt) and made orthonormal through
+// the eigendecomposition of its Gram matrix, dropping the directions below
+// drop * (largest Gram eigenvalue of the first block); the Ritz values of R on
+// K = [Q_0 .. Q_{q-1}] are the eigenvalues of T = K^T (R K).
+// ---------------------------------------------------------------------------
+
+// C (ra x rb, FP64) = A^T B for A stored [ra][n], B [rb][n]: all 32 x 32 tiles,
+// rows split into `chunks` slices summed in order by k_sum_chunks.
+template <typename T>
+__global__ void __launch_bounds__(256) k_xgram(const T* __restrict__ A, int ra,
+                                               const T* __restrict__ B, int rb, int64_t n,
+                                               int64_t rows_per_chunk, double* __restrict__ part) {
+    __shared__ T As[GR_K][GR_T + 1];
+    __shared__ T Bs[GR_K][GR_T + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int a0 = blockIdx.y * GR_T, b0 = blockIdx.x * GR_T;
+    const int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk;
+    int64_t r1 = r0 + rows_per_chunk;
+    if (r1 > n) r1 = n;
+    GramAcc<T> acc[2][2];
+    for (int64_t k0 = r0; k0 < r1; k0 += GR_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int col = e >> 5, kk = e & 31;
+            const int64_t r = k0 + kk;
+            const int ca = a0 + col, cb = b0 + col;
+            As[kk][col] = (ca < ra && r < r1) ? A[(int64_t)ca * n + r] : (T)0;
+            Bs[kk][col] = (cb < rb && r < r1) ? B[(int64_t)cb * n + r] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < GR_K; ++kk) {
+            const T x0 = As[kk][ty * 2], x1 = As[kk][ty * 2 + 1];
+            const T y0 = Bs[kk][tx * 2], y1 = Bs[kk][tx * 2 + 1];
+            acc[0][0].add(x0, y0);
+            acc[0][1].add(x0, y1);
+            acc[1][0].add(x1, y0);
+            acc[1][1].add(x1, y1);
+        }
+        __syncthreads();
+    }
+    double* out = part + (int64_t)blockIdx.z * ra * rb;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int a = a0 + ty * 2 + i, b = b0 + tx * 2 + j;
+            if (a < ra && b < rb) out[(int64_t)a * rb + b] = acc[i][j].value();
+        }
+}
+
+template <typename T>
+cudaError_t launch_xgram(const T* A, int ra, const T* B, int rb, int64_t n, int chunks,
+                         double* part, double* C, cudaStream_t st) {
+    int64_t rows = (n + chunks - 1) / chunks;
+    rows = (rows + GR_K - 1) / GR_K * GR_K;
+    dim3 grid((unsigned)((rb + GR_T - 1) / GR_T), (unsigned)((ra + GR_T - 1) / GR_T),
+              (unsigned)chunks);
+    k_xgram<T><<<grid, 256, 0, st>>>(A, ra, B, rb, n, rows, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t len = (int64_t)ra * rb;
+    k_sum_chunks<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(part, chunks, len, C);
+    return cudaGetLastError();
+}
+
+// Out[c][i] = In[c][i] (or 0) + scale * sum_r A[r][i] M[r][c] for i < n, c < rc;
+// A stored [ra][n], M (ra x rc) FP64 row-major.  One thread per row, 16
+// columns per block; M's 16 columns staged in shared memory in T.
+constexpr int TS_COLS = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_ts_mm(const T* __restrict__ A, int ra,
+                                               const double* __restrict__ M, int rc, double scale,
+                                               const T* In, T* Out, int64_t n) {
+    extern __shared__ unsigned char ts_raw[];
+    T* Ms = reinterpret_cast<T*>(ts_raw);  // [ra][TS_COLS]
+    const int c0 = blockIdx.y * TS_COLS;
+    for (int e = threadIdx.x; e < ra * TS_COLS; e += blockDim.x) {
+        const int r = e / TS_COLS, c = c0 + e % TS_COLS;
+        Ms[e] = c < rc ? (T)(scale * M[(int64_t)r * rc + c]) : (T)0;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T acc[TS_COLS];
+#pragma unroll
+    for (int c = 0; c < TS_COLS; ++c) acc[c] = (T)0;
+    for (int r = 0; r < ra; ++r) {
+        const T a = A[(int64_t)r * n + i];
+#pragma unroll
+        for (int c = 0; c < TS_COLS; ++c) acc[c] = Math<T>::fma(a, Ms[r * TS_COLS + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < TS_COLS; ++c) {
+        const int col = c0 + c;
+        if (col < rc) {
+            const int64_t idx = (int64_t)col * n + i;
+            Out[idx] = (In ? In[idx] : (T)0) + acc[c];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_ts_mm(const T* A, int ra, const double* M, int rc, double scale, const T* In,
+                         T* Out, int64_t n, cudaStream_t st) {
+    const size_t smem = (size_t)ra * TS_COLS * sizeof(T);
+    if (smem > 48 * 1024) {
+        cudaError_t r = cudaFuncSetAttribute(k_ts_mm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (r != cudaSuccess) return r;
+    }
+    dim3 grid((unsigned)((n + 127) / 128), (unsigned)((rc + TS_COLS - 1) / TS_COLS));
+    k_ts_mm<T><<<grid, 128, smem, st>>>(A, ra, M, rc, scale, In, Out, n);
+    return cudaGetLastError();
+}
+
+// Cyclic Jacobi (parallel ordering: every round rotates b/2 disjoint pairs of
+// the circle schedule) on the b x b symmetric G, b <= 64, in arithmetic T:
+// eigenvalues lam and eigenvectors U (columns), both written in FP64.
+constexpr int kJacobiMaxB = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, int b,
+                                                double* __restrict__ lam, double* __restrict__ Uout) {
+    extern __shared__ unsigned char jac_raw[];
+    T* A = reinterpret_cast<T*>(jac_raw);
+    T* U = A + b * b;
+    __shared__ T rc[kJacobiMaxB / 2 + 1][2];
+    __shared__ int rp[kJacobiMaxB / 2 + 1][2];
+    __shared__ double red[8];
+    __shared__ int stop;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < b * b; e += blockDim.x) {
+        A[e] = (T)G[e];
+        U[e] = (e / b == e % b) ? (T)1 : (T)0;
+    }
+    const int B = b + (b & 1), np = B / 2;
+    const double eps2 = sizeof(T) == 8 ? 1e-30 : 1e-14;
+    __syncthreads();
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int e = tid; e < b * b; e += blockDim.x) {
+            const int i = e / b, j = e % b;
+            const double v = (double)A[e];
+            if (i > j) off += v * v;
+            else if (i == j) dia += v * v;
+        }
+        off = warp_sum(off);
+        dia = warp_sum(dia);
+        if ((tid & 31) == 0) red[tid >> 5] = off;
+        __syncthreads();
+        if (tid == 0) {
+            double o = 0.0;
+            for (int w = 0; w < 8; ++w) o += red[w];
+            red[0] = o;
+        }
+        __syncthreads();
+        const double offt = red[0];
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = dia;
+        __syncthreads();
+        if (tid == 0) {
+            double d = 0.0;
+            for (int w = 0; w < 8; ++w) d += red[w];
+            stop = !(offt > eps2 * d);
+        }
+        __syncthreads();
+        if (stop) break;
+        for (int r = 0; r < B - 1; ++r) {
+            if (tid < np) {
+                int p, q;
+                if (tid == 0) {
+                    p = r;
+                    q = B - 1;
+                } else {
+                    p = (r + tid) % (B - 1);
+                    q = (r - tid + (B - 1)) % (B - 1);
+                }
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                T c = (T)1, sn = (T)0;
+                if (q < b) {
+                    const T apq = A[p * b + q];
+                    if (apq != (T)0) {
+                        const T th = (A[q * b + q] - A[p * b + p]) / ((T)2 * apq);
+                        const T t = th != (T)0 ? (th > (T)0 ? (T)1 : (T)-1) /
+                                                     (fabs(th) + sqrt(th * th + (T)1))
+                                               : (T)1;
+                        c = (T)1 / sqrt(t * t + (T)1);
+                        sn = t * c;
+                    }
+                }
+                rc[tid][0] = c;
+                rc[tid][1] = sn;
+                rp[tid][0] = p;
+                rp[tid][1] = q;
+            }
+            __syncthreads();
+            for (int e = tid; e < np * b; e += blockDim.x) {  // rows: A <- J^T A
+                const int k = e / b, j = e % b;
+                const int p = rp[k][0], q = rp[k][1];
+                if (q >= b) continue;
+                const T c = rc[k][0], sn = rc[k][1];
+                const T ap = A[p * b + j], aq = A[q * b + j];
+                A[p * b + j] = c * ap - sn * aq;
+                A[q * b + j] = sn * ap + c * aq;
+            }
+            __syncthreads();
+            for (int e = tid; e < np * b; e += blockDim.x) {  // columns: A <- A J, U <- U J
+                const int k = e / b, i = e % b;
+                const int p = rp[k][0], q = rp[k][1];
+                if (q >= b) continue;
+                const T c = rc[k][0], sn = rc[k][1];
+                const T ap = A[i * b + p], aq = A[i * b + q];
+                A[i * b + p] = c * ap - sn * aq;
+                A[i * b + q] = sn * ap + c * aq;
+                const T up = U[i * b + p], uq = U[i * b + q];
+                U[i * b + p] = c * up - sn * uq;
+                U[i * b + q] = sn * up + c * uq;
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < b * b; e += blockDim.x) Uout[e] = (double)U[e];
+    for (int i = tid; i < b; i += blockDim.x) lam[i] = (double)A[i * b + i];
+}
+
+template <typename T>
+cudaError_t launch_jacobi(const double* G, int b, double* lam, double* U, cudaStream_t st) {
+    if (b < 1 || b > kJacobiMaxB) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * b * b * sizeof(T);
+    if (smem > 48 * 1024) {
+        cudaError_t r = cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (r != cudaSuccess) return r;
+    }
+    k_jacobi<T><<<1, 256, smem, st>>>(G, b, lam, U);
+    return cudaGetLastError();
+}
+
+// M[:, c] = U[:, c] / sqrt(lam_c) where lam_c > drop * lam_ref, else 0.  The
+// first block (first != 0) sets lam_ref = max lam.
+__global__ void k_basis_coeffs(const double* __restrict__ lam, const double* __restrict__ U, int b,
+                               double* __restrict__ lam_ref, int first, double drop,
+                               double* __restrict__ M) {
+    __shared__ double ref;
+    if (threadIdx.x == 0) {
+        if (first) {
+            double mx = lam[0];
+            for (int i = 1; i < b; ++i) mx = fmax(mx, lam[i]);
+            *lam_ref = mx;
+        }
+        ref = *lam_ref;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int c = e % b;
+        const double l = lam[c];
+        M[e] = (l > drop * ref && l > 0.0) ? U[e] / sqrt(l) : 0.0;
+    }
+}
+
+__global__ void k_symmetrize(double* T, int N) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * N; e += gridDim.x * blockDim.x) {
+        const int i = e / N, j = e % N;
+        if (i < j) {
+            const double v = 0.5 * (T[(int64_t)i * N + j] + T[(int64_t)j * N + i]);
+            T[(int64_t)i * N + j] = v;
+            T[(int64_t)j * N + i] = v;
+        }
+    }
+}
+
+// out[0] = sum_{i<k, theta_i>0} theta_i ln(1/theta_i) + tail, out[1+i] = theta_i;
+// tail: the rest of the unit trace, 1 - sum theta_i, spread evenly over n - k.
+__global__ void k_krylov_combine(const double* __restrict__ ev, int k, int64_t n,
+                                 double* __restrict__ out) {
+    __shared__ double red[32];
+    double h = 0.0, sum = 0.0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const double t = ev[i];
+        out[1 + i] = t;
+        sum += t;
+        if (t > 0.0) h -= t * log(t);
+    }
+    const double H = block_sum(h, red);
+    __syncthreads();
+    const double S = block_sum(sum, red);
+    if (threadIdx.x == 0) {
+        double tot = H;
+        const double rest = 1.0 - S;
+        if (rest > 0.0 && n > k) tot += rest * log((double)(n - k) / rest);
+        out[0] = tot;
+    }
+}
+
+cudaError_t launch_basis_coeffs(const double* lam, const double* U, int b, double* lam_ref,
+                                int first, double drop, double* M, cudaStream_t st) {
+    k_basis_coeffs<<<1, 256, 0, st>>>(lam, U, b, lam_ref, first, drop, M);
+    return cudaGetLastError();
+}
+cudaError_t launch_symmetrize(double* T, int N, cudaStream_t st) {
+    k_symmetrize<<<(N * N + 255) / 256, 256, 0, st>>>(T, N);
+    return cudaGetLastError();
+}
+cudaError_t launch_krylov_combine(const double* ev, int k, int64_t n, double* out,
+                                  cudaStream_t st) {
+    k_krylov_combine<<<1, 256, 0, st>>>(ev, k, n, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_xgram<double>(const double*, int, const double*, int, int64_t, int,
+                                          double*, double*, cudaStream_t);
+template cudaError_t launch_xgram<float>(const float*, int, const float*, int, int64_t, int,
+                                         double*, double*, cudaStream_t);
+template cudaError_t launch_ts_mm<double>(const double*, int, const double*, int, double,
+                                          const double*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_ts_mm<float>(const float*, int, const double*, int, double,
+                                         const float*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_jacobi<double>(const double*, int, double*, double*, cudaStream_t);
+template cudaError_t launch_jacobi<float>(const double*, int, double*, double*, cudaStream_t);
+
 template cudaError_t launch_sketch<double>(double*, int64_t, int, int, uint64_t, int, cudaStream_t);
 template cudaError_t launch_sketch<float>(float*, int64_t, int, int, uint64_t, int, cudaStream_t);
 template cudaError_t launch_split_sum<double>(const double*, int, int64_t, double*, int, cudaStream_t);

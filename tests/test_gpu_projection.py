@@ -143,6 +143,50 @@ def test_projection_error_statuses():
     assert status(k=5) == INVALID_ARG          # k > s
     assert status(k=0) == INVALID_ARG
     assert status(s=513, k=2) == UNSUPPORTED   # beyond the eigensolver's N
-    assert status(krylov_iters=2) == UNSUPPORTED
+    assert status(krylov_iters=2, s=128, k=2) == UNSUPPORTED   # block above 64
+    assert status(krylov_iters=2, s=4, k=9) == INVALID_ARG     # k above q * b
     assert status(precision="bf16") == UNSUPPORTED
     assert status() == 0
+
+
+# ---------------------------------------------------------------------------
+# block Krylov extension: Ritz values on the same subspace as the oracle
+# (FP64 tolerance 1e-9 of theta_1 and H; FP32 1e-4)
+# ---------------------------------------------------------------------------
+
+def check_krylov(got, ref, tol):
+    assert abs(got.H - ref["H"]) <= tol * abs(ref["H"]), (got.H, ref["H"])
+    err = np.abs(got.p - ref["theta"]).max() / ref["theta"][0]
+    assert err <= tol, f"theta error {err:.3e}"
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_krylov_recovers_rank_k_exactly(kind):
+    n, r, b, q = 300, 6, 8, 3
+    R, p, _ = synth.dense_lowrank(n, r, 2.0, seed=3)
+    got = vne.entropy_projection(dev(R), r, b, kind, seed=2, krylov_iters=q)
+    np.testing.assert_allclose(got.p, p, rtol=1e-9)
+    H = float(-(p * np.log(p)).sum())
+    assert abs(got.H - H) <= 1e-9 * H
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,b,q,k", [(256, 16, 3, 24), (500, 32, 2, 40), (129, 8, 4, 20)])
+def test_krylov_parity_full_rank(prec, n, b, q, k):
+    R, p, _ = synth.dense_exp(n, 30.0, seed=n)
+    drop = 1e-12 if prec == "f64" else 1e-6
+    ref = OP.estimate_block_krylov(R, k, b, q, "gaussian", seed=4, drop=drop)
+    got = vne.entropy_projection(dev(R), k, b, "gaussian", seed=4, precision=prec,
+                                 krylov_iters=q)
+    check_krylov(got, ref, 1e-9 if prec == "f64" else 1e-4)
+
+
+def test_krylov_bench_shape():
+    # block 64, 4 iterations, top-64 Ritz values on the n = 8192 rank-64 matrix
+    w = synth.WORKLOADS["lowrank_n8192_k64"]
+    R, p, _ = synth.dense_lowrank(w["n"], w["k"], w["tau"], w["seed"])
+    got = vne.entropy_projection(dev(R), 64, 64, "gaussian", seed=1, precision="f32",
+                                 krylov_iters=4)
+    np.testing.assert_allclose(got.p, p, rtol=1e-4)
+    H = float(-(p * np.log(p)).sum())
+    assert abs(got.H - H) <= 1e-4 * H
