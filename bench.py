@@ -11,7 +11,8 @@ FP64 combine, and the estimates copied back to the host.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|bf16x3|f64]
                     [--workload dense_powerlaw_n8192|dense_exp_n512|band33_n1e7|
-                                lowrank_n8192_k64|learned_n8192|batched256|hermitian_n5000]
+                                lowrank_n8192_k64|krylov_n8192_b64|learned_n8192|batched256|
+                                hermitian_n5000]
                     [--impl reference]
 
 Prints one JSON line.  `--impl reference` times the CPU FP64 oracle on the
@@ -211,7 +212,10 @@ def oracle_projection_time(w, R):
     import oracle.projection as OP
 
     t0 = time.perf_counter()
-    OP.estimate_projection(R, w["k"], w["s"], w["sketch"], seed=w["seed"])
+    if w.get("krylov", 0):
+        OP.estimate_block_krylov(R, w["k"], w["s"], w["krylov"], w["sketch"], seed=w["seed"])
+    else:
+        OP.estimate_projection(R, w["k"], w["s"], w["sketch"], seed=w["seed"])
     t = time.perf_counter() - t0
     try:
         from threadpoolctl import threadpool_info
@@ -219,12 +223,19 @@ def oracle_projection_time(w, R):
     except Exception:
         threads = os.cpu_count() or 1
     desc = (f"oracle (NumPy FP64) Algorithm EN on the full n={w['n']} rank-{w['k']} matrix: "
-            f"{w['sketch']} sketch s={w['s']}, R Pi and its SVD, one whole estimate")
+            f"{w['sketch']} sketch s={w['s']}, R Pi and its SVD, one whole estimate"
+            if not w.get("krylov", 0) else
+            f"oracle (NumPy FP64) block Krylov on the full n={w['n']} rank-{w['k']} matrix: "
+            f"block {w['s']}, {w['krylov']} iterations, one whole estimate")
     return t, desc, threads
 
 
 PROJ_METRIC = ("entropies/s (rank-64 n=8192 density matrices through Algorithm EN: Gaussian "
                "sketch s=256, R Pi, singular values, top-64 entropy)")
+
+
+KRYLOV_METRIC = ("entropies/s (rank-64 n=8192 density matrices through the block-Krylov "
+                 "projection: Gaussian block 64, 4 iterations, top-64 Ritz values + tail)")
 
 
 def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
@@ -238,8 +249,11 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
     Rd = torch.as_tensor(Rh).to(dev)
     seed = w["seed"] + 1000 * rank
 
+    q = w.get("krylov", 0)
+
     def step(R):
-        return vne.entropy_projection(R, k, s, w["sketch"], seed=seed, precision=prec)
+        return vne.entropy_projection(R, k, s, w["sketch"], seed=seed, precision=prec,
+                                      krylov_iters=q)
 
     h = vne._handle(local)
     stream = torch.cuda.current_stream(dev)
@@ -282,7 +296,8 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
 
     rel = None
     if rank == 0 and prec != "f64" and not args.skip_f64_check:
-        ref = vne.entropy_projection(Rd, k, s, w["sketch"], seed=seed, precision="f64")
+        ref = vne.entropy_projection(Rd, k, s, w["sketch"], seed=seed, precision="f64",
+                                     krylov_iters=q)
         rel = {"H": abs(out.H - ref.H) / abs(ref.H),
                "p_max_rel_to_p1": float(np.abs(out.p - ref.p).max() / ref.p[0])}
     if rank != 0:
@@ -293,7 +308,7 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
     pk, pk_src = peaks()
     # FP32 (or FP64) SIMT product R Pi: 2 n^2 s flops per launch.  Peak of the
     # FP32 pipes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (FP64: 1.25 TFLOP/s).
-    flops = 2.0 * n * n * s * args.steps
+    flops = 2.0 * n * n * s * (q + 1) * args.steps   # q + 1 products R X with s columns
     achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
     peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == "f32" else 1.25
     traffic = profiled_traffic("k_simt_step_f32_lowrank_n8192_k64.md", "vne_dense_simt.cu") \
@@ -309,7 +324,7 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
         cpu = {"value": 1.0 / t_cpu, "unit": "entropies/s", "cores": threads, "kind": "oracle",
                "sample": desc}
     line = {
-        "metric": PROJ_METRIC,
+        "metric": PROJ_METRIC if not q else KRYLOV_METRIC,
         "value": world * args.steps / (ms_max / 1e3),
         "unit": "entropies/s",
         "n_gpus": world,
@@ -322,7 +337,7 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
         "dtype": prec,
         "data": "synthetic (seeded rank-k density matrices, no dataset)",
         "config": {"workload": args.workload, "n": n, "k": k, "s": s, "sketch": w["sketch"],
-                   "precision": prec, "input": "R FP64 resident in HBM",
+                   "krylov_iters": q, "precision": prec, "input": "R FP64 resident in HBM",
                    "l2": "inputs larger than L2 (R is %.0f MB)" % (Rh.nbytes / 1e6),
                    "parallelism": f"independent matrices, {world} GPU(s)"},
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
@@ -993,7 +1008,8 @@ def run_reference_projection(args, w, Rh):
             times.append(t)
     value = len(times) / sum(times)
     print(json.dumps({
-        "impl": "reference", "metric": PROJ_METRIC, "value": value, "unit": "entropies/s",
+        "impl": "reference", "metric": PROJ_METRIC if not w.get("krylov", 0) else KRYLOV_METRIC,
+        "value": value, "unit": "entropies/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",

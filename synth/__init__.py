@@ -256,6 +256,10 @@ WORKLOADS = {
     # rank-64 mixture for the random-projection estimator (Algorithm alg:EN)
     "lowrank_n8192_k64": dict(kind="lowrank", n=8192, k=64, tau=16.0, seed=4, s=256,
                               sketch="gaussian"),
+    # the same matrix through the block-Krylov extension: block 64, 4 iterations,
+    # top-64 Ritz values and the tail
+    "krylov_n8192_b64": dict(kind="lowrank", n=8192, k=64, tau=16.0, seed=4, s=64,
+                             sketch="gaussian", krylov=4),
     # the same band at n = 2e6 (profiling captures of the banded kernels)
     "band33_n2e6": dict(kind="band", n=2_000_000, half_bw=16, offdiag_scale=0.02,
                         seed=3, m=30, s=64, probe="rademacher", power_iters=30),
