@@ -804,7 +804,9 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, in
         U[e] = (e / b == e % b) ? (T)1 : (T)0;
     }
     const int B = b + (b & 1), np = B / 2;
-    const double eps2 = sizeof(T) == 8 ? 1e-30 : 1e-14;
+    // stop once the off-diagonal mass is at the rounding level of T: about
+    // b^2 (10 eps)^2 of the diagonal mass
+    const double eps2 = sizeof(T) == 8 ? 1e-26 : 1e-9;
     __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
         double off = 0.0, dia = 0.0;
