@@ -68,6 +68,13 @@ cudaError_t launch_trace(const void* R, int layout, int dtype, int64_t n, int64_
                          double* partial, unsigned int* counter, double* sc, cudaStream_t st);
 cudaError_t launch_set_u(double* sc, double u, cudaStream_t st);
 
+// ---- L2 residency of the bf16 R (vne_power.cu) ---------------------------------
+// Rows [0, l2_keep_rows) of a matrix whose rows take row_bytes are loaded with
+// an evict-last L2 policy by the power-method and tensor-core kernels, so that
+// they stay in L2 from one pass over R to the next; the rest streams with
+// evict-first.  Budget: VNE_L2_KEEP_MB (MB of the 129 MB L2; default 0, off).
+int64_t l2_keep_rows(int64_t rows, int64_t row_bytes);
+
 // ---- power method (vne_power.cu) ---------------------------------------------
 // x vectors are stored [trial][row] in float (bf16/FP32 paths) or double (FP64).
 template <typename TX>

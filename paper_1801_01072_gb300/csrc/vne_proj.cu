@@ -804,9 +804,11 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, in
         U[e] = (e / b == e % b) ? (T)1 : (T)0;
     }
     const int B = b + (b & 1), np = B / 2;
-    // stop once the off-diagonal mass is at the rounding level of T: about
-    // b^2 (10 eps)^2 of the diagonal mass
-    const double eps2 = sizeof(T) == 8 ? 1e-26 : 1e-9;
+    // stop when the off-diagonal mass is negligible, or (after 4 sweeps) when
+    // a sweep no longer halves it: convergence is quadratic until the rounding
+    // level of T, where the mass stays put
+    const double eps2 = sizeof(T) == 8 ? 1e-30 : 1e-16;
+    double off_prev = 0.0;
     __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
         double off = 0.0, dia = 0.0;
@@ -833,8 +835,9 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, in
         if (tid == 0) {
             double d = 0.0;
             for (int w = 0; w < 8; ++w) d += red[w];
-            stop = !(offt > eps2 * d);
+            stop = !(offt > eps2 * d) || (sweep >= 4 && offt > 0.5 * off_prev);
         }
+        off_prev = offt;
         __syncthreads();
         if (stop) break;
         for (int r = 0; r < B - 1; ++r) {

@@ -186,6 +186,7 @@ struct TcArgs {
     int BN, stages, nkb, x3;
     int CM, CN;  // cluster shape: CM CTAs along M share B tiles, CN along N share A tiles
     int ksplit;  // 2: a CTA pair (cluster along z) splits K and swaps half accumulators
+    int64_t keep_rows;  // row tiles starting below this load R evict-last (kept in L2)
     int epi_tma;       // 1: Y_{t-1}, Y_{t-2} of the CTA's own chunks arrive by TMA into smem
     uint32_t ops_off;  // byte offset of that operand area in the 1024-aligned smem
     uint32_t body;     // bytes before the barrier tail: max(operand ring, operand area end)
@@ -281,9 +282,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool timed_out = false;
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        // R streams through L2 once (evict first); the Y shadows are re-read
-        // by every row tile (evict last).
-        const uint64_t pol_R = policy_evict_first();
+        // R: the rows kept in L2 from pass to pass (power method and earlier
+        // steps) load evict-last, the rest streams evict-first; the Y shadows
+        // are re-read by every row tile (evict last).
+        const uint64_t pol_R = (int64_t)m0 < a.keep_rows ? policy_evict_last() : policy_evict_first();
         const uint64_t pol_Y = policy_evict_last();
         int issued_kb = 0;
         for (int i = 0; i < nkb_local && rank_ok; ++i) {
@@ -781,6 +783,8 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.CM = sh.CM;
     a.CN = sh.CN;
     a.ksplit = sh.ksplit;
+    // L2 residency: the rows the power method keeps (same budget; bf16x3 streams R_hi and R_lo)
+    a.keep_rows = l2_keep_rows(s.rows_pad, s.ldk * 2 * (x3 ? 2 : 1));
     CUtensorMap mYp, mYp2;
     if (epi_tma) {
         epi_tma = make_map(&mYp, s.Yprev, s.n, s.S, s.n, TC_BM, 32, true) &&
