@@ -791,18 +791,22 @@ constexpr int kJacobiMaxB = 64;
 template <typename T>
 __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, int b,
                                                 double* __restrict__ lam, double* __restrict__ Uout) {
+    // A and U with row stride b + 1: the column updates (lanes along a column)
+    // then fall in distinct shared-memory banks
     extern __shared__ unsigned char jac_raw[];
+    const int ld = b + 1;
     T* A = reinterpret_cast<T*>(jac_raw);
-    T* U = A + b * b;
+    T* U = A + b * ld;
     __shared__ T rc[kJacobiMaxB / 2 + 1][2];
     __shared__ int rp[kJacobiMaxB / 2 + 1][2];
     __shared__ double red[8];
     __shared__ int stop;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < b * b; e += blockDim.x) {
-        A[e] = (T)G[e];
-        U[e] = (e / b == e % b) ? (T)1 : (T)0;
-    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int i = warp; i < b; i += nwarps)
+        for (int j = lane; j < b; j += 32) {
+            A[i * ld + j] = (T)G[i * b + j];
+            U[i * ld + j] = (i == j) ? (T)1 : (T)0;
+        }
     const int B = b + (b & 1), np = B / 2;
     // stop when the off-diagonal mass is negligible, or (after 4 sweeps) when
     // a sweep no longer halves it: convergence is quadratic until the rounding
@@ -812,29 +816,29 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, in
     __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
         double off = 0.0, dia = 0.0;
-        for (int e = tid; e < b * b; e += blockDim.x) {
-            const int i = e / b, j = e % b;
-            const double v = (double)A[e];
-            if (i > j) off += v * v;
-            else if (i == j) dia += v * v;
-        }
+        for (int i = warp; i < b; i += nwarps)
+            for (int j = lane; j < b; j += 32) {
+                const double v = (double)A[i * ld + j];
+                if (i > j) off += v * v;
+                else if (i == j) dia += v * v;
+            }
         off = warp_sum(off);
         dia = warp_sum(dia);
-        if ((tid & 31) == 0) red[tid >> 5] = off;
+        if (lane == 0) red[warp] = off;
         __syncthreads();
         if (tid == 0) {
             double o = 0.0;
-            for (int w = 0; w < 8; ++w) o += red[w];
+            for (int w = 0; w < nwarps; ++w) o += red[w];
             red[0] = o;
         }
         __syncthreads();
         const double offt = red[0];
         __syncthreads();
-        if ((tid & 31) == 0) red[tid >> 5] = dia;
+        if (lane == 0) red[warp] = dia;
         __syncthreads();
         if (tid == 0) {
             double d = 0.0;
-            for (int w = 0; w < 8; ++w) d += red[w];
+            for (int w = 0; w < nwarps; ++w) d += red[w];
             stop = !(offt > eps2 * d) || (sweep >= 4 && offt > 0.5 * off_prev);
         }
         off_prev = offt;
@@ -857,9 +861,9 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, in
                 }
                 T c = (T)1, sn = (T)0;
                 if (q < b) {
-                    const T apq = A[p * b + q];
+                    const T apq = A[p * ld + q];
                     if (apq != (T)0) {
-                        const T th = (A[q * b + q] - A[p * b + p]) / ((T)2 * apq);
+                        const T th = (A[q * ld + q] - A[p * ld + p]) / ((T)2 * apq);
                         const T t = th != (T)0 ? (th > (T)0 ? (T)1 : (T)-1) /
                                                      (fabs(th) + sqrt(th * th + (T)1))
                                                : (T)1;
@@ -873,39 +877,42 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ G, in
                 rp[tid][1] = q;
             }
             __syncthreads();
-            for (int e = tid; e < np * b; e += blockDim.x) {  // rows: A <- J^T A
-                const int k = e / b, j = e % b;
+            for (int k = warp; k < np; k += nwarps) {  // rows: A <- J^T A
                 const int p = rp[k][0], q = rp[k][1];
                 if (q >= b) continue;
                 const T c = rc[k][0], sn = rc[k][1];
-                const T ap = A[p * b + j], aq = A[q * b + j];
-                A[p * b + j] = c * ap - sn * aq;
-                A[q * b + j] = sn * ap + c * aq;
+                for (int j = lane; j < b; j += 32) {
+                    const T ap = A[p * ld + j], aq = A[q * ld + j];
+                    A[p * ld + j] = c * ap - sn * aq;
+                    A[q * ld + j] = sn * ap + c * aq;
+                }
             }
             __syncthreads();
-            for (int e = tid; e < np * b; e += blockDim.x) {  // columns: A <- A J, U <- U J
-                const int k = e / b, i = e % b;
+            for (int k = warp; k < np; k += nwarps) {  // columns: A <- A J, U <- U J
                 const int p = rp[k][0], q = rp[k][1];
                 if (q >= b) continue;
                 const T c = rc[k][0], sn = rc[k][1];
-                const T ap = A[i * b + p], aq = A[i * b + q];
-                A[i * b + p] = c * ap - sn * aq;
-                A[i * b + q] = sn * ap + c * aq;
-                const T up = U[i * b + p], uq = U[i * b + q];
-                U[i * b + p] = c * up - sn * uq;
-                U[i * b + q] = sn * up + c * uq;
+                for (int i = lane; i < b; i += 32) {
+                    const T ap = A[i * ld + p], aq = A[i * ld + q];
+                    A[i * ld + p] = c * ap - sn * aq;
+                    A[i * ld + q] = sn * ap + c * aq;
+                    const T up = U[i * ld + p], uq = U[i * ld + q];
+                    U[i * ld + p] = c * up - sn * uq;
+                    U[i * ld + q] = sn * up + c * uq;
+                }
             }
             __syncthreads();
         }
     }
-    for (int e = tid; e < b * b; e += blockDim.x) Uout[e] = (double)U[e];
-    for (int i = tid; i < b; i += blockDim.x) lam[i] = (double)A[i * b + i];
+    for (int i = warp; i < b; i += nwarps)
+        for (int j = lane; j < b; j += 32) Uout[i * b + j] = (double)U[i * ld + j];
+    for (int i = tid; i < b; i += blockDim.x) lam[i] = (double)A[i * ld + i];
 }
 
 template <typename T>
 cudaError_t launch_jacobi(const double* G, int b, double* lam, double* U, cudaStream_t st) {
     if (b < 1 || b > kJacobiMaxB) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)2 * b * b * sizeof(T);
+    const size_t smem = (size_t)2 * b * (b + 1) * sizeof(T);
     if (smem > 48 * 1024) {
         cudaError_t r = cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
