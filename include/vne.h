@@ -354,9 +354,10 @@ vne_status vne_probe_block(vne_handle* h, int64_t n, int32_t s, int32_t probe, u
 /* Per-kernel timing: when enabled, the handle records CUDA events on the call's
  * stream around the launches of kernel class `kind` (0 = dense tensor-core
  * steps, 1 = dense SIMT steps, 2 = banded steps, 3 = power-method products):
- * around each launch for classes 1-3, and around the whole run of consecutive
- * tensor-core steps of a call for class 0 (those launches overlap each other's
- * start-up, which an event between them would prevent).  vne_profile_read
+ * around each launch for classes 1 and 2, and around the whole run of
+ * consecutive launches of a call for classes 0 and 3 (the tensor-core steps and
+ * the power-method products overlap each other's start-up, which an event
+ * between them would prevent).  vne_profile_read
  * returns the total time (ms) and the number of launches since the last reset. */
 vne_status vne_profile_enable(vne_handle* h, int32_t on);
 vne_status vne_profile_read(vne_handle* h, int32_t kind, double* total_ms, int64_t* launches);

@@ -411,18 +411,20 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         const int rdt = tc ? 2 : (f64 ? 0 : 1);
         const void* Rp = tc ? (const void*)Rhi : Rk;
         const int64_t ldp = tc ? ldk : ldr;
+        // the products are timed as one span: an event between two of them
+        // would stop the next one from starting early (programmatic launch)
+        c.prof_begin();
         for (int it = 0; it <= p->power_iters && c.ok(); ++it) {
             const int fin = it == p->power_iters;
-            c.prof_begin();
             if (dense)
                 c.launched(launch_power_step_dense(Rp, rdt, n, ldp, xa, xb, f64, q, sc, ppart,
                                                    counter, fin, u_scale, power_blocks, c.st));
             else
                 c.launched(launch_power_step_dia(Rk, f64 ? 0 : 1, n, ldr, D, xa, xb, q, sc, ppart,
                                                  counter, fin, u_scale, power_blocks, c.st));
-            c.prof_end(3);
             std::swap(xa, xb);
         }
+        c.prof_end(3, p->power_iters + 1);
     } else {
         c.launched(launch_set_u(sc, p->u_override > 0.0 ? p->u_override : 1.0, c.st));
     }

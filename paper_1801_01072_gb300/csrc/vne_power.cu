@@ -334,8 +334,7 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         timeout = 0;
     }
-    load_inv_norms<float>(sc, 1, inv_sh);  // includes __syncthreads
-    const float inv = inv_sh[0];
+    __syncthreads();
     auto issue = [&](int blk) {
         const int st = blk % kStreamStages;
         const int64_t rb = r0 + (int64_t)blk * kStreamRB;
@@ -345,8 +344,13 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
             bulk_load_hint(sraw + ((size_t)st * kStreamRB + r) * row_bytes, R + (rb + r) * ld,
                            row_bytes, &full[st], l2_policy(rb + r - r0 < keep_per_cta));
     };
+    // R does not change between products: its first stages are requested
+    // before waiting for the previous product (programmatic dependent launch)
     if (tid == 0)
         for (int blk = 0; blk < nblk && blk < kStreamStages; ++blk) issue(blk);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    load_inv_norms<float>(sc, 1, inv_sh);  // includes __syncthreads
+    const float inv = inv_sh[0];
     // x of this thread's column groups (g = gt + 128 i), already divided by ||x||
     float xr[NG][8];
 #pragma unroll
@@ -410,6 +414,8 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
         group_sync(bar_id, 128);  // red[grp] reused by this half's next block
     }
     __syncthreads();
+    // the next product may start its prologue and its first R loads now
+    if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0 && timeout) {
         // let every copy already issued land before the block exits
         volatile int never = 0;
@@ -465,10 +471,21 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_
     do {                                                                                       \
         auto kern = k_power_dense_bf16_stream<NGV>;                                            \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e == cudaSuccess)                                                                  \
-            kern<<<g, 256, smem, st>>>((const __nv_bfloat16*)R, n, ld, (const float*)x,      \
-                                       (float*)y, sc, partial, counter, final_step, u_scale,  \
-                                       keep_per_cta);                                         \
+        if (e == cudaSuccess) {                                                                \
+            cudaLaunchConfig_t cfg = {};                                                       \
+            cudaLaunchAttribute at[1];                                                         \
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                     \
+            at[0].val.programmaticStreamSerializationAllowed = 1;                              \
+            cfg.gridDim = dim3(g);                                                             \
+            cfg.blockDim = dim3(256);                                                          \
+            cfg.dynamicSmemBytes = smem;                                                       \
+            cfg.stream = st;                                                                   \
+            cfg.attrs = at;                                                                    \
+            cfg.numAttrs = 1;                                                                  \
+            e = cudaLaunchKernelEx(&cfg, kern, (const __nv_bfloat16*)R, n, ld,                 \
+                                   (const float*)x, (float*)y, sc, partial, counter,           \
+                                   final_step, u_scale, keep_per_cta);                        \
+        }                                                                                      \
     } while (0)
             if (smem <= 200 * 1024) {
                 if (ng <= 1) VNE_STREAM(1);
