@@ -64,7 +64,7 @@ def profiled_traffic(profile_name, source):
         return None
     for line in text.splitlines():
         if line.strip().startswith("- traffic_bytes_per_launch:"):
-            return int(line.split(":")[1])
+            return int(line.split(":")[1].split()[0])
     return None
 
 

@@ -10,6 +10,8 @@
 // The Gram route squares the singular values: the top-k p~_i keep full
 // relative accuracy, values below ~1e-8 p~_1 (FP64) only absolute accuracy,
 // and they enter H~ as p ln(1/p), i.e. at the 1e-15 level.
+#include <cstdlib>
+
 #include "vne_common.cuh"
 #include "vne_internal.h"
 
@@ -572,6 +574,12 @@ __global__ void __launch_bounds__(32) k_bisect_multi(const double* __restrict__ 
 int eig_cluster_size(int N) {
     int C = 1;
     while (C < kClusterMax && C * 16 < N) C *= 2;
+    static int force = -1;
+    if (force < 0) {
+        force = 0;
+        if (const char* e = getenv("VNE_EIG_CLUSTER")) force = atoi(e);
+    }
+    if (force == 1 || force == 2 || force == 4 || force == 8 || force == 16) C = force;
     if ((int64_t)((N + C - 1) / C) * N * 8 > 160 * 1024) return -1;
     return C;
 }
