@@ -383,6 +383,22 @@ def run_gpu_learned(args, w, Rh, p, world, rank, local, dev):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del data
+    # held out: 10k sampled spectra at n = 8192 (outside the training sizes),
+    # degree 16 + network against plain degree 16 and plain degree 64 on the
+    # same probes, errors against the exact entropies
+    held = {}
+    sp = synth.learned_sample_params(10000, 77, 8192, 8192)
+    a16 = learned.spectral_samples(sp, m=16, s=s, device=local)
+    a64 = learned.spectral_samples(sp, m=64, s=s, device=local)
+    corr = learned.mlp_forward(theta, a16["features"]).double()
+    nn_ = torch.tensor(sp["n"], dtype=torch.float64, device=dev)
+    uu = torch.exp(10.0 * a16["features"][:, 18].double())
+    He = a16["H_exact"]
+    for key, est in (("degree16", a16["H_low"]), ("degree64", a64["H_low"]),
+                     ("degree16_plus_network", a16["H_low"] + corr * nn_ * uu / 100.0)):
+        r = ((est - He).abs() / He)
+        held[key] = {"mean_rel_err": float(r.mean()), "p90_rel_err": float(r.quantile(0.9))}
+    del a16, a64
 
     def step(R):
         return learned.entropy_chebyshev_learned(R, theta, s=s, seed=seed, precision=prec,
@@ -469,6 +485,7 @@ def run_gpu_learned(args, w, Rh, p, world, rank, local, dev):
         "clocks": clk.summary(),
         "training": {"spectra": w["train_count"], "epochs": w["train_epochs"],
                      "seconds_incl_sampling": train_s, "final_loss": hist[-1][1] if hist else None},
+        "held_out_10k_spectra_n8192": held,
         "vs_plain_fp64": {"m": w["m_ref"], "ms": f64_ms, "speedup": f64_ms / (ms_max / args.steps),
                           "rel_err_exact_plain_fp64": abs(ref.H - H_exact) / H_exact},
         "estimates": {"H_learned": out.H, "H_plain_m16": out.H_plain, "H_exact": H_exact,
