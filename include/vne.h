@@ -366,6 +366,13 @@ vne_status vne_profile_reset(vne_handle* h);
 /* Number of the library's own kernel launches enqueued by this handle so far. */
 int64_t vne_launch_count(const vne_handle* h);
 
+/* Check of the library's failure path for lost arrivals (no counterpart in
+ * the paper): launches a kernel whose mbarrier wait has no arrival, so its
+ * bounded wait gives up after the library's deadline (2 s), flags the
+ * timeout and returns.  Expected result: VNE_ERR_TIMEOUT, with the context
+ * still usable for the next call.  Synchronises `stream`. */
+vne_status vne_selftest_timeout(vne_handle* h, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* vne_status_string(vne_status s);
 /* cudaError_t behind the last VNE_ERR_CUDA of this handle (0 if none). */

@@ -1097,6 +1097,23 @@ vne_status vne_tc_autotune(vne_handle* h, const vne_matrix* R, const vne_params*
     return VNE_OK;
 }
 
+vne_status vne_selftest_timeout(vne_handle* h, void* stream) {
+    if (!h) return VNE_ERR_INVALID_ARG;
+    DeviceGuard guard(h->device);
+    vne_status vs = ensure_ws(h, SC_COUNT * sizeof(double) + 4096);
+    if (vs != VNE_OK) return vs;
+    double* sc = reinterpret_cast<double*>(h->ws);
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(sc, 0, SC_COUNT * sizeof(double), st);
+    if (e == cudaSuccess) e = launch_wait_never(sc, st);
+    h->launches++;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->host_sc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return map_err(h, e);
+    return slot_status(h->host_sc, 0);
+}
+
 vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,
                           double* lam_out, void* stream) {
     if (!lam_out) return VNE_ERR_INVALID_ARG;

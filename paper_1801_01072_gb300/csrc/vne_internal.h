@@ -191,6 +191,9 @@ cudaError_t mlp_train_step(float* th, float* am, float* av, int step, float lr, 
 cudaError_t launch_learned(const double* mom, int m, int s, int64_t n, double* sc,
                            const float* params, float* ws, int* launches, cudaStream_t st);
 
+// ---- bounded-wait check (vne_selftest.cu) ----------------------------------------
+cudaError_t launch_wait_never(double* sc, cudaStream_t st);
+
 // ---- combine (vne_combine.cu) ----------------------------------------------------
 // moments[k][j] for k = 0..m of the Chebyshev columns / Taylor columns, then
 // the FP64 estimates into sc.

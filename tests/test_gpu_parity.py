@@ -288,3 +288,18 @@ def test_launches_are_counted():
     R, p, _ = synth.dense_exp(64, 10.0, seed=8)
     vne.entropy_chebyshev(dev(R), 4, 4)
     assert h.launch_count() > before
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    # a wait that nothing satisfies ends with VNE_ERR_TIMEOUT after the
+    # deadline; the next call on the same handle and stream works
+    import time
+    h = vne._handle(0)
+    t0 = time.perf_counter()
+    st = h.lib.vne_selftest_timeout(h.h, None)
+    dt = time.perf_counter() - t0
+    assert st == 6, st  # VNE_ERR_TIMEOUT
+    assert 1.5 < dt < 30.0
+    R, p, _ = synth.dense_exp(64, 10.0, seed=1)
+    res = vne.entropy_chebyshev(dev(R), 6, 4, seed=1, precision="f64")
+    assert np.isfinite(res.H)
