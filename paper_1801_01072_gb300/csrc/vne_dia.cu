@@ -285,7 +285,9 @@ template <typename T, int HB>
 static int grid_hb(int64_t n, int ncols, int sm_count) {
     using C = DiaCfg<T, HB>;
     const int nw = (ncols + 31) / 32;
-    const size_t smem = (size_t)C::NR * C::BP * sizeof(T) + (size_t)(C::CH + 2 * C::W) * 4 * 8;
+    // the sign bits take ceil(s / 64) words per row, s <= ncols
+    const size_t smem = (size_t)C::NR * C::BP * sizeof(T) +
+                        (size_t)(C::CH + 2 * C::W) * ((ncols + 63) / 64) * 8;
     auto kern = (sizeof(T) == 4 && ncols == 64) ? k_dia_step<T, HB, 64> : k_dia_step<T, HB, 0>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
