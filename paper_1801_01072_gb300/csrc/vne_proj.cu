@@ -511,6 +511,33 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
     return c;
 }
 
+// The same count in FP32 (rescaling outside [2^-60, 2^60]): cheap, and
+// exact away from the eigenvalues; used only to narrow the bracket before the
+// FP64 rounds, which re-check it.
+__device__ __forceinline__ int sturm_count_f32(const float* d, const float* e2, int N, float x) {
+    int c = 0;
+    float pm2 = 0.f, pm1 = 1.f;
+    for (int i = 0; i < N; ++i) {
+        float p = (d[i] - x) * pm1;
+        if (i > 0) p = fmaf(-e2[i - 1], pm2, p);
+        int bits = __float_as_int(p);
+        if ((bits << 1) == 0) {
+            p = -pm1 * 0x1.0p-30f;
+            bits = __float_as_int(p);
+        }
+        c += (int)(((unsigned)bits >> 31) ^ ((unsigned)__float_as_int(pm1) >> 31));
+        const int ex = ((bits >> 23) & 0xFF) - 127;
+        if (ex > 60 || ex < -60) {
+            const float sc = __int_as_float((127 - ex) << 23);  // 2^-ex
+            p *= sc;
+            pm1 *= sc;
+        }
+        pm2 = pm1;
+        pm1 = p;
+    }
+    return c;
+}
+
 // Multisection: each group of kMsLanes lanes owns one eigenvalue (ascending
 // rank j >= j0) and splits its bracket [a, b] (count(a) <= j < count(b)) at kMsLanes interior points
 // per round, keeping the sub-interval where the count passes j.  It stops
@@ -522,11 +549,14 @@ __global__ void __launch_bounds__(32) k_bisect_multi(const double* __restrict__ 
                                                      const double* __restrict__ e_in, int N,
                                                      int j0, double* __restrict__ evals) {
     __shared__ double d[kEigMaxN], e[kEigMaxN], e2[kEigMaxN];
+    __shared__ float df[kEigMaxN], e2f[kEigMaxN];
     const int lane = threadIdx.x;
     for (int i = lane; i < N; i += 32) {
         d[i] = d_in[i];
         e[i] = e_in[i];
         e2[i] = e_in[i] * e_in[i];
+        df[i] = (float)d[i];
+        e2f[i] = (float)e2[i];
     }
     __syncwarp();
     double lo = 1e308, hi = -1e308, emax2 = 0.0;
@@ -552,8 +582,36 @@ __global__ void __launch_bounds__(32) k_bisect_multi(const double* __restrict__ 
     const unsigned gmask =
         kMsLanes == 32 ? 0xFFFFFFFFu : (((1u << (kMsLanes & 31)) - 1u) << (g * kMsLanes));
     double a = lo - pad, b = hi + pad;
+    // FP32 rounds down to ~64 FP32 ulps of the scale, then an FP64 check of the
+    // bracket (count(a) <= j < count(b)); a bracket that fails it restarts
+    // from the Gershgorin bounds
+    const double tol32 = 64.0 * 1.1920928955078125e-07 * scale;
+    for (int round = 0; round < 16; ++round) {
+        if (!(b - a > tol32)) break;
+        const double x = a + (b - a) * ((double)(l + 1) / (double)(kMsLanes + 1));
+        const bool up = live ? sturm_count_f32(df, e2f, N, (float)x) >= j + 1 : true;
+        const unsigned bal = (__ballot_sync(gmask, up) & gmask) >> (g * kMsLanes);
+        const int L = bal ? __ffs(bal) - 1 : kMsLanes;
+        const double xl = __shfl_sync(gmask, x, g * kMsLanes + (L > 0 ? L - 1 : 0));
+        const double xr = __shfl_sync(gmask, x, g * kMsLanes + (L < kMsLanes ? L : kMsLanes - 1));
+        const double na = L > 0 ? xl : a;
+        const double nb = L < kMsLanes ? xr : b;
+        if (!(na >= a && nb <= b && na < nb)) break;
+        a = na;
+        b = nb;
+    }
+    {
+        const double xe = l == 0 ? a : b;
+        const int ce = (live && l < 2) ? sturm_count(d, e2, N, xe) : 0;
+        const int ca = __shfl_sync(gmask, ce, g * kMsLanes);
+        const int cb = __shfl_sync(gmask, ce, g * kMsLanes + 1);
+        if (live && !(ca <= j && cb >= j + 1)) {
+            a = lo - pad;
+            b = hi + pad;
+        }
+    }
     for (int round = 0; round < 64; ++round) {
-        if (!(b - a > tol)) break;  // uniform within the half-warp
+        if (!(b - a > tol)) break;  // uniform within the lane group
         const double x = a + (b - a) * ((double)(l + 1) / (double)(kMsLanes + 1));
         const bool up = live ? sturm_count(d, e2, N, x) >= j + 1 : true;
         const unsigned bal = (__ballot_sync(gmask, up) & gmask) >> (g * kMsLanes);
