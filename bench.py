@@ -939,7 +939,10 @@ def run_gpu(args):
             peak = peak_value(pk, "bf16_tflops_sustained", "bf16_tflops")
             bound, unit = "tensor", "TFLOP/s"
         else:
-            peak, bound, unit = None, "alu", "TFLOP/s"
+            # CUDA-core peaks: FP32 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 the
+            # nominal 1.25 TFLOP/s (an FMA-chain probe measured 1.20)
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == "f32" else 1.25
+            bound, unit = "alu", "TFLOP/s"
         # DRAM bytes of one fused 256-column launch (ncu), when the source is unchanged
         traffic = profiled_traffic("k_tc_step_dense_n8192.md", "vne_tc.cu") \
             if (kind == 0 and args.workload == "dense_powerlaw_n8192") else None
@@ -947,7 +950,8 @@ def run_gpu(args):
                 "frac": (achieved / peak) if (achieved and peak) else None, "traffic": traffic,
                 "kernel": "k_tc_step" if kind == 0 else "k_simt_step",
                 "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
-                "peak_source": pk_src + (" bf16 sustained" if peak else "")}
+                "peak_source": pk_src + " bf16 sustained" if prec in ("bf16", "bf16x3")
+                else ("derived: FP32 lanes x 2 x max SM clock" if prec == "f32" else "nominal FP64")}
     else:
         # algorithmic bytes of the m banded steps of one estimate: every step reads
         # the band (4n(D)) and the packed signs (8n per 64 probes) and writes Y_t
