@@ -945,7 +945,7 @@ def run_gpu(args):
             bound, unit = "alu", "TFLOP/s"
         # DRAM bytes of one fused 256-column launch (ncu), when the source is unchanged
         traffic = profiled_traffic("k_tc_step_dense_n8192.md", "vne_tc.cu") \
-            if (kind == 0 and args.workload == "dense_powerlaw_n8192") else None
+            if (prec == "bf16" and args.workload == "dense_powerlaw_n8192") else None
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": (achieved / peak) if (achieved and peak) else None, "traffic": traffic,
                 "kernel": "k_tc_step" if kind == 0 else "k_simt_step",
