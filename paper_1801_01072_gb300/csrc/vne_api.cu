@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -863,8 +864,21 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
 namespace {
 uint64_t mix(uint64_t hsh, uint64_t v) { return splitmix_out(hsh ^ v, 0x51ull); }
 
+// Streams of a batched call: VNE_BATCH_STREAMS (1..64), default 8.
+int batch_streams() {
+    static int k = 0;
+    if (!k) {
+        k = 8;
+        if (const char* e = getenv("VNE_BATCH_STREAMS")) {
+            const int v = atoi(e);
+            if (v >= 1 && v <= 64) k = v;
+        }
+    }
+    return k;
+}
+
 vne_status batch_resources(vne_handle* h, size_t ws_bytes, size_t count) {
-    const int K = 8;
+    const int K = batch_streams();
     while ((int)h->bstreams.size() < K) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -940,7 +954,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     }
     vne_status vs = batch_resources(h, off[count], (size_t)count);
     if (vs != VNE_OK) return vs;
-    const int K = 8;
+    const int K = batch_streams();
     cudaStream_t user = (cudaStream_t)stream;
     cudaStream_t origin = h->bstreams[0];
     const int saved_prof = h->prof_on;
