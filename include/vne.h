@@ -167,7 +167,7 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
  * alg:power, applied to each).  Rs[i] (DEVICE memory, any layout and dtype a
  * single call accepts) is estimated with the same parameters p; method is
  * VNE_METHOD_CHEBYSHEV, VNE_METHOD_TAYLOR or VNE_METHOD_BOTH.  The matrices
- * run concurrently on the handle's streams (8, or VNE_BATCH_STREAMS in 1..64,
+ * run concurrently on the handle's streams (32, or VNE_BATCH_STREAMS in 1..64,
  * read once per process), each with its own slice of a
  * batch workspace.  use_graph != 0 captures the whole batch once as a CUDA
  * graph and replays it while the matrices (pointers, sizes, layouts), p and

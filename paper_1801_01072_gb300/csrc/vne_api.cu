@@ -864,11 +864,12 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
 namespace {
 uint64_t mix(uint64_t hsh, uint64_t v) { return splitmix_out(hsh ^ v, 0x51ull); }
 
-// Streams of a batched call: VNE_BATCH_STREAMS (1..64), default 8.
+// Streams of a batched call: VNE_BATCH_STREAMS (1..64), default 32 (measured on
+// the 256-matrix batch: 6.40k entropies/s with 8 streams, 7.01k with 16, 7.34k with 32).
 int batch_streams() {
     static int k = 0;
     if (!k) {
-        k = 8;
+        k = 32;
         if (const char* e = getenv("VNE_BATCH_STREAMS")) {
             const int v = atoi(e);
             if (v >= 1 && v <= 64) k = v;
