@@ -652,7 +652,7 @@ def run_gpu_batched(args, w, specs, world, rank, local, dev):
                    "probe": w["probe"], "power_iters": w["power_iters"], "precision": prec,
                    "input": "FP64 matrices resident in HBM (%.1f GB)" % (h2d / 1e9),
                    "l2": "inputs larger than L2", "graph": "one CUDA graph launch per step",
-                   "parallelism": f"8 streams inside the graph, {world} GPU(s)"},
+                   "parallelism": f"32 streams inside the graph, {world} GPU(s)"},
         "e2e": {"value": world * len(specs) * 1e3 / e2e_ms, "unit": "entropies/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(specs) * 200 * 8},
         "gpu_launches": int(per_batch * args.steps),  # kernels of the replayed graph
