@@ -166,6 +166,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
           "=r"(r[31])                                                                           \
         : "r"(taddr))
 
+// Named barrier 1 (barrier 0 is __syncthreads): `count` threads of whole warps.
+__device__ __forceinline__ void named_bar_arrive(uint32_t id, uint32_t count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -217,6 +225,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epi_bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][BN]
+    float* gstash = red + 4 * a.BN;                         // [2 warps][32 cols][32 lanes]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM;
@@ -272,48 +281,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (in_cluster) cluster_sync_all();  // peers' barriers are initialised before any multicast
     tc_fence_after();
+    // R: the rows kept in L2 from pass to pass (power method and earlier steps)
+    // load evict-last, the rest streams evict-first; the Y shadows are re-read
+    // by every row tile (evict last).  This CTA's slices: rows [cy*arows,
+    // +arows) of A, [cx*brows, +brows) of B.
+    const bool producer = warp == 0 && lane == 0;
+    const uint64_t pol_R =
+        producer ? ((int64_t)m0 < a.keep_rows ? policy_evict_last() : policy_evict_first()) : 0ull;
+    const uint32_t offA = (uint32_t)(cy * arows) * (TC_BK * 2);
+    const uint32_t offB = (uint32_t)(cx * brows) * (TC_BK * 2);
+    auto load_A = [&](int i) {
+        const int st = i % a.stages;
+        uint8_t* sA = smem + (size_t)st * stage_bytes;
+        const int kb = kb_begin + i;
+        mbar_expect_tx(&full_bar[st], stage_bytes);  // whole tiles (A and B) arrive here
+        tma_load_2d_hint(sA + offA, &mapRhi, &full_bar[st], kb * TC_BK, m0 + cy * arows, maskA, pol_R);
+        if (a.x3)
+            tma_load_2d_hint(sA + bytesA + bytesB + offA, &mapRlo, &full_bar[st], kb * TC_BK,
+                             m0 + cy * arows, maskA, pol_R);
+    };
+    // R is written before the steps start and never by a step, so the A tiles
+    // of the first ring round are requested before waiting on the previous
+    // step (their slots are fresh: no empty-barrier wait is needed).
+    const int pre = rank_ok ? (nkb_local < a.stages ? nkb_local : a.stages) : 0;
+    if (producer)
+        for (int i = 0; i < pre; ++i) load_A(i);
     // Launched as a programmatic dependent of the previous step: everything
-    // above (barriers, TMEM, tensor-map prefetch) overlapped that step's tail;
-    // from here on this step reads what the previous one wrote.
+    // above (barriers, TMEM, tensor-map prefetch, the first R tiles) overlapped
+    // that step's tail; from here on this step reads what the previous one wrote.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t tmem_base = *tmem_slot;
     if (!rank_ok && threadIdx.x == 0) *abort_flag = 1;
 
     bool timed_out = false;
-    if (warp == 0 && lane == 0) {
+    if (producer) {
         // ---------------- TMA producer ----------------
-        // R: the rows kept in L2 from pass to pass (power method and earlier
-        // steps) load evict-last, the rest streams evict-first; the Y shadows
-        // are re-read by every row tile (evict last).
-        const uint64_t pol_R = (int64_t)m0 < a.keep_rows ? policy_evict_last() : policy_evict_first();
         const uint64_t pol_Y = policy_evict_last();
         int issued_kb = 0;
         for (int i = 0; i < nkb_local && rank_ok; ++i) {
             const int kb = kb_begin + i;
             const int st = i % a.stages;
             const uint32_t ph = (uint32_t)(i / a.stages) & 1u;
-            if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) {
-                timed_out = true;
-                break;
+            if (i >= pre) {
+                if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) {
+                    timed_out = true;
+                    break;
+                }
+                load_A(i);
             }
-            uint8_t* sA = smem + (size_t)st * stage_bytes;
-            uint8_t* sB = sA + bytesA;
-            // this CTA's slices: rows [cy*arows, +arows) of A, [cx*brows, +brows) of B
-            const uint32_t offA = (uint32_t)(cy * arows) * (TC_BK * 2);
-            const uint32_t offB = (uint32_t)(cx * brows) * (TC_BK * 2);
-            mbar_expect_tx(&full_bar[st], stage_bytes);  // whole tiles arrive here
-            tma_load_2d_hint(sA + offA, &mapRhi, &full_bar[st], kb * TC_BK, m0 + cy * arows, maskA,
-                             pol_R);
+            uint8_t* sB = smem + (size_t)st * stage_bytes + bytesA;
             tma_load_2d_hint(sB + offB, &mapYhi, &full_bar[st], kb * TC_BK, n0 + cx * brows, maskB,
                              pol_Y);
-            if (a.x3) {
-                uint8_t* sAl = sB + bytesB;
-                uint8_t* sBl = sAl + bytesA;
-                tma_load_2d_hint(sAl + offA, &mapRlo, &full_bar[st], kb * TC_BK, m0 + cy * arows,
-                                 maskA, pol_R);
-                tma_load_2d_hint(sBl + offB, &mapYlo, &full_bar[st], kb * TC_BK, n0 + cx * brows,
-                                 maskB, pol_Y);
-            }
+            if (a.x3)
+                tma_load_2d_hint(sB + bytesB + bytesA + offB, &mapYlo, &full_bar[st], kb * TC_BK,
+                                 n0 + cx * brows, maskB, pol_Y);
             issued_kb = i + 1;
         }
         if (timed_out) {
@@ -374,29 +395,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int half = nchunks / 2;
     const int ck_lo = a.ksplit > 1 ? kz * half : 0;
     const int ck_hi = a.ksplit > 1 ? ck_lo + half : nchunks;
-    const int RS = half * 32 + 4;  // padded row stride (floats) of the receive buffer
-    // Epilogue operands (G, Y_{t-1}, Y_{t-2}) of a 32-column chunk: every load
-    // of the chunk is issued before any store (the stores could otherwise alias
-    // them and serialise the chunk).  Issuing them during the mainloop instead
-    // was measured slower: they compete with the operand stream.
-    float gv[32], yp[32], yp2[32];
-    auto prefetch = [&](int ck) {
+    const int ck_first = ck_lo + chalf;
+    const int cb0 = a.cols.cheb_c0, cb1 = a.cols.cheb_c0 + a.cols.ncheb;
+    const bool three_term = a.cols.cheb_kind == EPI_CHEB;
+    // G of the 32 columns of chunk ck at this thread's row (0 outside the
+    // active columns); the columns map to consecutive probes unless the chunk
+    // wraps past s.
+    auto load_g = [&](int ck, float* g) {
         const int cbase = n0 + ck * 32;
+        const int j0 = cbase % a.s;
+        const bool nowrap = j0 + 32 <= a.s;
+        const float* gcol = a.G + (int64_t)j0 * a.n + row;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-            const int c = cbase + q;  // warp-uniform
-            gv[q] = 0.f;
-            yp[q] = 0.f;
-            yp2[q] = 0.f;
-            if (c >= a.col_end || !row_ok) continue;
-            const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
-            const int64_t idx = (int64_t)c * a.n + row;
-            gv[q] = __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
-            if (!cheb || a.cols.cheb_kind == EPI_CHEB) yp[q] = __ldg(a.Yprev + idx);
-            if (cheb && a.cols.cheb_kind == EPI_CHEB) yp2[q] = __ldg(a.Yprev2 + idx);
+            const int c = cbase + q;
+            g[q] = 0.f;
+            if (c < a.col_end && row_ok)
+                g[q] = nowrap ? __ldg(gcol + (int64_t)q * a.n)
+                              : __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
         }
     };
-    const int ck_first = ck_lo + chalf;
+    // G does not depend on this step: the first chunk's values are requested
+    // now, so their latency hides behind the mainloop.  Warps 0 and 1 come
+    // here only at the mainloop's end (their lane 0 produces and issues), so
+    // warps 4 and 5, which own the same rows, stage those warps' first chunk
+    // in shared memory; loads still in flight in warps 0 and 1 would hold up
+    // their next shared-memory access and the cluster barrier behind it.
+    float gv[32];
+    if (warp >= 2 && ck_first < ck_hi) load_g(ck_first, gv);
+    if (warp == 4 || warp == 5) {
+        float gs[32];
+        load_g(ck_lo, gs);  // ck_lo < ck_hi: every CTA owns at least one chunk
+        float* dst = gstash + (warp - 4) * 32 * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) dst[q * 32] = gs[q];
+        named_bar_arrive(1, 128);
+    }
 
     // the next step may start its prologue on free SMs now
     if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -413,19 +447,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     // Y_{t-1} and Y_{t-2} of this CTA's own chunks, [chunk][2][32 cols][128 rows]
     // FP32 in smem, by TMA: the operand ring is idle now, and the copies overlap
-    // the accumulator exchange below.
+    // the accumulator exchange below.  A chunk loads only what its columns use:
+    // Y_{t-1} for Taylor and three-term Chebyshev columns, Y_{t-2} for the latter.
     float* ops = reinterpret_cast<float*>(smem + a.ops_off);
     const int nown = ck_hi - ck_lo;
+    auto chunk_needs = [&](int ck, bool& n1, bool& n2) {
+        const int c0 = n0 + ck * 32;
+        const int c1 = c0 + 32 < a.col_end ? c0 + 32 : a.col_end;
+        const int o0 = c0 > cb0 ? c0 : cb0, o1 = c1 < cb1 ? c1 : cb1;
+        const int ncheb = o1 > o0 ? o1 - o0 : 0;
+        const int nall = c1 > c0 ? c1 - c0 : 0;
+        n1 = (nall > ncheb) || (ncheb > 0 && three_term);
+        n2 = ncheb > 0 && three_term;
+    };
     if (a.epi_tma && !aborted && threadIdx.x == 0) {
-        mbar_expect_tx(epi_bar, (uint32_t)nown * 2u * 32u * TC_BM * 4u);
+        uint32_t bytes = 0;
         for (int oc = 0; oc < nown; ++oc) {
+            bool n1, n2;
+            chunk_needs(ck_lo + oc, n1, n2);
+            bytes += (n1 ? 1u : 0u) + (n2 ? 1u : 0u);
+        }
+        mbar_expect_tx(epi_bar, bytes * 32u * TC_BM * 4u);
+        for (int oc = 0; oc < nown; ++oc) {
+            bool n1, n2;
+            chunk_needs(ck_lo + oc, n1, n2);
             const int c0 = n0 + (ck_lo + oc) * 32;
-            tma_load_2d(ops + (size_t)(oc * 2 + 0) * 32 * TC_BM, &mapYp, epi_bar, m0, c0);
-            tma_load_2d(ops + (size_t)(oc * 2 + 1) * 32 * TC_BM, &mapYp2, epi_bar, m0, c0);
+            if (n1) tma_load_2d(ops + (size_t)(oc * 2 + 0) * 32 * TC_BM, &mapYp, epi_bar, m0, c0);
+            if (n2) tma_load_2d(ops + (size_t)(oc * 2 + 1) * 32 * TC_BM, &mapYp2, epi_bar, m0, c0);
         }
     }
 
-    const float* recv = reinterpret_cast<const float*>(smem);
+    // Receive buffer of the split-K exchange: float4 slot (chunk*8 + q)*128 + r
+    // holds columns 4q..4q+3 of row r, so a warp's 16-byte stores and loads
+    // cover 512 contiguous bytes.
+    const float4* recv = reinterpret_cast<const float4*>(smem);
     if (a.ksplit > 1) {
         cluster_sync_all();  // both accumulators are final and both rings are idle
         if (!aborted) {
@@ -436,91 +491,118 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
                 tmem_wait_ld();
                 const uint32_t dst =
-                    rbase + (uint32_t)(((rg * 32 + lane) * RS + (ck - peer * half) * 32) * 4);
+                    rbase + (uint32_t)(((ck - peer * half) * 8 * TC_BM + rg * 32 + lane) * 16);
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    st_cluster_v4(dst + 16 * q, r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+                    st_cluster_v4(dst + (uint32_t)(q * TC_BM * 16), r[4 * q], r[4 * q + 1],
+                                  r[4 * q + 2], r[4 * q + 3]);
             }
         }
         cluster_sync_all();  // the peer's half has landed here
     }
     const bool ops_ready = a.epi_tma && !aborted && mbar_wait(epi_bar, 0u, abort_flag);
-    if (!aborted) {
+
+    // One 32-column chunk: Z from TMEM (plus the peer's half), the step's
+    // update, Y_t and its bf16 shadows, then the moment partial of each column
+    // (transpose-reduce: afterwards lane l holds the 32-row sum of column l).
+    // ypf(q) / yp2f(q) return Y_{t-1} / Y_{t-2} of column q; read only where used.
+    auto finish_chunk = [&](int ck, uint32_t* r, const float* g, auto ypf, auto yp2f) {
+        const int cbase = n0 + ck * 32;
+        if (a.ksplit > 1) {
+            const float4* rp = recv + (ck - ck_lo) * 8 * TC_BM + rg * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 p4 = rp[q * TC_BM];
+                r[4 * q] = __float_as_uint(__uint_as_float(r[4 * q]) + p4.x);
+                r[4 * q + 1] = __float_as_uint(__uint_as_float(r[4 * q + 1]) + p4.y);
+                r[4 * q + 2] = __float_as_uint(__uint_as_float(r[4 * q + 2]) + p4.z);
+                r[4 * q + 3] = __float_as_uint(__uint_as_float(r[4 * q + 3]) + p4.w);
+            }
+        }
+        float v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int c = cbase + q;
+            v[q] = 0.f;
+            if (c >= a.col_end || !row_ok) continue;
+            const float z = __uint_as_float(r[q]);
+            const int64_t idx = (int64_t)c * a.n + row;
+            const bool cheb = c >= cb0 && c < cb1;
+            float y;
+            if (cheb) {
+                if (!three_term) y = fmaf(fa, z, -g[q]);
+                else y = 2.f * fmaf(fa, z, -ypf(q)) - yp2f(q);
+                v[q] = g[q] * y;
+            } else {
+                v[q] = g[q] * z;
+                y = fmaf(-z, finvu, ypf(q));
+            }
+            a.Ynew[idx] = y;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+            a.Yhi_out[(int64_t)c * a.ldk + row] = hi;
+            if (a.Ylo_out)
+                a.Ylo_out[(int64_t)c * a.ldk + row] = __float2bfloat16_rn(y - __bfloat162float(hi));
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < o; ++k) {
+                const float send = upper ? v[k] : v[k + o];
+                const float keep = upper ? v[k + o] : v[k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        red[rg * a.BN + ck * 32 + lane] = v[0];
+    };
+    if (warp < 2) {
+        named_bar_sync(1, 128);  // warps 4 and 5 have staged this warp's first G chunk
+        const float* src = gstash + warp * 32 * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) gv[q] = src[q * 32];
+    }
+    if (!aborted && ops_ready) {
+        // operands in smem; the next chunk's G is requested while this one runs
         for (int ck = ck_first; ck < ck_hi; ck += 2) {
             uint32_t r[32];
-            const uint32_t taddr = tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32);
-            TMEM_LD32(taddr, r);
-            const int cbase = n0 + ck * 32;
-            if (ops_ready) {
-                const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
-                // probe index of the chunk's first column; the 32 columns map to
-                // consecutive probes unless the chunk wraps past s
-                const int j0 = cbase % a.s;
-                const bool nowrap = j0 + 32 <= a.s;
-                const float* gcol = a.G + (int64_t)j0 * a.n + row;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int c = cbase + q;
-                    gv[q] = 0.f;
-                    if (c < a.col_end && row_ok)
-                        gv[q] = nowrap ? __ldg(gcol + (int64_t)q * a.n)
-                                       : __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
-                    yp[q] = ob[q * TC_BM];
-                    yp2[q] = ob[32 * TC_BM + q * TC_BM];
-                }
-            } else {
-                prefetch(ck);
-            }
+            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
+            const bool more = ck + 2 < ck_hi;
+            float gn[32];
+            if (more) load_g(ck + 2, gn);
+            const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
             tmem_wait_ld();
-            if (a.ksplit > 1) {
-                const float4* rp = reinterpret_cast<const float4*>(
-                    recv + (rg * 32 + lane) * RS + (ck - ck_lo) * 32);
+            finish_chunk(
+                ck, r, gv, [&](int q) { return ob[q * TC_BM]; },
+                [&](int q) { return ob[32 * TC_BM + q * TC_BM]; });
+            if (more) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 p4 = rp[q];
-                    r[4 * q] = __float_as_uint(__uint_as_float(r[4 * q]) + p4.x);
-                    r[4 * q + 1] = __float_as_uint(__uint_as_float(r[4 * q + 1]) + p4.y);
-                    r[4 * q + 2] = __float_as_uint(__uint_as_float(r[4 * q + 2]) + p4.z);
-                    r[4 * q + 3] = __float_as_uint(__uint_as_float(r[4 * q + 3]) + p4.w);
-                }
+                for (int q = 0; q < 32; ++q) gv[q] = gn[q];
             }
-            float v[32];
+        }
+    } else if (!aborted) {
+        // operands from global memory (rows not 16-byte aligned for TMA):
+        // every load of a chunk is issued before any store, which could
+        // otherwise alias them and serialise the chunk
+        for (int ck = ck_first; ck < ck_hi; ck += 2) {
+            uint32_t r[32];
+            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
+            if (ck != ck_first) load_g(ck, gv);
+            float yp[32], yp2[32];
+            const int cbase = n0 + ck * 32;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                const int c = cbase + q;
-                v[q] = 0.f;
+                const int c = cbase + q;  // warp-uniform
+                yp[q] = 0.f;
+                yp2[q] = 0.f;
                 if (c >= a.col_end || !row_ok) continue;
-                const float z = __uint_as_float(r[q]);
-                const float g = gv[q];
+                const bool cheb = c >= cb0 && c < cb1;
                 const int64_t idx = (int64_t)c * a.n + row;
-                const bool cheb = c >= a.cols.cheb_c0 && c < a.cols.cheb_c0 + a.cols.ncheb;
-                float y;
-                if (cheb) {
-                    if (a.cols.cheb_kind == EPI_CHEB1) y = fmaf(fa, z, -g);
-                    else y = 2.f * fmaf(fa, z, -yp[q]) - yp2[q];
-                    v[q] = g * y;
-                } else {
-                    v[q] = g * z;
-                    y = fmaf(-z, finvu, yp[q]);
-                }
-                a.Ynew[idx] = y;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(y);
-                a.Yhi_out[(int64_t)c * a.ldk + row] = hi;
-                if (a.Ylo_out)
-                    a.Ylo_out[(int64_t)c * a.ldk + row] = __float2bfloat16_rn(y - __bfloat162float(hi));
+                if (!cheb || three_term) yp[q] = __ldg(a.Yprev + idx);
+                if (cheb && three_term) yp2[q] = __ldg(a.Yprev2 + idx);
             }
-            // transpose-reduce: afterwards lane l holds the 32-row sum of column l
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                const bool upper = (lane & o) != 0;
-#pragma unroll
-                for (int k = 0; k < o; ++k) {
-                    const float send = upper ? v[k] : v[k + o];
-                    const float keep = upper ? v[k + o] : v[k];
-                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                }
-            }
-            red[rg * a.BN + ck * 32 + lane] = v[0];
+            tmem_wait_ld();
+            finish_chunk(
+                ck, r, gv, [&](int q) { return yp[q]; }, [&](int q) { return yp2[q]; });
         }
     }
     tc_fence_before();
@@ -747,7 +829,8 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
         mYlo = mYhi;
     }
     const uint32_t stage_bytes = (uint32_t)(TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (x3 ? 2u : 1u);
-    const size_t tail = 2 * 8 * 16 + 16 + 16 + 4 * 256 * 4;  // barriers, slot, flag, red
+    // barriers, slot, flag, red, staged G of two warps
+    const size_t tail = 2 * 8 * 16 + 16 + 16 + 4 * 256 * 4 + 2 * 32 * 32 * 4;
     const size_t max_smem = 227 * 1024;
     int stages = (int)((max_smem - 1024 - tail) / stage_bytes);
     if (stages > 8) stages = 8;
@@ -755,7 +838,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     // epilogue operand area (after the split-K receive buffer, if any)
     const int nch = BN / 32;
     const int nown = sh.ksplit > 1 ? nch / 2 : nch;
-    const size_t recv_bytes = sh.ksplit > 1 ? (size_t)TC_BM * (nch / 2 * 32 + 4) * 4 : 0;
+    const size_t recv_bytes = sh.ksplit > 1 ? (size_t)(nch / 2) * 8 * TC_BM * 16 : 0;
     const size_t ops_off = (recv_bytes + 1023) / 1024 * 1024;
     const size_t ops_end = ops_off + (size_t)nown * 2 * 32 * TC_BM * 4;
     size_t body = (size_t)stages * stage_bytes;
