@@ -181,6 +181,45 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // ---------------------------------------------------------------------------
 // Kernel
 // ---------------------------------------------------------------------------
+
+// One full 32-column chunk whose columns are all of one kind, at this thread's
+// row: branch-free, so the shared-memory reads, updates and stores of the 32
+// columns can be scheduled together.  KIND 0: Taylor, Y_t = Y_{t-1} - Z/u,
+// moment g Z; 1: first Chebyshev step, Y_1 = (2/u) Z - G; 2: three-term
+// Chebyshev step, Y_t = 2((2/u) Z - Y_{t-1}) - Y_{t-2}; moment g Y_t for both.
+// ob: Y_{t-1} of the chunk in smem ([32 cols][128 rows], Y_{t-2} 32*128 floats
+// later); yn / yh / yl: this row's entry of the chunk's first column in Y_t and
+// its bf16 shadows (yl null without the low shadow).
+template <int KIND>
+__device__ __forceinline__ void epi_chunk_uniform(const uint32_t* r, const float* g,
+                                                  const float* ob, float* yn, __nv_bfloat16* yh,
+                                                  __nv_bfloat16* yl, int64_t n, int64_t ldk,
+                                                  float fa, float finvu, bool row_ok, float* v) {
+    float y[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const float z = __uint_as_float(r[q]);
+        if (KIND == 0) {
+            y[q] = fmaf(-z, finvu, ob[q * TC_BM]);
+            v[q] = g[q] * z;
+        } else if (KIND == 1) {
+            y[q] = fmaf(fa, z, -g[q]);
+            v[q] = g[q] * y[q];
+        } else {
+            y[q] = 2.f * fmaf(fa, z, -ob[q * TC_BM]) - ob[(32 + q) * TC_BM];
+            v[q] = g[q] * y[q];
+        }
+    }
+    if (row_ok) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            yn[q * n] = y[q];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(y[q]);
+            yh[q * ldk] = hi;
+            if (yl) yl[q * ldk] = __float2bfloat16_rn(y[q] - __bfloat162float(hi));
+        }
+    }
+}
 struct TcArgs {
     const float* G;
     const float* Yprev;
@@ -506,7 +545,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // update, Y_t and its bf16 shadows, then the moment partial of each column
     // (transpose-reduce: afterwards lane l holds the 32-row sum of column l).
     // ypf(q) / yp2f(q) return Y_{t-1} / Y_{t-2} of column q; read only where used.
-    auto finish_chunk = [&](int ck, uint32_t* r, const float* g, auto ypf, auto yp2f) {
+    auto finish_chunk = [&](int ck, uint32_t* r, const float* g, bool uniform_ok, auto ypf,
+                            auto yp2f) {
         const int cbase = n0 + ck * 32;
         if (a.ksplit > 1) {
             const float4* rp = recv + (ck - ck_lo) * 8 * TC_BM + rg * 32 + lane;
@@ -520,6 +560,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
         float v[32];
+        // a full chunk of one kind with its operands in smem takes the
+        // branch-free path (G is 0 on rows past n, so their moments vanish)
+        const bool full = cbase + 32 <= a.col_end;
+        const bool all_cheb = cbase >= cb0 && cbase + 32 <= cb1;
+        const bool all_tay = cbase >= cb1 || cbase + 32 <= cb0;
+        if (uniform_ok && full && (all_cheb || all_tay)) {
+            const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
+            float* yn = a.Ynew + (int64_t)cbase * a.n + row;
+            __nv_bfloat16* yh = a.Yhi_out + (int64_t)cbase * a.ldk + row;
+            __nv_bfloat16* yl = a.Ylo_out ? a.Ylo_out + (int64_t)cbase * a.ldk + row : nullptr;
+            if (all_tay)
+                epi_chunk_uniform<0>(r, g, ob, yn, yh, yl, a.n, a.ldk, fa, finvu, row_ok, v);
+            else if (!three_term)
+                epi_chunk_uniform<1>(r, g, ob, yn, yh, yl, a.n, a.ldk, fa, finvu, row_ok, v);
+            else
+                epi_chunk_uniform<2>(r, g, ob, yn, yh, yl, a.n, a.ldk, fa, finvu, row_ok, v);
+        } else {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             const int c = cbase + q;
@@ -542,6 +599,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             a.Yhi_out[(int64_t)c * a.ldk + row] = hi;
             if (a.Ylo_out)
                 a.Ylo_out[(int64_t)c * a.ldk + row] = __float2bfloat16_rn(y - __bfloat162float(hi));
+        }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -572,7 +630,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
             tmem_wait_ld();
             finish_chunk(
-                ck, r, gv, [&](int q) { return ob[q * TC_BM]; },
+                ck, r, gv, true, [&](int q) { return ob[q * TC_BM]; },
                 [&](int q) { return ob[32 * TC_BM + q * TC_BM]; });
             if (more) {
 #pragma unroll
@@ -602,7 +660,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tmem_wait_ld();
             finish_chunk(
-                ck, r, gv, [&](int q) { return yp[q]; }, [&](int q) { return yp2[q]; });
+                ck, r, gv, false, [&](int q) { return yp[q]; }, [&](int q) { return yp2[q]; });
         }
     }
     tc_fence_before();
