@@ -174,6 +174,29 @@ __device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Arrive (release, cluster scope) on the mbarrier at this shared::cluster
+// address, typically one in the peer CTA (from mapa).
+__device__ __forceinline__ void mbar_remote_arrive(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+// Bounded wait with cluster-scope acquire: what the arriving peer wrote
+// before its release-arrive is visible afterwards.  False on timeout.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 255u && globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -261,7 +284,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t* empty_bar = full_bar + a.stages;
     uint64_t* accum_bar = empty_bar + a.stages;
     uint64_t* epi_bar = accum_bar + 1;  // epilogue operands landed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epi_bar + 1);
+    uint64_t* idle_bar = epi_bar + 1;   // split K: the peer's ring is idle (1 arrival)
+    uint64_t* recv_bar = idle_bar + 1;  // split K: the peer's half has landed (1 per warp)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(recv_bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][BN]
     float* gstash = red + 4 * a.BN;                         // [2 warps][32 cols][32 lanes]
@@ -304,6 +329,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         mbar_init(accum_bar, 1);
         mbar_init(epi_bar, 1);
+        mbar_init(idle_bar, 1);
+        mbar_init(recv_bar, TC_THREADS / 32);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapRhi)) : "memory");
@@ -480,7 +507,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         volatile int never = 0;
         if (threadIdx.x == 0) mbar_wait(accum_bar, 0u, &never);
     }
-    const bool aborted = (*abort_flag != 0) || !have_acc;
+    bool aborted = (*abort_flag != 0) || !have_acc;
     tc_fence_after();
     __syncwarp();
 
@@ -519,25 +546,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // Receive buffer of the split-K exchange: float4 slot (chunk*8 + q)*128 + r
     // holds columns 4q..4q+3 of row r, so a warp's 16-byte stores and loads
     // cover 512 contiguous bytes.
+    // The pair signals through mbarriers in each other's shared memory: thread
+    // 0 tells the peer that this ring is idle (its MMAs are complete), every
+    // warp tells it when its part of the half has been written.  Both signals
+    // are sent also by a CTA that aborted, and every CTA waits for the peer's
+    // writes before it leaves, so no wait depends on the other CTA's state.
     const float4* recv = reinterpret_cast<const float4*>(smem);
     if (a.ksplit > 1) {
-        cluster_sync_all();  // both accumulators are final and both rings are idle
-        if (!aborted) {
-            const int peer = 1 - kz;
-            const uint32_t rbase = mapa_peer(smem_u32(smem), (uint32_t)peer);
-            for (int ck = peer * half + chalf; ck < peer * half + half; ck += 2) {
+        const uint32_t peer = (uint32_t)(1 - kz);
+        if (threadIdx.x == 0) mbar_remote_arrive(mapa_peer(smem_u32(idle_bar), peer));
+        const bool peer_idle = mbar_wait_cluster(idle_bar, 0u);
+        if (!aborted && peer_idle) {
+            const uint32_t rbase = mapa_peer(smem_u32(smem), peer);
+            for (int ck = (int)peer * half + chalf; ck < (int)peer * half + half; ck += 2) {
                 uint32_t r[32];
                 TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
                 tmem_wait_ld();
                 const uint32_t dst =
-                    rbase + (uint32_t)(((ck - peer * half) * 8 * TC_BM + rg * 32 + lane) * 16);
+                    rbase + (uint32_t)(((ck - (int)peer * half) * 8 * TC_BM + rg * 32 + lane) * 16);
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     st_cluster_v4(dst + (uint32_t)(q * TC_BM * 16), r[4 * q], r[4 * q + 1],
                                   r[4 * q + 2], r[4 * q + 3]);
             }
         }
-        cluster_sync_all();  // the peer's half has landed here
+        __syncwarp();
+        if (lane == 0) mbar_remote_arrive(mapa_peer(smem_u32(recv_bar), peer));
+        // the peer's half has landed here
+        if (!mbar_wait_cluster(recv_bar, 0u) || !peer_idle) aborted = true;
     }
     const bool ops_ready = a.epi_tma && !aborted && mbar_wait(epi_bar, 0u, abort_flag);
 
@@ -675,7 +711,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     }
     // no CTA leaves while a peer may still multicast into it or arrive on it
-    if (in_cluster) cluster_sync_all();
+    // (a split-K pair has already waited for all of its peer's signals)
+    if (csize > 1) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
