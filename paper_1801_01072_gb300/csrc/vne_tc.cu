@@ -860,8 +860,10 @@ int tc_candidates(int64_t n, int ncols, int (*out)[4], int max) {
 }
 
 // Default: the widest tile (BN up to 256 columns, the largest N of one MMA);
-// when that leaves most SMs idle, a CTA pair splits K (ksplit = 2).  A shape
-// set by the autotuner for this bucket comes first; VNE_TC_TILE overrides both.
+// when that leaves most SMs idle and the doubled grid still fits in one wave
+// (one CTA per SM), a CTA pair splits K (ksplit = 2): a second wave would cost
+// more than the idle SMs.  A shape set by the autotuner for this bucket comes
+// first; VNE_TC_TILE overrides both.
 static TcShape choose_shape(int ncols, int mtiles, int nkb, int sm_count) {
     TcShape sh;
     const int ntn = (ncols + 255) / 256;
@@ -869,7 +871,8 @@ static TcShape choose_shape(int ncols, int mtiles, int nkb, int sm_count) {
     sh.ntn = (ncols + sh.BN - 1) / sh.BN;
     sh.CM = sh.CN = 1;
     sh.ksplit = 1;
-    if ((int64_t)mtiles * sh.ntn * 4 < (int64_t)sm_count * 3 && sh.BN % 64 == 0 && nkb >= 2)
+    if ((int64_t)mtiles * sh.ntn * 4 < (int64_t)sm_count * 3 &&
+        (int64_t)mtiles * sh.ntn * 2 <= (int64_t)sm_count && sh.BN % 64 == 0 && nkb >= 2)
         sh.ksplit = 2;
     static int o_bn = -1, o_cm = 0, o_cn = 0, o_ks = 1;
     if (o_bn < 0) {
