@@ -194,6 +194,18 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
 vne_status vne_tc_autotune(vne_handle* h, const vne_matrix* R, const vne_params* p,
                            int32_t method, int32_t* shape_out, double* us_out, void* stream);
 
+/* The tile shape the tensor-core step takes for n rows and ncols step columns
+ * (2s for the fused Chebyshev + Taylor steps, s otherwise) on sm_count SMs,
+ * without the autotuner's or VNE_TC_TILE's choice: the widest tile (BN up to
+ * 256), with the K split over a CTA pair (ksplit = 2) when the row tiles leave
+ * most SMs idle and the doubled grid still fits in one wave.  Host logic only:
+ * no CUDA call, no handle.
+ *   shape_out: host, 4 ints (BN, CM, CN, ksplit).
+ * Errors: VNE_ERR_INVALID_ARG for n, ncols or sm_count < 1 or a NULL shape_out.
+ * An autotuned shape for the same size bucket, or VNE_TC_TILE, replaces this
+ * default inside the estimators. */
+vne_status vne_tc_shape(int64_t n, int32_t ncols, int32_t sm_count, int32_t* shape_out);
+
 /* Algorithm alg:power: p1~ = max_j x_t^T R x_t / x_t^T x_t over q = power_trials
  * start vectors in {+1,-1}^n after t = power_iters products (each iterate is
  * divided by its 2-norm, which leaves the Rayleigh quotient unchanged).  The

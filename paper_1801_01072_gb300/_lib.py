@@ -62,6 +62,7 @@ SIGNATURES = [
       C.c_void_p]),
     ("vne_tc_autotune", C.c_int,
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), C.c_int32, C.c_void_p, _D, C.c_void_p]),
+    ("vne_tc_shape", C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p]),
     ("vne_selftest_timeout", C.c_int, [_H, C.c_void_p]),
     ("vne_lambda_max", C.c_int, [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, C.c_void_p]),
     ("vne_lambda_max_static", C.c_int,

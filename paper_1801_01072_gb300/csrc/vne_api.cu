@@ -1061,6 +1061,14 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     return first;
 }
 
+vne_status vne_tc_shape(int64_t n, int32_t ncols, int32_t sm_count, int32_t* shape_out) {
+    if (!shape_out) return VNE_ERR_INVALID_ARG;
+    int sh[4];
+    if (tc_plan(n, ncols, sm_count, sh) != 0) return VNE_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) shape_out[k] = sh[k];
+    return VNE_OK;
+}
+
 vne_status vne_tc_autotune(vne_handle* h, const vne_matrix* R, const vne_params* p,
                            int32_t method, int32_t* shape_out, double* us_out, void* stream) {
     if (!h || !R || !p) return VNE_ERR_INVALID_ARG;

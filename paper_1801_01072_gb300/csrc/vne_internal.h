@@ -135,6 +135,9 @@ cudaError_t launch_tc_step(const TcStep& a, int sm_count, cudaStream_t st);
 // autotuner: set (BN = 0 clears) the shape of n x ncols steps; candidates
 int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit);
 int tc_candidates(int64_t n, int ncols, int (*out)[4], int max);
+// The shape launch_tc_step would use for n rows and ncols step columns on
+// sm_count SMs: out = {BN, CM, CN, ksplit}; 0, or -1 on bad arguments.
+int tc_plan(int64_t n, int ncols, int sm_count, int* out);
 int tc_tile_m();
 int tc_tile_k();
 

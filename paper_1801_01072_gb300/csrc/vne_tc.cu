@@ -896,6 +896,18 @@ static TcShape choose_shape(int ncols, int mtiles, int nkb, int sm_count) {
     return sh;
 }
 
+int tc_plan(int64_t n, int ncols, int sm_count, int* out) {
+    if (n < 1 || ncols < 1 || sm_count < 1 || !out) return -1;
+    const int64_t rows_pad = (n + TC_BM - 1) / TC_BM * TC_BM;
+    const int64_t ldk = (n + TC_BK - 1) / TC_BK * TC_BK;
+    const TcShape sh = choose_shape(ncols, (int)(rows_pad / TC_BM), (int)(ldk / TC_BK), sm_count);
+    out[0] = sh.BN;
+    out[1] = sh.CM;
+    out[2] = sh.CN;
+    out[3] = sh.ksplit;
+    return 0;
+}
+
 cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     int col0, col_end;
     if (s.cols.ncheb > 0) {

@@ -70,3 +70,38 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     H = C.c_double()
     assert lib.vne_entropy_chebyshev(None, None, None, C.byref(H), None, None, None) == 1
     assert lib.vne_create(None, 0) == 1
+
+
+def tc_shape(lib, n, ncols, sms=152):
+    out = (C.c_int32 * 4)()
+    assert lib.vne_tc_shape(n, ncols, sms, C.cast(out, C.c_void_p)) == 0
+    return tuple(out)
+
+
+@pytest.mark.parametrize("n,ncols,shape", [
+    (8192, 256, (256, 1, 1, 2)),   # 64 row tiles: the K split fills 128 SMs in one wave
+    (10000, 256, (256, 1, 1, 1)),  # 79 row tiles: a split grid (158 CTAs) would need two waves
+    (9728, 256, (256, 1, 1, 2)),   # 76 row tiles: 152 CTAs, exactly one wave
+    (9729, 256, (256, 1, 1, 1)),   # 77 row tiles
+    (10000, 200, (224, 1, 1, 1)),  # 7 chunks of 32 columns cannot be halved
+    (4096, 64, (64, 1, 1, 2)),
+    (4096, 32, (32, 1, 1, 1)),     # one chunk: nothing to split
+    (2048, 300, (160, 1, 1, 1)),   # two column tiles of 160
+    (65536, 256, (256, 1, 1, 1)),  # 512 row tiles fill the GPU without a split
+])
+def test_tc_shape_rules(lib, n, ncols, shape):
+    assert tc_shape(lib, n, ncols) == shape
+
+
+def test_tc_shape_scales_with_sm_count(lib):
+    # the one-wave rule uses the SM count it is given
+    assert tc_shape(lib, 8192, 256, sms=100) == (256, 1, 1, 1)
+    assert tc_shape(lib, 8192, 256, sms=128) == (256, 1, 1, 2)
+
+
+def test_tc_shape_rejects_bad_arguments(lib):
+    out = (C.c_int32 * 4)()
+    assert lib.vne_tc_shape(0, 256, 152, C.cast(out, C.c_void_p)) == 1
+    assert lib.vne_tc_shape(8192, 0, 152, C.cast(out, C.c_void_p)) == 1
+    assert lib.vne_tc_shape(8192, 256, 0, C.cast(out, C.c_void_p)) == 1
+    assert lib.vne_tc_shape(8192, 256, 152, None) == 1
