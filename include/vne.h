@@ -182,14 +182,15 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
 
 /* Autotuner of the tensor-core step (BF16 / BF16X3 dense paths; not in the
  * paper).  Times every candidate tile shape -- BN probe columns per CTA (the
- * widest MMA, half of it, 128), clusters of 1 or 2 CTAs along M or N, and the
- * K split over a CTA pair -- on full estimator calls of R with p and method
+ * widest MMA, half of it, 128), each with and without the K split over a CTA
+ * pair -- on full estimator calls of R with p and method
  * (CUDA events around the tensor-core steps), and keeps the fastest for the
  * size bucket of R (ceil log2 of its 128-row tiles) and of the step's column
  * count.  The choice is process-wide and applies to later calls (single and
  * batched) whose sizes fall in the same buckets; the environment variable
- * VNE_TC_TILE="BN,CM,CN[,ksplit]" still overrides it.
- *   shape_out: host, 4 ints (BN, CM, CN, ksplit) or NULL;
+ * VNE_TC_TILE="BN,1,1[,ksplit]" still overrides it.
+ *   shape_out: host, 4 ints (BN, CM, CN, ksplit) or NULL; CM = CN = 1 always
+ *              (every CTA loads its own operand tiles);
  *   us_out:    host, the chosen shape's microseconds per step, or NULL. */
 vne_status vne_tc_autotune(vne_handle* h, const vne_matrix* R, const vne_params* p,
                            int32_t method, int32_t* shape_out, double* us_out, void* stream);
@@ -229,18 +230,25 @@ vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* 
  * other allocating routine.  The caller still passes R and receives lam_out.
  *   - Device: the calling thread's current device.  The first call on a
  *     device looks up the array's device address (cudaGetSymbolAddress);
- *     make that first call before any stream capture.
+ *     make that first call before any stream capture.  The address is kept
+ *     with the device's context: a call from a thread with no current
+ *     context yet, or after a device reset (a new primary context), looks
+ *     it up again.
+ *   - Results: the same power-method kernels with the same block counts as
+ *     vne_lambda_max, so the same lam_out for the same R and p.
  *   - Limits: R must be device memory stored in the computed precision
  *     (F64 with VNE_PREC_F64, F32 with VNE_PREC_F32); n * power_trials
  *     must not exceed VNE_STATIC_MAX_VECTOR_ELEMS.  Anything else returns
- *     VNE_ERR_UNSUPPORTED; bad arguments return VNE_ERR_INVALID_ARG.
+ *     VNE_ERR_UNSUPPORTED; bad arguments (including n_diags < 1 for a
+ *     banded R) return VNE_ERR_INVALID_ARG.  Device-side failures map as in
+ *     vne_lambda_max: VNE_ERR_TIMEOUT, VNE_ERR_BAD_INTERVAL, VNE_ERR_NONFINITE.
  *   - Sharing: every call on a device uses the same array, which keeps the
  *     previous call's contents (the call clears what must start at zero).
  *     Calls that overlap on the GPU (other streams or host threads) race on
  *     it and must be serialised by the caller.
  *   - Synchronises `stream` before returning. */
 #define VNE_STATIC_MAX_VECTOR_ELEMS 131072
-#define VNE_STATIC_SCRATCH_BYTES 2359296
+#define VNE_STATIC_SCRATCH_BYTES 2621440
 vne_status vne_lambda_max_static(const vne_matrix* R, const vne_params* p, double* lam_out,
                                  void* stream);
 

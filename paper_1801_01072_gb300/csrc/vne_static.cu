@@ -15,9 +15,11 @@
 // it and it keeps the last call's contents; the call clears what must start
 // at zero.  Calls whose work overlaps on the GPU (other streams, other host
 // threads) race on the array: serialise them.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -27,7 +29,7 @@
 
 namespace {
 
-constexpr int kMaxBlocks = 1024;        // power-method blocks (partials rows)
+constexpr int kMaxBlocks = 2048;        // power-method blocks (partials rows): >= 8 per SM
 constexpr int kMaxTrials = 8;           // q
 constexpr int64_t kSc = vne::SC_COUNT;  // doubles
 constexpr int64_t kCounter = 32;        // doubles (64 unsigned counters)
@@ -44,13 +46,40 @@ static __device__ __align__(256) double g_scratch[VNE_STATIC_SCRATCH_BYTES / 8];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_ptr[kMaxDevices] = {};
+void* g_ctx[kMaxDevices] = {};  // the context the address belongs to
 int g_sms[kMaxDevices] = {};
 
+// The calling thread's current driver context (cuCtxGetCurrent, reached
+// through the runtime's entry-point query, so no driver library is linked).
+void* current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+        looked = true;
+    }
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
 // Once per device, with that device current: the device address of the array.
+// The address belongs to the device's context, so it is cached with that
+// context; a thread with no current context yet, or a context that is not
+// the cached one (after a device reset the primary context is a new one),
+// runs the look-up again (cudaGetSymbolAddress also makes the device's
+// primary context current).
 vne_status setup(int dev, double** base, int* sms) {
     if (dev < 0 || dev >= kMaxDevices) return VNE_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
+    void* ctx = current_context();
+    if (!g_ptr[dev] || !ctx || ctx != g_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
@@ -63,6 +92,7 @@ vne_status setup(int dev, double** base, int* sms) {
             return VNE_ERR_CUDA;
         }
         g_ptr[dev] = p;
+        g_ctx[dev] = current_context();
         g_sms[dev] = n;
     }
     *base = static_cast<double*>(g_ptr[dev]);
@@ -86,6 +116,7 @@ extern "C" vne_status vne_lambda_max_static(const vne_matrix* R, const vne_param
     if (p->precision != VNE_PREC_F64 && p->precision != VNE_PREC_F32) return VNE_ERR_UNSUPPORTED;
     const bool f64 = p->precision == VNE_PREC_F64;
     if ((R->dtype == VNE_F64) != f64) return VNE_ERR_UNSUPPORTED;
+    if (R->layout == VNE_DIA && R->n_diags < 1) return VNE_ERR_INVALID_ARG;
     if (R->layout == VNE_DIA && vne::dia_supported_halfbw(R->n_diags) < 0)
         return VNE_ERR_UNSUPPORTED;
     const int q = p->power_trials;
@@ -109,7 +140,8 @@ extern "C" vne_status vne_lambda_max_static(const vne_matrix* R, const vne_param
     double* x1 = x0 + kVec;
     const int64_t n = R->n;
     const bool dense = R->layout == VNE_DENSE;
-    int blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 4 * (int64_t)sms) : 4 * sms;
+    // the block counts of vne_lambda_max, so both sum the same partials in the same order
+    int blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 8 * (int64_t)sms) : 4 * sms;
     if (blocks > kMaxBlocks) blocks = kMaxBlocks;
     const double u_scale = p->u_scale > 0.0 ? p->u_scale : 1.0;
 
@@ -142,7 +174,11 @@ extern "C" vne_status vne_lambda_max_static(const vne_matrix* R, const vne_param
     }
     unsigned long long flags;
     memcpy(&flags, &out[vne::SC_FLAGS], sizeof(flags));
+    // the statuses of vne_lambda_max, in its order
+    if (flags & vne::FLAG_TIMEOUT) return VNE_ERR_TIMEOUT;
     if (flags & vne::FLAG_BAD_INTERVAL) return VNE_ERR_BAD_INTERVAL;
+    if (flags & vne::FLAG_NONFINITE) return VNE_ERR_NONFINITE;
+    if (!std::isfinite(out[vne::SC_LAM])) return VNE_ERR_NONFINITE;
     *lam_out = out[vne::SC_LAM];
     return VNE_OK;
 }

@@ -43,26 +43,14 @@ constexpr int TC_THREADS = 256;
 int tc_tile_m() { return TC_BM; }
 int tc_tile_k() { return TC_BK; }
 
-// Tiled 2-D TMA load with an L2 cache-policy hint; with mask != 0 the tile is
-// multicast to every CTA of the cluster in `mask` (same smem offset and the
-// same mbarrier offset in each destination CTA).
+// Tiled 2-D TMA load into this CTA's shared memory with an L2 cache-policy hint.
 __device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                                 int x, int y, uint16_t mask, uint64_t policy) {
-    if (mask == 0) {
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-            " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-            "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
-            : "memory");
-    } else {
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            ".multicast::cluster.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5, %6;" ::"r"(
-                smem_u32(dst)),
-            "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask),
-            "l"(policy)
-            : "memory");
-    }
+                                                 int x, int y, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+        : "memory");
 }
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
@@ -83,11 +71,6 @@ __device__ __forceinline__ uint32_t cluster_ctarank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
-__device__ __forceinline__ uint32_t cluster_ctaid_x() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctaid.x;" : "=r"(r));
-    return r;
-}
 __device__ __forceinline__ uint32_t cluster_ctaid_z() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctaid.z;" : "=r"(r));
@@ -103,20 +86,6 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_
     asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b),
                  "r"(c), "r"(d)
                  : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_ctaid_y() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctaid.y;" : "=r"(r));
-    return r;
-}
-// Arrive on the mbarrier at this offset in every CTA of `mask` once all
-// previously issued tcgen05.mma of this thread have completed.
-__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -254,7 +223,6 @@ struct TcArgs {
     int S, s;
     int col0, col_end;  // active columns [col0, col_end)
     int BN, stages, nkb, x3;
-    int CM, CN;  // cluster shape: CM CTAs along M share B tiles, CN along N share A tiles
     int ksplit;  // 2: a CTA pair (cluster along z) splits K and swaps half accumulators
     int64_t keep_rows;  // row tiles starting below this load R evict-last (kept in L2)
     int epi_tma;       // 1: Y_{t-1}, Y_{t-2} of the CTA's own chunks arrive by TMA into smem
@@ -294,38 +262,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM;
     const int n0 = a.col0 + blockIdx.y * a.BN;
-    // Cluster of CM x CN CTAs: the CN CTAs of one M row share the A tile (each
-    // loads 128/CN rows and multicasts them), the CM CTAs of one N column share
-    // the B tile (BN/CM rows each).  A ring slot is refilled only when every
-    // CTA of the cluster has released it (empty barrier count = cluster size).
-    const int csize = a.CM * a.CN;  // multicast group
-    const bool in_cluster = csize > 1 || a.ksplit > 1;
-    int cx = 0, cy = 0, kz = 0;
+    // The only cluster is the split-K CTA pair (along z): each CTA loads its
+    // own operand tiles, and the pair meets only in the accumulator exchange.
+    const bool in_cluster = a.ksplit > 1;
+    int kz = 0;
     bool rank_ok = true;
     if (in_cluster) {
-        cx = (int)cluster_ctaid_x();
-        cy = (int)cluster_ctaid_y();
         kz = (int)cluster_ctaid_z();
-        rank_ok = (int)cluster_ctarank() == cx + cy * a.CM + kz * csize;
+        rank_ok = (int)cluster_ctarank() == kz;
     }
     // K range of this CTA (the whole K unless the pair splits it)
     const int kb_begin = a.ksplit > 1 ? kz * (a.nkb / 2) : 0;
     const int kb_end = a.ksplit > 1 ? (kz == 0 ? a.nkb / 2 : a.nkb) : a.nkb;
     const int nkb_local = kb_end - kb_begin;
-    uint16_t maskA = 0, maskB = 0, mask_all = 0;
-    if (csize > 1) {
-        for (int y = 0; y < a.CN; ++y) maskA |= (uint16_t)(1u << (cx + y * a.CM));
-        for (int x = 0; x < a.CM; ++x) maskB |= (uint16_t)(1u << (x + cy * a.CM));
-        mask_all = (uint16_t)((1u << csize) - 1u);
-        if (a.CN == 1) maskA = 0;
-        if (a.CM == 1) maskB = 0;
-    }
-    const int arows = TC_BM / a.CN, brows = a.BN / a.CM;
-
     if (threadIdx.x == 0) {
         for (int s2 = 0; s2 < a.stages; ++s2) {
             mbar_init(&full_bar[s2], 1);
-            mbar_init(&empty_bar[s2], (uint32_t)csize);
+            mbar_init(&empty_bar[s2], 1);
         }
         mbar_init(accum_bar, 1);
         mbar_init(epi_bar, 1);
@@ -345,26 +298,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (in_cluster) cluster_sync_all();  // peers' barriers are initialised before any multicast
+    if (in_cluster) cluster_sync_all();  // the peer's barriers are initialised before any signal
     tc_fence_after();
     // R: the rows kept in L2 from pass to pass (power method and earlier steps)
     // load evict-last, the rest streams evict-first; the Y shadows are re-read
-    // by every row tile (evict last).  This CTA's slices: rows [cy*arows,
-    // +arows) of A, [cx*brows, +brows) of B.
+    // by every row tile (evict last).
     const bool producer = warp == 0 && lane == 0;
     const uint64_t pol_R =
         producer ? ((int64_t)m0 < a.keep_rows ? policy_evict_last() : policy_evict_first()) : 0ull;
-    const uint32_t offA = (uint32_t)(cy * arows) * (TC_BK * 2);
-    const uint32_t offB = (uint32_t)(cx * brows) * (TC_BK * 2);
     auto load_A = [&](int i) {
         const int st = i % a.stages;
         uint8_t* sA = smem + (size_t)st * stage_bytes;
         const int kb = kb_begin + i;
         mbar_expect_tx(&full_bar[st], stage_bytes);  // whole tiles (A and B) arrive here
-        tma_load_2d_hint(sA + offA, &mapRhi, &full_bar[st], kb * TC_BK, m0 + cy * arows, maskA, pol_R);
+        tma_load_2d_hint(sA, &mapRhi, &full_bar[st], kb * TC_BK, m0, pol_R);
         if (a.x3)
-            tma_load_2d_hint(sA + bytesA + bytesB + offA, &mapRlo, &full_bar[st], kb * TC_BK,
-                             m0 + cy * arows, maskA, pol_R);
+            tma_load_2d_hint(sA + bytesA + bytesB, &mapRlo, &full_bar[st], kb * TC_BK, m0, pol_R);
     };
     // R is written before the steps start and never by a step, so the A tiles
     // of the first ring round are requested before waiting on the previous
@@ -396,11 +345,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 load_A(i);
             }
             uint8_t* sB = smem + (size_t)st * stage_bytes + bytesA;
-            tma_load_2d_hint(sB + offB, &mapYhi, &full_bar[st], kb * TC_BK, n0 + cx * brows, maskB,
-                             pol_Y);
+            tma_load_2d_hint(sB, &mapYhi, &full_bar[st], kb * TC_BK, n0, pol_Y);
             if (a.x3)
-                tma_load_2d_hint(sB + bytesB + bytesA + offB, &mapYlo, &full_bar[st], kb * TC_BK,
-                                 n0 + cx * brows, maskB, pol_Y);
+                tma_load_2d_hint(sB + bytesB + bytesA, &mapYlo, &full_bar[st], kb * TC_BK, n0, pol_Y);
             issued_kb = i + 1;
         }
         if (timed_out) {
@@ -440,9 +387,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     umma_bf16(tmem_base, dAl + 2 * k, dB + 2 * k, idesc, 1u);
                 }
             }
-            // frees the ring slot (in every CTA of the cluster) once these MMAs finish
-            if (csize > 1) tc_commit_mc(&empty_bar[st], mask_all);
-            else tc_commit(&empty_bar[st]);
+            // frees the ring slot once these MMAs finish
+            tc_commit(&empty_bar[st]);
         }
         if (timed_out) *abort_flag = 1;
         tc_commit(accum_bar);  // all issued MMAs (possibly none) complete -> arrive
@@ -710,9 +656,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             a.P.slot(a.t)[(size_t)blockIdx.x * a.S + c] = tot;
         }
     }
-    // no CTA leaves while a peer may still multicast into it or arrive on it
-    // (a split-K pair has already waited for all of its peer's signals)
-    if (csize > 1) cluster_sync_all();
+    // (a split-K pair has already waited for all of its peer's signals, so
+    // neither CTA can still be written or signalled by the other here)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -777,28 +722,20 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t 
     return true;
 }
 
-// Tile shape and cluster shape of one step.  BN: probe columns per CTA
-// (multiple of 32, <= 256); CM x CN: cluster along M (row tiles sharing the
-// Y tile) and N (column tiles sharing the R tile).  VNE_TC_TILE="BN,CM,CN"
-// overrides the default (used to sweep shapes); invalid overrides are ignored.
+// Tile shape of one step.  BN: probe columns per CTA (multiple of 32, <= 256);
+// ksplit 2: a CTA pair (cluster along z) splits K.  CM and CN (CTAs along M and
+// N sharing operand tiles) are always 1: every CTA loads its own operand
+// tiles.  VNE_TC_TILE="BN,1,1[,ksplit]" overrides the default
+// (used to sweep shapes); invalid overrides are ignored.
 struct TcShape {
     int BN, ntn, CM, CN, ksplit;
 };
 
-static int pick_cluster(int tiles, int want) {
-    int c = want;
-    while (c > 1 && tiles % c != 0) c /= 2;
-    return c < 1 ? 1 : c;
-}
-
 static bool shape_ok(const TcShape& t, int ncols, int mtiles, int nkb) {
-    if (!(t.BN >= 32 && t.BN <= 256 && t.BN % 32 == 0 && t.CM >= 1 && t.CN >= 1 &&
-          t.CM * t.CN <= 8 && (t.BN / t.CM) % 8 == 0 && (TC_BM / t.CN) % 8 == 0))
-        return false;
-    if (!(t.ksplit == 1 || (t.ksplit == 2 && t.CM == 1 && t.CN == 1 && t.BN % 64 == 0 && nkb >= 2)))
-        return false;
-    const int ntn = (ncols + t.BN - 1) / t.BN;
-    return mtiles % t.CM == 0 && ntn % t.CN == 0;
+    (void)ncols;
+    (void)mtiles;
+    if (!(t.BN >= 32 && t.BN <= 256 && t.BN % 32 == 0 && t.CM == 1 && t.CN == 1)) return false;
+    return t.ksplit == 1 || (t.ksplit == 2 && t.BN % 64 == 0 && nkb >= 2);
 }
 
 // Shapes chosen by the autotuner, per bucket of row tiles (ceil log2) and of
@@ -835,18 +772,18 @@ int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit) {
 }
 
 // Candidate shapes for n x ncols steps: column tiles of one or two MMAs'
-// width, clusters of 1, 2 (along M or N), K split over a CTA pair.
+// width or 128, each with and without the K split over a CTA pair.
 int tc_candidates(int64_t n, int ncols, int (*out)[4], int max) {
     const int mtiles = (int)((n + TC_BM - 1) / TC_BM);
     const int nkb = (int)((n + TC_BK - 1) / TC_BK);
     const int wide = std::min(256, (ncols + 31) / 32 * 32);
     const int bns[3] = {wide, std::max(32, (wide / 2 + 31) / 32 * 32), 128};
-    const int cl[4][3] = {{1, 1, 1}, {1, 1, 2}, {2, 1, 1}, {1, 2, 1}};
+    const int cl[2][3] = {{1, 1, 1}, {1, 1, 2}};
     int cnt = 0;
     for (int bi = 0; bi < 3; ++bi) {
         if (bi > 0 && bns[bi] == bns[0]) continue;
         if (bi == 2 && bns[2] == bns[1]) continue;
-        for (int ci = 0; ci < 4 && cnt < max; ++ci) {
+        for (int ci = 0; ci < 2 && cnt < max; ++ci) {
             TcShape t{bns[bi], (ncols + bns[bi] - 1) / bns[bi], cl[ci][0], cl[ci][1], cl[ci][2]};
             if (!shape_ok(t, ncols, mtiles, nkb)) continue;
             out[cnt][0] = t.BN;
@@ -928,12 +865,11 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     if (x3 && (!s.Ylo || !s.Ylo_out)) return cudaErrorInvalidValue;
 
     CUtensorMap mRhi, mRlo, mYhi, mYlo;
-    const int arows = TC_BM / sh.CN, brows = BN / sh.CM;
-    if (!make_map(&mRhi, s.Rhi, s.ldk, s.rows_pad, s.ldk, TC_BK, arows)) return cudaErrorInvalidValue;
-    if (!make_map(&mYhi, s.Yhi, s.ldk, S_pad, s.ldk, TC_BK, brows)) return cudaErrorInvalidValue;
+    if (!make_map(&mRhi, s.Rhi, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
+    if (!make_map(&mYhi, s.Yhi, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
     if (x3) {
-        if (!make_map(&mRlo, s.Rlo, s.ldk, s.rows_pad, s.ldk, TC_BK, arows)) return cudaErrorInvalidValue;
-        if (!make_map(&mYlo, s.Ylo, s.ldk, S_pad, s.ldk, TC_BK, brows)) return cudaErrorInvalidValue;
+        if (!make_map(&mRlo, s.Rlo, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
+        if (!make_map(&mYlo, s.Ylo, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
     } else {
         mRlo = mRhi;
         mYlo = mYhi;
@@ -973,8 +909,6 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.stages = stages;
     a.nkb = (int)(s.ldk / TC_BK);
     a.x3 = x3 ? 1 : 0;
-    a.CM = sh.CM;
-    a.CN = sh.CN;
     a.ksplit = sh.ksplit;
     // L2 residency: the rows the power method keeps (same budget; bf16x3 streams R_hi and R_lo)
     a.keep_rows = l2_keep_rows(s.rows_pad, s.ldk * 2 * (x3 ? 2 : 1));
@@ -1010,8 +944,8 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     cfg.stream = st;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)sh.CM;
-    attr[0].val.clusterDim.y = (unsigned)sh.CN;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = (unsigned)sh.ksplit;
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[1].val.programmaticStreamSerializationAllowed = 1;

@@ -97,11 +97,12 @@ def test_power_method_f64(q):
 
 @pytest.mark.parametrize("n,q", [(300, 1), (1024, 1), (2500, 1), (1024, 3)])
 def test_power_method_tensor_core_path(n, q):
-    """The BF16 path's power method (per-row-scaled e4m3 copy of R for one
-    trial, bf16 for several) stays within the BF16 path's 1e-3 of the FP64
-    power method.  (After t = 30 products the iterate is not converged, so the
-    Rayleigh quotient moves to first order with the rounding of R; the
-    deviation, ~1e-4, is far below the method's own gap to p_1.)"""
+    """The BF16 path's power method (products with the bf16 copy of R, FP32
+    accumulation, FP64 Rayleigh quotient) stays within the BF16 path's 1e-3
+    of the FP64 power method.  (After t = 30 products the iterate is not
+    converged, so the Rayleigh quotient moves to first order with the
+    rounding of R; the deviation, ~1e-4, is far below the method's own gap to
+    p_1.)"""
     R, p, _ = synth.dense_exp(n, n / 10.0, seed=40 + n)
     lam = vne.lambda_max(dev(R), power_iters=30, power_trials=q, seed=2, precision="bf16")
     ref, _ = O.power_method(R, rng.power_start(n, q, 2), 30)

@@ -77,11 +77,49 @@ def test_static_dense_f64_matches_allocating_entry_point():
     assert p.max() / 6 <= got[0] <= p.max() * (1 + 1e-12)
 
 
+def test_static_dense_f32_matches_allocating_entry_point():
+    # same kernels and block counts as vne_lambda_max: the FP32 sums agree too
+    R, _, _ = synth.dense_exp(3000, 300.0, seed=2)
+    ref, got = _both(torch.as_tensor(R.astype(np.float32)).cuda(), "dense", "f32", trials=2)
+    for g in got:
+        assert abs(g - ref) <= 1e-6 * abs(ref)
+
+
 def test_static_banded_f32_matches_allocating_entry_point():
     vals = synth.band_diag_dominant(100_000, half_bw=16, seed=3, dtype=np.float32)
     ref, got = _both(torch.as_tensor(vals).cuda(), "dia", "f32")
     for g in got:
         assert abs(g - ref) <= RTOL * abs(ref)
+
+
+def test_static_banded_several_trials():
+    vals = synth.band_diag_dominant(40_000, half_bw=8, seed=5, dtype=np.float64)
+    ref, got = _both(torch.as_tensor(vals).cuda(), "dia", "f64", trials=3)
+    for g in got:
+        assert abs(g - ref) <= RTOL * abs(ref)
+
+
+def test_static_allocates_no_device_memory():
+    """The property the entry point exists for: after a first call (which
+    loads the library's module), further calls leave the device's free
+    memory and torch's allocator statistics unchanged."""
+    lib = _lib.load()
+    R, _, _ = synth.dense_exp(1024, 100.0, seed=4)
+    t = torch.as_tensor(R).cuda()
+    mat = _matrix(t, "dense")
+    par = _params("f64", 30, 2, 9)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    lam = C.c_double()
+    assert lib.vne_lambda_max_static(C.byref(mat), C.byref(par), C.byref(lam), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(5):
+        assert lib.vne_lambda_max_static(C.byref(mat), C.byref(par), C.byref(lam), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == alloc0
 
 
 def test_static_refuses_sizes_beyond_its_scratch():
@@ -93,3 +131,16 @@ def test_static_refuses_sizes_beyond_its_scratch():
     lam = C.c_double()
     st = lib.vne_lambda_max_static(C.byref(mat), C.byref(par), C.byref(lam), None)
     assert st == 8  # VNE_ERR_UNSUPPORTED
+
+
+def test_static_refuses_a_band_without_diagonals():
+    # refused on the host, before any launch
+    lib = _lib.load()
+    vals = torch.zeros((1, 1000), dtype=torch.float64, device="cuda")
+    mat = _matrix(vals, "dia")
+    par = _params("f64", 3, 1, 1)
+    lam = C.c_double()
+    for bad in (0, -1):
+        mat.n_diags = bad
+        st = lib.vne_lambda_max_static(C.byref(mat), C.byref(par), C.byref(lam), None)
+        assert st == 1  # VNE_ERR_INVALID_ARG
