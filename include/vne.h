@@ -59,11 +59,23 @@ enum { VNE_F64 = 0, VNE_F32 = 1, VNE_C128 = 2, VNE_C64 = 3 };
  *   F64     : FP64 operands, FP64 accumulation (dense and banded)
  *   F32     : FP32 operands, FP32 accumulation (dense and banded)
  *   BF16    : R and Y rounded to bf16, FP32 accumulation on the tensor cores
- *   BF16X3  : R = R_hi + R_lo, Y = Y_hi + Y_lo in bf16, products
- *             R_hi Y_hi + R_hi Y_lo + R_lo Y_hi accumulated in FP32 (dense only)
+ *   BF16X3  : R = R_0 + R_1, Y = Y_0 + Y_1 in bf16 (piece k = bf16 of the
+ *             residual of the earlier pieces), products R_0 Y_0 + R_0 Y_1 +
+ *             R_1 Y_0 accumulated in FP32 (dense only)
+ *   BF16X6  : three bf16 pieces of R and of Y, the six products R_a Y_b with
+ *             a + b <= 2 accumulated in FP32: about FP32 operand precision
+ *             (dense only)
  * The three-term update keeps an FP32 (or FP64) master copy of Y; moments,
- * coefficients and the final combination are always FP64. */
-enum { VNE_PREC_F64 = 0, VNE_PREC_F32 = 1, VNE_PREC_BF16 = 2, VNE_PREC_BF16X3 = 3 };
+ * coefficients and the final combination are always FP64.  The power method
+ * (the interval u) runs in bf16 for BF16, and in the input's precision (FP64
+ * for an FP64 R) for the split modes BF16X3 and BF16X6. */
+enum {
+    VNE_PREC_F64 = 0,
+    VNE_PREC_F32 = 1,
+    VNE_PREC_BF16 = 2,
+    VNE_PREC_BF16X3 = 3,
+    VNE_PREC_BF16X6 = 4
+};
 /* vne_params.probe: law of the trace-estimator probe vectors g_j */
 enum { VNE_RADEMACHER = 0, VNE_GAUSSIAN = 1 };
 /* vne_matrix.memory */
@@ -211,7 +223,8 @@ vne_status vne_tc_shape(int64_t n, int32_t ncols, int32_t sm_count, int32_t* sha
  * start vectors in {+1,-1}^n after t = power_iters products (each iterate is
  * divided by its 2-norm, which leaves the Rayleigh quotient unchanged).  The
  * products use the arithmetic of p->precision (BF16 modes use bf16 R with FP32
- * accumulation); the Rayleigh quotient is accumulated in FP64.
+ * accumulation; BF16X3 / BF16X6 use R in its input precision); the Rayleigh
+ * quotient is accumulated in FP64.
  *   lam_out : host, 1 double. */
 vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* p,
                           double* lam_out, void* stream);

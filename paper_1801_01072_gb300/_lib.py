@@ -14,7 +14,7 @@ STATUS = {
 }
 DENSE, DIA = 0, 1
 F64, F32, C128, C64 = 0, 1, 2, 3
-PREC = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3}
+PREC = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4}
 PROBE = {"rademacher": 0, "gaussian": 1}
 MEM_DEVICE, MEM_HOST = 0, 1
 

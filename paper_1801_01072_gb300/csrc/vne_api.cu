@@ -209,7 +209,7 @@ vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
         if (R->n_diags < 1) return VNE_ERR_INVALID_ARG;
         if (dia_supported_halfbw(R->n_diags) < 0) return VNE_ERR_UNSUPPORTED;
     }
-    if (p->precision < VNE_PREC_F64 || p->precision > VNE_PREC_BF16X3) return VNE_ERR_INVALID_ARG;
+    if (p->precision < VNE_PREC_F64 || p->precision > VNE_PREC_BF16X6) return VNE_ERR_INVALID_ARG;
     if (p->probe != VNE_RADEMACHER && p->probe != VNE_GAUSSIAN) return VNE_ERR_INVALID_ARG;
     // u_override > 0 replaces the power method; u must lie in (0, 1] (Algorithms 1a/1b step 3)
     if (std::isnan(p->u_override) || std::isinf(p->u_override) || p->u_override > 1.0)
@@ -255,7 +255,8 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     const bool dense = R.layout == VNE_DENSE;
     const int prec = p->precision;
     const bool tc = dense && prec >= VNE_PREC_BF16;
-    const bool x3 = prec == VNE_PREC_BF16X3;
+    // bf16 pieces of R and Y on the tensor-core path: 1 (BF16), 2 (bf16x3), 3 (bf16x6)
+    const int pieces = !tc ? 0 : prec == VNE_PREC_BF16 ? 1 : prec == VNE_PREC_BF16X3 ? 2 : 3;
     const bool f64 = prec == VNE_PREC_F64;
     const bool has_cheb = mode == MODE_CHEB || mode == MODE_BOTH;
     const bool has_tay = mode == MODE_TAYLOR || mode == MODE_BOTH;
@@ -291,10 +292,19 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     }
     const int power_blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 8 * h->sm_count)
                                    : 4 * h->sm_count;
+    // Arithmetic of the power-method products (dense): the FP64/FP32 paths use
+    // their own; BF16 streams bf16 R; the split modes (bf16x3, bf16x6) keep
+    // lambda_max and u in the input's precision (FP64 for an FP64 R; the FP32
+    // embedding of a complex R), so that u does not carry bf16 rounding.
+    int pw_rdt;  // 0 FP64 R, 1 FP32 R, 2 bf16 piece 0
+    if (!tc) pw_rdt = f64 ? 0 : 1;
+    else if (pieces == 1) pw_rdt = 2;
+    else pw_rdt = (!cplx && R.dtype == VNE_F64) ? 0 : 1;
+    const int pw_xdouble = dense ? (pw_rdt == 0 ? 1 : 0) : (f64 ? 1 : 0);
 
     // ---- workspace plan (two passes) ----
     const size_t vt = f64 ? 8 : 4;  // master / operand element size of SIMT & DIA paths
-    auto plan = [&](Bump& b, void** Rcopy, void** Rop, __nv_bfloat16** Rhi, __nv_bfloat16** Rlo,
+    auto plan = [&](Bump& b, void** Rcopy, void** Rop, __nv_bfloat16** Rpc,
                     double** sc, double** ppart, unsigned int** counter, void** x0, void** x1,
                     void** G, uint64_t** bits, void** Yb0, void** Yb1, void** Yb2, void** Zpart,
                     __nv_bfloat16** Sh, double** part, double** mom_c, double** mom_t,
@@ -307,10 +317,9 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         if (R.memory == VNE_MEM_HOST)
             *Rcopy = b.take<char>((size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype));
         *Rop = nullptr;
-        *Rhi = *Rlo = nullptr;
+        for (int k = 0; k < kMaxPieces; ++k) Rpc[k] = nullptr;
         if (tc) {
-            *Rhi = b.take<__nv_bfloat16>((size_t)rows_pad * ldk);
-            if (x3) *Rlo = b.take<__nv_bfloat16>((size_t)rows_pad * ldk);
+            for (int k = 0; k < pieces; ++k) Rpc[k] = b.take<__nv_bfloat16>((size_t)rows_pad * ldk);
         } else {
             const int want = f64 ? VNE_F64 : VNE_F32;
             if (R.dtype != want) *Rop = b.take<char>((size_t)(dense ? n * n : (int64_t)D * n) * vt);
@@ -318,7 +327,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         if (tc && cplx) {  // the embedding, FP32, before the bf16 split
             *Rop = b.take<char>((size_t)n * n * 4);
         }
-        const size_t xs = tc ? 4 : vt;
+        const size_t xs = pw_xdouble ? 8 : 4;
         *x0 = b.take<char>((size_t)n * q * xs);
         *x1 = b.take<char>((size_t)n * q * xs);
         *G = *Yb0 = *Yb1 = *Yb2 = *Zpart = nullptr;
@@ -335,20 +344,20 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         *Yb1 = b.take<char>((size_t)n * S * ms);
         *Yb2 = b.take<char>((size_t)n * S * ms);
         if (dense && !tc) *Zpart = b.take<char>((size_t)splitk * S * n * vt);
-        if (tc) *Sh = b.take<__nv_bfloat16>((size_t)4 * S_pad * ldk);
+        if (tc) *Sh = b.take<__nv_bfloat16>((size_t)2 * pieces * S_pad * ldk);
         *part = b.take<double>((size_t)ntiles0 * S + (size_t)T_steps * ntiles * S);
         *mom_c = b.take<double>((size_t)(m + 1) * s);
         *mom_t = b.take<double>((size_t)(m + 1) * s);
     };
     void *Rcopy, *Rop, *x0, *x1, *G, *Yb0, *Yb1, *Yb2, *Zpart;
-    __nv_bfloat16 *Rhi, *Rlo, *Sh;
+    __nv_bfloat16 *Rpc[kMaxPieces], *Sh;
     double *sc, *ppart, *part, *mom_c, *mom_t;
     float* mws;
     unsigned int* counter;
     uint64_t* bits;
     {
         Bump b0(nullptr);
-        plan(b0, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
+        plan(b0, &Rcopy, &Rop, Rpc, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
              &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
         if (out.measure) {
             *out.measured = b0.off + 4096;
@@ -361,7 +370,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             base = h->ws;
         }
         Bump b1(base);
-        plan(b1, &Rcopy, &Rop, &Rhi, &Rlo, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
+        plan(b1, &Rcopy, &Rop, Rpc, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
              &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
     }
     h->ev_used = 0;
@@ -389,9 +398,9 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         Rk = Rop;
         ldr = n;
         if (tc)
-            c.launched(launch_dense_convert_bf16(Rop, VNE_F32, n, n, Rhi, Rlo, rows_pad, ldk, c.st));
-    } else if (tc) {
-        c.launched(launch_dense_convert_bf16(Rdata, R.dtype, n, R.ld, Rhi, Rlo, rows_pad, ldk, c.st));
+            c.launched(launch_dense_convert_bf16(Rop, VNE_F32, n, n, Rpc, pieces, rows_pad, ldk, c.st));
+    } else if (tc && (mode != MODE_POWER || pw_rdt == 2)) {
+        c.launched(launch_dense_convert_bf16(Rdata, R.dtype, n, R.ld, Rpc, pieces, rows_pad, ldk, c.st));
     } else if (Rop) {
         if (dense) {
             if (f64) c.launched(launch_dense_convert_f64(Rdata, R.dtype, n, R.ld, (double*)Rop, c.st));
@@ -405,21 +414,20 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
 
     // ---- power method (Algorithm alg:power) or the given u ----
     if (do_power) {
-        if (f64) c.launched(launch_power_init<double>((double*)x0, n, q, p->seed, sc, c.st));
+        if (pw_xdouble) c.launched(launch_power_init<double>((double*)x0, n, q, p->seed, sc, c.st));
         else c.launched(launch_power_init<float>((float*)x0, n, q, p->seed, sc, c.st));
         void* xa = x0;
         void* xb = x1;
-        const int rdt = tc ? 2 : (f64 ? 0 : 1);
-        const void* Rp = tc ? (const void*)Rhi : Rk;
-        const int64_t ldp = tc ? ldk : ldr;
+        const void* Rp = pw_rdt == 2 ? (const void*)Rpc[0] : Rk;
+        const int64_t ldp = pw_rdt == 2 ? ldk : ldr;
         // the products are timed as one span: an event between two of them
         // would stop the next one from starting early (programmatic launch)
         c.prof_begin();
         for (int it = 0; it <= p->power_iters && c.ok(); ++it) {
             const int fin = it == p->power_iters;
             if (dense)
-                c.launched(launch_power_step_dense(Rp, rdt, n, ldp, xa, xb, f64, q, sc, ppart,
-                                                   counter, fin, u_scale, power_blocks, c.st));
+                c.launched(launch_power_step_dense(Rp, pw_rdt, n, ldp, xa, xb, pw_xdouble, q, sc,
+                                                   ppart, counter, fin, u_scale, power_blocks, c.st));
             else
                 c.launched(launch_power_step_dia(Rk, f64 ? 0 : 1, n, ldr, D, xa, xb, q, sc, ppart,
                                                  counter, fin, u_scale, power_blocks, c.st));
@@ -433,23 +441,22 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     // ---- probes, recurrence, combine ----
     if (mode != MODE_POWER && c.ok()) {
         Partials P{part, ntiles0, ntiles, S};
-        __nv_bfloat16* sh_hi[2] = {nullptr, nullptr};
-        __nv_bfloat16* sh_lo[2] = {nullptr, nullptr};
+        // bf16 pieces of the probe blocks, double-buffered across steps: sh[b][k]
+        __nv_bfloat16* sh[2][kMaxPieces] = {};
         if (tc) {
-            c.chk(cudaMemsetAsync(Sh, 0, (size_t)4 * S_pad * ldk * sizeof(__nv_bfloat16), c.st));
-            sh_hi[0] = Sh;
-            sh_hi[1] = Sh + (size_t)S_pad * ldk;
-            sh_lo[0] = Sh + (size_t)2 * S_pad * ldk;
-            sh_lo[1] = Sh + (size_t)3 * S_pad * ldk;
+            c.chk(cudaMemsetAsync(Sh, 0, (size_t)2 * pieces * S_pad * ldk * sizeof(__nv_bfloat16),
+                                  c.st));
+            for (int b = 0; b < 2; ++b)
+                for (int k = 0; k < pieces; ++k)
+                    sh[b][k] = Sh + (size_t)(b * pieces + k) * S_pad * ldk;
         }
         if (dense) {
             if (f64)
-                c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, nullptr, 0,
+                c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, 0, 0,
                                                      n, S, s, p->probe, p->seed, P, 256, c.st,
                                                      R.n));
             else
-                c.launched(launch_dense_init<float>((float*)G, (float*)Yb0, sh_hi[0],
-                                                    x3 ? sh_lo[0] : nullptr, ldk, n, S, s,
+                c.launched(launch_dense_init<float>((float*)G, (float*)Yb0, sh[0], pieces, ldk, n, S, s,
                                                     p->probe, p->seed, P, rows_per_tile0, c.st,
                                                     R.n));
         } else {
@@ -484,12 +491,12 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             if (!tc) c.prof_begin();
             if (tc) {
                 TcStep a{};
-                a.Rhi = Rhi;
-                a.Rlo = x3 ? Rlo : nullptr;
-                a.Yhi = sh_hi[(t - 1) & 1];
-                a.Ylo = x3 ? sh_lo[(t - 1) & 1] : nullptr;
-                a.Yhi_out = sh_hi[t & 1];
-                a.Ylo_out = x3 ? sh_lo[t & 1] : nullptr;
+                a.pieces = pieces;
+                for (int k = 0; k < pieces; ++k) {
+                    a.R[k] = Rpc[k];
+                    a.Y[k] = sh[(t - 1) & 1][k];
+                    a.Y_out[k] = sh[t & 1][k];
+                }
                 a.G = (const float*)G;
                 a.Yprev = (const float*)Yp;
                 a.Yprev2 = (const float*)Yp2;

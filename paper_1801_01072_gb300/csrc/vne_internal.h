@@ -38,8 +38,9 @@ cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint
 // Dense layout [column][row] with row stride n (master) / ldk (bf16 shadows).
 // Rows i < probe_n draw counter j*probe_n + i; rows probe_n <= i < n are zero
 // (the lower half of the probes [g; 0] of a Hermitian embedding).
+// Ysh[k], k < pieces (pieces 0: none): the bf16 pieces of Y0 (see launch_tc_step).
 template <typename T>
-cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
+cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
                               int rows_per_tile, cudaStream_t st, int64_t probe_n);
 // Banded layout [row][column] (row stride S).  Rademacher probes are packed
@@ -54,9 +55,10 @@ cudaError_t launch_dense_convert_f64(const void* src, int src_dtype, int64_t n, 
                                      double* dst, cudaStream_t st);
 cudaError_t launch_dense_convert_f32(const void* src, int src_dtype, int64_t n, int64_t ld,
                                      float* dst, cudaStream_t st);
-// bf16 split, zero padded to rows_pad x ldk (ldk >= n): hi = bf16(R), lo = bf16(R - hi)
+// bf16 split, zero padded to rows_pad x ldk (ldk >= n): piece 0 = bf16(R), piece k
+// = bf16(R - pieces 0..k-1), residuals in FP64; out[k] for k < pieces (1..3)
 cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
-                                      __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t rows_pad,
+                                      __nv_bfloat16* const* out, int pieces, int64_t rows_pad,
                                       int64_t ldk, cudaStream_t st);
 cudaError_t launch_dia_convert(const void* src, int src_dtype, int64_t n, int64_t ld, int D,
                                void* dst, int dst_dtype, cudaStream_t st);
@@ -113,13 +115,15 @@ int dia_supported_halfbw(int D);  // the compiled window >= D-1, or -1
 int dia_step_grid(int is_double, int D, int64_t n, int ncols, int sm_count);
 
 // ---- dense tensor-core recurrence (vne_tc.cu) -------------------------------------
+// R and Y are each a sum of `pieces` bf16 matrices (1: BF16; 2: bf16x3; 3:
+// bf16x6): piece k holds the rounding residual of pieces 0..k-1.  The step
+// accumulates the products R_a Y_b with a + b < pieces in FP32 (1, 3 or 6).
+constexpr int kMaxPieces = 3;
 struct TcStep {
-    const __nv_bfloat16* Rhi;
-    const __nv_bfloat16* Rlo;   // NULL unless bf16x3
-    const __nv_bfloat16* Yhi;   // shadows of Y_{t-1}, [S][ldk]
-    const __nv_bfloat16* Ylo;   // NULL unless bf16x3
-    __nv_bfloat16* Yhi_out;     // shadows of Y_t
-    __nv_bfloat16* Ylo_out;
+    const __nv_bfloat16* R[kMaxPieces];  // [rows_pad][ldk]; pieces >= `pieces` unused
+    const __nv_bfloat16* Y[kMaxPieces];  // shadows of Y_{t-1}, [S_pad][ldk]
+    __nv_bfloat16* Y_out[kMaxPieces];    // shadows of Y_t
+    int pieces;
     const float* G;             // [s][n]
     const float* Yprev;         // FP32 master Y_{t-1} [S][n]
     const float* Yprev2;        // FP32 master Y_{t-2}

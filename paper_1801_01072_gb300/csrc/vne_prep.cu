@@ -79,37 +79,65 @@ cudaError_t launch_dense_convert_f32(const void* src, int src_dtype, int64_t n, 
     return cudaGetLastError();
 }
 
-// hi = bf16(R), lo = bf16(R - hi) (R first rounded to FP32), zero padding
-// outside the n x n block.  Each thread converts 8 consecutive columns.
+// Piece 0 = bf16(R), piece k = bf16(R - pieces 0..k-1), zero padding outside
+// the n x n block.  One or two pieces split R rounded to FP32 (the residual of
+// a float and its bf16 rounding is exact in FP32); three pieces take the
+// residuals in FP64, since they resolve R beyond FP32's 24 bits.  Each thread
+// converts 8 consecutive columns.
+struct BfPieces {
+    __nv_bfloat16* p[kMaxPieces];
+};
+template <int PIECES>
 __global__ void k_dense_convert_bf16(const void* src, int dtype, int64_t n, int64_t ld,
-                                     __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t rows_pad,
-                                     int64_t ldk) {
+                                     BfPieces out, int64_t rows_pad, int64_t ldk) {
     const int64_t groups = ldk / 8;
     const int64_t total = rows_pad * groups;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / groups, k0 = (e - i * groups) * 8;
-        __align__(16) __nv_bfloat16 h8[8], l8[8];
+        __align__(16) __nv_bfloat16 b8[PIECES][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t k = k0 + q;
-            float v = 0.f;
-            if (i < n && k < n) v = (float)load_entry(src, dtype, i * ld + k);
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            h8[q] = h;
-            l8[q] = __float2bfloat16_rn(v - __bfloat162float(h));
+            const bool in = i < n && k < n;
+            if (PIECES < 3) {
+                const float v = in ? (float)load_entry(src, dtype, i * ld + k) : 0.f;
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                b8[0][q] = h;
+                if (PIECES == 2) b8[PIECES - 1][q] = __float2bfloat16_rn(v - __bfloat162float(h));
+            } else {
+                double r = in ? load_entry(src, dtype, i * ld + k) : 0.0;
+#pragma unroll
+                for (int c = 0; c < PIECES; ++c) {
+                    // bf16 of the FP64 residual through FP32 (the FP32 rounding
+                    // moves it by far less than the bf16 spacing)
+                    const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
+                    b8[c][q] = b;
+                    r -= (double)__bfloat162float(b);
+                }
+            }
         }
-        *(uint4*)(hi + i * ldk + k0) = *(const uint4*)h8;
-        if (lo) *(uint4*)(lo + i * ldk + k0) = *(const uint4*)l8;
+#pragma unroll
+        for (int c = 0; c < PIECES; ++c) *(uint4*)(out.p[c] + i * ldk + k0) = *(const uint4*)b8[c];
     }
 }
 
 cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
-                                      __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t rows_pad,
+                                      __nv_bfloat16* const* out, int pieces, int64_t rows_pad,
                                       int64_t ldk, cudaStream_t st) {
-    if (ldk % 8 != 0) return cudaErrorInvalidValue;
-    k_dense_convert_bf16<<<grid_for(rows_pad * (ldk / 8)), 256, 0, st>>>(src, src_dtype, n, ld, hi,
-                                                                         lo, rows_pad, ldk);
+    if (ldk % 8 != 0 || pieces < 1 || pieces > kMaxPieces || !out) return cudaErrorInvalidValue;
+    BfPieces ps{};
+    for (int c = 0; c < pieces; ++c) {
+        if (!out[c]) return cudaErrorInvalidValue;
+        ps.p[c] = out[c];
+    }
+    const unsigned g = grid_for(rows_pad * (ldk / 8));
+    if (pieces == 1)
+        k_dense_convert_bf16<1><<<g, 256, 0, st>>>(src, src_dtype, n, ld, ps, rows_pad, ldk);
+    else if (pieces == 2)
+        k_dense_convert_bf16<2><<<g, 256, 0, st>>>(src, src_dtype, n, ld, ps, rows_pad, ldk);
+    else
+        k_dense_convert_bf16<3><<<g, 256, 0, st>>>(src, src_dtype, n, ld, ps, rows_pad, ldk);
     return cudaGetLastError();
 }
 

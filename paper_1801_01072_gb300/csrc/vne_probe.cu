@@ -27,12 +27,15 @@ cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint
 
 // Dense layout: one thread per row of a row tile (blockDim.x = rows_per_tile),
 // blockIdx.y = probe j.  Writes G[j][i], Y0[c][i] for every column c = j + r*s
-// (r < S/s), the bf16 hi/lo shadows of Y0 if requested, and the slot-0
-// partials sum_i g_j[i]^2 of each row tile.
+// (r < S/s), the bf16 pieces of Y0 if requested (piece k = bf16 of the
+// residual of pieces 0..k-1, exact in FP32), and the slot-0 partials
+// sum_i g_j[i]^2 of each row tile.
+struct Pieces {
+    __nv_bfloat16* p[kMaxPieces];
+};
 template <typename T>
-__global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
-                             int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                             int64_t probe_n) {
+__global__ void k_dense_init(T* G, T* Y0, Pieces Ysh, int pieces, int64_t ldk, int64_t n, int S,
+                             int s, int kind, uint64_t seed, Partials P, int64_t probe_n) {
     __shared__ double sh[32];
     const int j = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,11 +50,11 @@ __global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo
         G[(int64_t)j * n + i] = gt;
         for (int c = j; c < S; c += s) {
             Y0[(int64_t)c * n + i] = gt;
-            if (Yhi) {
-                const float gf = (float)gt;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(gf);
-                Yhi[(int64_t)c * ldk + i] = hi;
-                if (Ylo) Ylo[(int64_t)c * ldk + i] = __float2bfloat16_rn(gf - __bfloat162float(hi));
+            float r = (float)gt;
+            for (int k = 0; k < pieces; ++k) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(r);
+                Ysh.p[k][(int64_t)c * ldk + i] = b;
+                r -= __bfloat162float(b);
             }
         }
     }
@@ -67,18 +70,24 @@ __global__ void k_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo
 }
 
 template <typename T>
-cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, int64_t ldk,
+cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
                               int rows_per_tile, cudaStream_t st, int64_t probe_n) {
+    if (pieces < 0 || pieces > kMaxPieces || (pieces > 0 && !Ysh)) return cudaErrorInvalidValue;
+    Pieces ps{};
+    for (int k = 0; k < pieces; ++k) {
+        if (!Ysh[k]) return cudaErrorInvalidValue;
+        ps.p[k] = Ysh[k];
+    }
     dim3 grid((unsigned)((n + rows_per_tile - 1) / rows_per_tile), (unsigned)s);
-    k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, Yhi, Ylo, ldk, n, S, s, kind, seed, P,
+    k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, ps, pieces, ldk, n, S, s, kind, seed, P,
                                                     probe_n);
     return cudaGetLastError();
 }
-template cudaError_t launch_dense_init<double>(double*, double*, __nv_bfloat16*, __nv_bfloat16*,
+template cudaError_t launch_dense_init<double>(double*, double*, __nv_bfloat16* const*, int,
                                                int64_t, int64_t, int, int, int, uint64_t, Partials,
                                                int, cudaStream_t, int64_t);
-template cudaError_t launch_dense_init<float>(float*, float*, __nv_bfloat16*, __nv_bfloat16*,
+template cudaError_t launch_dense_init<float>(float*, float*, __nv_bfloat16* const*, int,
                                               int64_t, int64_t, int, int, int, uint64_t, Partials,
                                               int, cudaStream_t, int64_t);
 

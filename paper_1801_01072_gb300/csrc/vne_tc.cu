@@ -1,6 +1,9 @@
 // Dense recurrence step on the 5th-generation tensor cores (tcgen05, TMEM,
-// TMA), BF16 operands with FP32 accumulation, optionally split precision
-// (bf16x3: R_hi Y_hi + R_hi Y_lo + R_lo Y_hi).
+// TMA), BF16 operands with FP32 accumulation, optionally split precision:
+// R and Y are each held as P bf16 pieces (piece k = bf16 of the residual of
+// pieces 0..k-1) and the step accumulates the products R_a Y_b with a + b < P:
+// P = 1 BF16, P = 2 bf16x3 (R_0 Y_0 + R_0 Y_1 + R_1 Y_0), P = 3 bf16x6 (every
+// product down to the 2^-16 level: about the precision of FP32 operands).
 //
 // One CTA computes a 128 x BN tile of Z = R Y_{t-1} (rows of R x probe
 // columns) and applies the fused epilogue of the step:
@@ -11,9 +14,11 @@
 //   Y_t = Y_{t-1} - Z/u;
 // and writes the bf16 hi/lo shadows of Y_t that are the next step's B operand.
 //
-// Operands: R_hi/R_lo [rows_pad][ldk] and the Y shadows [S_pad][ldk], both
-// K-major bf16, loaded by TMA into 128-byte-swizzled shared memory tiles
-// (BK = 64 elements = 128 bytes per row).  Roles (256 threads, 8 warps):
+// Operands: the R pieces [rows_pad][ldk] and the Y shadows [S_pad][ldk], both
+// K-major bf16, loaded by TMA into swizzled shared memory tiles (BK = 64
+// elements = 128-byte rows with the 128-byte swizzle, or BK = 32 = 64-byte rows
+// with the 64-byte swizzle, which keeps a 3-deep ring for P = 3).  Roles (256
+// threads, 8 warps):
 //   warp 0 lane 0 : TMA producer over a ring of `stages` buffers
 //   warp 1        : TMEM allocation; lane 0 issues tcgen05.mma (M=128, N=BN,
 //                   K=16 per instruction) and commits to the ring's "empty"
@@ -27,6 +32,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include <algorithm>
 
@@ -107,20 +113,64 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+// K-major operand tile with rows of bk bf16: bk = 64 -> 128-byte rows, 128-byte
+// swizzle, 8-row groups 1024 B apart; bk = 32 -> 64-byte rows, 64-byte swizzle,
+// 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr, int bk) {
+    const uint32_t row_bytes = (uint32_t)bk * 2u;
     uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-    d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
-    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                    // descriptor version
-    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused here)
+    d |= (uint64_t)((8u * row_bytes) >> 4) << 32;  // stride byte offset: 8 rows
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)(bk == 64 ? 2 : 4) << 61;    // 128-byte / 64-byte swizzle
     return d;
 }
 // kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+
+// The MMAs of one ring stage: products R_a Y_b with a + b < P over the stage's
+// NKS K=16 slices (+32 bytes along K per slice, descriptor units of 16 B),
+// descriptors computed once per stage (the issuing thread must keep ahead of
+// the tensor pipe).  Larger terms first, except with SMALL_FIRST (chunked
+// accumulation), where the small products go first while the fresh
+// accumulator is still small.  acc: accumulate flag of the first MMA.
+template <int P, int NKS, bool SMALL_FIRST>
+__device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint32_t aA, uint32_t bytesA,
+                                            uint32_t aB, uint32_t bytesB, int bk, uint32_t idesc,
+                                            uint32_t acc) {
+    uint64_t dA[P], dB[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        dA[p] = desc_sw(aA + (uint32_t)p * bytesA, bk);
+        dB[p] = desc_sw(aB + (uint32_t)p * bytesB, bk);
+    }
+    if (SMALL_FIRST) {
+#pragma unroll
+        for (int oo = 0; oo < P; ++oo) {
+            const int o = P - 1 - oo;
+#pragma unroll
+            for (int k = 0; k < NKS; ++k)
+#pragma unroll
+                for (int pa = 0; pa <= o; ++pa) {
+                    umma_bf16(d_tmem, dA[pa] + 2 * k, dB[o - pa] + 2 * k, idesc, acc);
+                    acc = 1u;
+                }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NKS; ++k)
+#pragma unroll
+            for (int o = 0; o < P; ++o)
+#pragma unroll
+                for (int pa = 0; pa <= o; ++pa) {
+                    umma_bf16(d_tmem, dA[pa] + 2 * k, dB[o - pa] + 2 * k, idesc, acc);
+                    acc = 1u;
+                }
+    }
 }
 
 #define TMEM_LD32(taddr, r)                                                                     \
@@ -134,6 +184,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),        \
           "=r"(r[31])                                                                           \
         : "r"(taddr))
+
+#define TMEM_ST32(taddr, r)                                                                     \
+    asm volatile(                                                                               \
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12," \
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"    \
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]),          \
+        "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]),          \
+        "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]),      \
+        "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),      \
+        "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])                              \
+        : "memory")
 
 // Named barrier 1 (barrier 0 is __syncthreads): `count` threads of whole warps.
 __device__ __forceinline__ void named_bar_arrive(uint32_t id, uint32_t count) {
@@ -169,6 +230,13 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// Plain arrive (count 1) on a barrier of this CTA.
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Kernel
@@ -180,13 +248,26 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // moment g Z; 1: first Chebyshev step, Y_1 = (2/u) Z - G; 2: three-term
 // Chebyshev step, Y_t = 2((2/u) Z - Y_{t-1}) - Y_{t-2}; moment g Y_t for both.
 // ob: Y_{t-1} of the chunk in smem ([32 cols][128 rows], Y_{t-2} 32*128 floats
-// later); yn / yh / yl: this row's entry of the chunk's first column in Y_t and
-// its bf16 shadows (yl null without the low shadow).
+// later); yn / ysh[k]: this row's entry of the chunk's first column in Y_t and
+// in its bf16 pieces k < pieces.
+struct ShPtr {
+    __nv_bfloat16* p[kMaxPieces];
+};
+__device__ __forceinline__ void store_pieces(float y, const ShPtr& ysh, int pieces, int64_t off) {
+    __nv_bfloat16 b = __float2bfloat16_rn(y);
+    ysh.p[0][off] = b;
+    if (pieces > 1) {
+        y -= __bfloat162float(b);  // exact: y minus its own rounding
+        b = __float2bfloat16_rn(y);
+        ysh.p[1][off] = b;
+        if (pieces > 2) ysh.p[2][off] = __float2bfloat16_rn(y - __bfloat162float(b));
+    }
+}
 template <int KIND>
 __device__ __forceinline__ void epi_chunk_uniform(const uint32_t* r, const float* g,
-                                                  const float* ob, float* yn, __nv_bfloat16* yh,
-                                                  __nv_bfloat16* yl, int64_t n, int64_t ldk,
-                                                  float fa, float finvu, bool row_ok, float* v) {
+                                                  const float* ob, float* yn, const ShPtr& ysh,
+                                                  int pieces, int64_t n, int64_t ldk, float fa,
+                                                  float finvu, bool row_ok, float* v) {
     float y[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
@@ -206,9 +287,7 @@ __device__ __forceinline__ void epi_chunk_uniform(const uint32_t* r, const float
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             yn[q * n] = y[q];
-            const __nv_bfloat16 hi = __float2bfloat16_rn(y[q]);
-            yh[q * ldk] = hi;
-            if (yl) yl[q * ldk] = __float2bfloat16_rn(y[q] - __bfloat162float(hi));
+            store_pieces(y[q], ysh, pieces, q * ldk);
         }
     }
 }
@@ -217,12 +296,20 @@ struct TcArgs {
     const float* Yprev;
     const float* Yprev2;
     float* Ynew;
-    __nv_bfloat16* Yhi_out;
-    __nv_bfloat16* Ylo_out;
+    ShPtr Yout;  // bf16 pieces of Y_t, [S_pad][ldk] each
     int64_t n, ldk;
     int S, s;
     int col0, col_end;  // active columns [col0, col_end)
-    int BN, stages, nkb, x3;
+    int BN, stages, nkb, pieces;
+    int bk;      // K per ring stage: 64 (128-byte swizzle) or 32 (64-byte swizzle)
+    int gst;     // 1: warps 4 and 5 stage the first G chunk of warps 0 and 1 in smem
+    // 1: chunked accumulation.  The tensor cores' FP32 accumulation truncates
+    // toward zero, a bias that grows with the number of MMAs summed into one
+    // accumulator.  Each ring stage is accumulated afresh in one of two TMEM
+    // buffers (columns [0, BN) and [BN, 2BN)), its small correction products
+    // first, and warps 4-7 add it with round-to-nearest FP32 adds into a
+    // running sum in columns [2BN, 3BN), which the epilogue reads.
+    int flush;
     int ksplit;  // 2: a CTA pair (cluster along z) splits K and swaps half accumulators
     int64_t keep_rows;  // row tiles starting below this load R evict-last (kept in L2)
     int epi_tma;       // 1: Y_{t-1}, Y_{t-2} of the CTA's own chunks arrive by TMA into smem
@@ -235,18 +322,24 @@ struct TcArgs {
     int t;
 };
 
+// Tensor maps of one step: the R pieces, the Y pieces (B operand), and the
+// FP32 masters Y_{t-1}, Y_{t-2} read by the epilogue.
+struct TcMaps {
+    CUtensorMap R[kMaxPieces];
+    CUtensorMap Y[kMaxPieces];
+    CUtensorMap Yp, Yp2;
+};
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_step(const __grid_constant__ CUtensorMap mapRhi, const __grid_constant__ CUtensorMap mapRlo,
-              const __grid_constant__ CUtensorMap mapYhi, const __grid_constant__ CUtensorMap mapYlo,
-              const __grid_constant__ CUtensorMap mapYp, const __grid_constant__ CUtensorMap mapYp2,
-              const TcArgs a) {
+    k_tc_step(const __grid_constant__ TcMaps maps, const TcArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1024-byte aligned carve-out: [stages][A_hi | B_hi | (A_lo | B_lo)] then barriers
+    // 1024-byte aligned carve-out: [stages][A_0 .. A_{P-1} | B_0 .. B_{P-1}] then barriers
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
-    const uint32_t bytesA = TC_BM * TC_BK * 2;
-    const uint32_t bytesB = (uint32_t)a.BN * TC_BK * 2;
-    const uint32_t stage_bytes = (bytesA + bytesB) * (a.x3 ? 2u : 1u);
+    const int P = a.pieces;
+    const uint32_t bytesA = TC_BM * (uint32_t)a.bk * 2;
+    const uint32_t bytesB = (uint32_t)a.BN * (uint32_t)a.bk * 2;
+    const uint32_t stage_bytes = (uint32_t)P * (bytesA + bytesB);
     uint8_t* tail = smem + a.body;  // barriers etc. after both the ring and the operand area
     uint64_t* full_bar = reinterpret_cast<uint64_t*>(tail);
     uint64_t* empty_bar = full_bar + a.stages;
@@ -254,7 +347,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t* epi_bar = accum_bar + 1;  // epilogue operands landed
     uint64_t* idle_bar = epi_bar + 1;   // split K: the peer's ring is idle (1 arrival)
     uint64_t* recv_bar = idle_bar + 1;  // split K: the peer's half has landed (1 per warp)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(recv_bar + 1);
+    uint64_t* accf_bar = recv_bar + 1;  // flush: TMEM buffer b holds a finished chunk [2]
+    uint64_t* acce_bar = accf_bar + 2;  // flush: buffer b has been added to the sum [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce_bar + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][BN]
     float* gstash = red + 4 * a.BN;                         // [2 warps][32 cols][32 lanes]
@@ -284,10 +379,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_init(epi_bar, 1);
         mbar_init(idle_bar, 1);
         mbar_init(recv_bar, TC_THREADS / 32);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], 4);  // one arrival per summing warp
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapRhi)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapYhi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.R[0])) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.Y[0])) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -311,9 +410,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* sA = smem + (size_t)st * stage_bytes;
         const int kb = kb_begin + i;
         mbar_expect_tx(&full_bar[st], stage_bytes);  // whole tiles (A and B) arrive here
-        tma_load_2d_hint(sA, &mapRhi, &full_bar[st], kb * TC_BK, m0, pol_R);
-        if (a.x3)
-            tma_load_2d_hint(sA + bytesA + bytesB, &mapRlo, &full_bar[st], kb * TC_BK, m0, pol_R);
+        for (int p = 0; p < P; ++p)
+            tma_load_2d_hint(sA + p * bytesA, &maps.R[p], &full_bar[st], kb * a.bk, m0, pol_R);
     };
     // R is written before the steps start and never by a step, so the A tiles
     // of the first ring round are requested before waiting on the previous
@@ -344,10 +442,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 load_A(i);
             }
-            uint8_t* sB = smem + (size_t)st * stage_bytes + bytesA;
-            tma_load_2d_hint(sB, &mapYhi, &full_bar[st], kb * TC_BK, n0, pol_Y);
-            if (a.x3)
-                tma_load_2d_hint(sB + bytesB + bytesA, &mapYlo, &full_bar[st], kb * TC_BK, n0, pol_Y);
+            uint8_t* sB = smem + (size_t)st * stage_bytes + P * bytesA;
+            for (int p = 0; p < P; ++p)
+                tma_load_2d_hint(sB + p * bytesB, &maps.Y[p], &full_bar[st], kb * a.bk, n0, pol_Y);
             issued_kb = i + 1;
         }
         if (timed_out) {
@@ -371,27 +468,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t aA = smem_u32(smem + (size_t)st * stage_bytes);
-            const uint32_t aB = aA + bytesA;
-            const uint64_t dA = desc_sw128(aA), dB = desc_sw128(aB);
-#pragma unroll
-            for (int k = 0; k < TC_BK / 16; ++k) {
-                // +32 bytes along K per K=16 slice (descriptor units of 16 B)
-                umma_bf16(tmem_base, dA + 2 * k, dB + 2 * k, idesc, (i | k) != 0);
-            }
-            if (a.x3) {
-                const uint32_t aAl = aB + bytesB, aBl = aAl + bytesA;
-                const uint64_t dAl = desc_sw128(aAl), dBl = desc_sw128(aBl);
-#pragma unroll
-                for (int k = 0; k < TC_BK / 16; ++k) {
-                    umma_bf16(tmem_base, dA + 2 * k, dBl + 2 * k, idesc, 1u);
-                    umma_bf16(tmem_base, dAl + 2 * k, dB + 2 * k, idesc, 1u);
+            const uint32_t aB = aA + (uint32_t)P * bytesA;
+            if (a.flush) {
+                // this stage is one chunk, accumulated afresh in buffer i & 1
+                // once the summing warps have taken its previous contents
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait(&acce_bar[b], (uint32_t)((i >> 1) - 1) & 1u, abort_flag)) {
+                    timed_out = true;
+                    break;
                 }
+                tc_fence_after();
+                const uint32_t dcol = tmem_base + (uint32_t)(b * a.BN);
+                // the small products first, while the accumulator is small
+                if (a.bk == 32)
+                    issue_stage<3, 2, true>(dcol, aA, bytesA, aB, bytesB, 32, idesc, 0u);
+                else
+                    issue_stage<3, 4, true>(dcol, aA, bytesA, aB, bytesB, 64, idesc, 0u);
+                tc_commit(&accf_bar[b]);
+                tc_commit(&empty_bar[st]);
+                continue;
             }
+            const uint32_t acc0 = i != 0 ? 1u : 0u;
+            if (P == 1)
+                issue_stage<1, 4, false>(tmem_base, aA, bytesA, aB, bytesB, 64, idesc, acc0);
+            else if (P == 2)
+                issue_stage<2, 4, false>(tmem_base, aA, bytesA, aB, bytesB, 64, idesc, acc0);
+            else if (a.bk == 32)
+                issue_stage<3, 2, false>(tmem_base, aA, bytesA, aB, bytesB, 32, idesc, acc0);
+            else
+                issue_stage<3, 4, false>(tmem_base, aA, bytesA, aB, bytesB, 64, idesc, acc0);
             // frees the ring slot once these MMAs finish
             tc_commit(&empty_bar[st]);
         }
         if (timed_out) *abort_flag = 1;
         tc_commit(accum_bar);  // all issued MMAs (possibly none) complete -> arrive
+    } else if (a.flush && warp >= 4 && rank_ok) {
+        // ---------------- chunk sums (flush) ----------------
+        // warp 4 + g reads TMEM lanes 32g..32g+31: the rows of lane group g
+        const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t run = tmem_base + lrow + (uint32_t)(2 * a.BN);
+        for (int c = 0; c < nkb_local; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(&accf_bar[b], (uint32_t)(c >> 1) & 1u, abort_flag)) {
+                timed_out = true;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t buf = tmem_base + lrow + (uint32_t)(b * a.BN);
+            for (int cb = 0; cb < a.BN / 32; ++cb) {
+                uint32_t r[32];
+                TMEM_LD32(buf + (uint32_t)(cb * 32), r);
+                if (c > 0) {
+                    uint32_t q[32];
+                    TMEM_LD32(run + (uint32_t)(cb * 32), q);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(q[e]));
+                } else {
+                    tmem_wait_ld();
+                }
+                TMEM_ST32(run + (uint32_t)(cb * 32), r);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_local(&acce_bar[b]);
+        }
+        if (timed_out) *abort_flag = 1;
     }
     __syncwarp();
 
@@ -433,9 +577,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // warps 4 and 5, which own the same rows, stage those warps' first chunk
     // in shared memory; loads still in flight in warps 0 and 1 would hold up
     // their next shared-memory access and the cluster barrier behind it.
+    // (Without room for that stash, gst = 0, warps 0 and 1 load their own.)
     float gv[32];
-    if (warp >= 2 && ck_first < ck_hi) load_g(ck_first, gv);
-    if (warp == 4 || warp == 5) {
+    if ((warp >= 2 || !a.gst) && ck_first < ck_hi) load_g(ck_first, gv);
+    if (a.gst && (warp == 4 || warp == 5)) {
         float gs[32];
         load_g(ck_lo, gs);  // ck_lo < ck_hi: every CTA owns at least one chunk
         float* dst = gstash + (warp - 4) * 32 * 32 + lane;
@@ -453,9 +598,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         volatile int never = 0;
         if (threadIdx.x == 0) mbar_wait(accum_bar, 0u, &never);
     }
+    // flush: the summing warps have finished (their TMEM stores are complete)
+    if (a.flush) named_bar_sync(2, TC_THREADS);
     bool aborted = (*abort_flag != 0) || !have_acc;
     tc_fence_after();
     __syncwarp();
+    const uint32_t zcol = a.flush ? (uint32_t)(2 * a.BN) : 0u;  // columns holding Z
 
     // Y_{t-1} and Y_{t-2} of this CTA's own chunks, [chunk][2][32 cols][128 rows]
     // FP32 in smem, by TMA: the operand ring is idle now, and the copies overlap
@@ -484,8 +632,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool n1, n2;
             chunk_needs(ck_lo + oc, n1, n2);
             const int c0 = n0 + (ck_lo + oc) * 32;
-            if (n1) tma_load_2d(ops + (size_t)(oc * 2 + 0) * 32 * TC_BM, &mapYp, epi_bar, m0, c0);
-            if (n2) tma_load_2d(ops + (size_t)(oc * 2 + 1) * 32 * TC_BM, &mapYp2, epi_bar, m0, c0);
+            if (n1) tma_load_2d(ops + (size_t)(oc * 2 + 0) * 32 * TC_BM, &maps.Yp, epi_bar, m0, c0);
+            if (n2) tma_load_2d(ops + (size_t)(oc * 2 + 1) * 32 * TC_BM, &maps.Yp2, epi_bar, m0, c0);
         }
     }
 
@@ -506,7 +654,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t rbase = mapa_peer(smem_u32(smem), peer);
             for (int ck = (int)peer * half + chalf; ck < (int)peer * half + half; ck += 2) {
                 uint32_t r[32];
-                TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
+                TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck * 32), r);
                 tmem_wait_ld();
                 const uint32_t dst =
                     rbase + (uint32_t)(((ck - (int)peer * half) * 8 * TC_BM + rg * 32 + lane) * 16);
@@ -550,14 +698,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (uniform_ok && full && (all_cheb || all_tay)) {
             const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
             float* yn = a.Ynew + (int64_t)cbase * a.n + row;
-            __nv_bfloat16* yh = a.Yhi_out + (int64_t)cbase * a.ldk + row;
-            __nv_bfloat16* yl = a.Ylo_out ? a.Ylo_out + (int64_t)cbase * a.ldk + row : nullptr;
+            ShPtr ysh;
+            const int64_t o0 = (int64_t)cbase * a.ldk + row;
+#pragma unroll
+            for (int k = 0; k < kMaxPieces; ++k)
+                ysh.p[k] = k < a.pieces ? a.Yout.p[k] + o0 : nullptr;
             if (all_tay)
-                epi_chunk_uniform<0>(r, g, ob, yn, yh, yl, a.n, a.ldk, fa, finvu, row_ok, v);
+                epi_chunk_uniform<0>(r, g, ob, yn, ysh, a.pieces, a.n, a.ldk, fa, finvu, row_ok, v);
             else if (!three_term)
-                epi_chunk_uniform<1>(r, g, ob, yn, yh, yl, a.n, a.ldk, fa, finvu, row_ok, v);
+                epi_chunk_uniform<1>(r, g, ob, yn, ysh, a.pieces, a.n, a.ldk, fa, finvu, row_ok, v);
             else
-                epi_chunk_uniform<2>(r, g, ob, yn, yh, yl, a.n, a.ldk, fa, finvu, row_ok, v);
+                epi_chunk_uniform<2>(r, g, ob, yn, ysh, a.pieces, a.n, a.ldk, fa, finvu, row_ok, v);
         } else {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -577,10 +728,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 y = fmaf(-z, finvu, ypf(q));
             }
             a.Ynew[idx] = y;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(y);
-            a.Yhi_out[(int64_t)c * a.ldk + row] = hi;
-            if (a.Ylo_out)
-                a.Ylo_out[(int64_t)c * a.ldk + row] = __float2bfloat16_rn(y - __bfloat162float(hi));
+            store_pieces(y, a.Yout, a.pieces, (int64_t)c * a.ldk + row);
         }
         }
 #pragma unroll
@@ -595,7 +743,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         red[rg * a.BN + ck * 32 + lane] = v[0];
     };
-    if (warp < 2) {
+    if (a.gst && warp < 2) {
         named_bar_sync(1, 128);  // warps 4 and 5 have staged this warp's first G chunk
         const float* src = gstash + warp * 32 * 32 + lane;
 #pragma unroll
@@ -605,7 +753,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // operands in smem; the next chunk's G is requested while this one runs
         for (int ck = ck_first; ck < ck_hi; ck += 2) {
             uint32_t r[32];
-            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
+            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck * 32), r);
             const bool more = ck + 2 < ck_hi;
             float gn[32];
             if (more) load_g(ck + 2, gn);
@@ -625,7 +773,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // otherwise alias them and serialise the chunk
         for (int ck = ck_first; ck < ck_hi; ck += 2) {
             uint32_t r[32];
-            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + (uint32_t)(ck * 32), r);
+            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck * 32), r);
             if (ck != ck_first) load_g(ck, gv);
             float yp[32], yp2[32];
             const int cbase = n0 + ck * 32;
@@ -710,10 +858,15 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t 
     cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * (fp32 ? 4 : 2)};
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
+    // bf16 operand tiles: the swizzle matches the row length (box_inner * 2 bytes)
+    const CUtensorMapSwizzle sw = fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                  : box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : box_inner * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                         : CU_TENSOR_MAP_SWIZZLE_NONE;
+    if (!fp32 && sw == CU_TENSOR_MAP_SWIZZLE_NONE) return false;
     CUresult r = enc(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                      2, const_cast<void*>(base), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
     Entry& e = cache[next];
@@ -858,27 +1011,49 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     if (ncols <= 0) return cudaSuccess;
     if ((s.ldk % TC_BK) != 0 || (s.rows_pad % TC_BM) != 0) return cudaErrorInvalidValue;
     const int mtiles = (int)(s.rows_pad / TC_BM);
-    const TcShape sh = choose_shape(ncols, mtiles, (int)(s.ldk / TC_BK), sm_count);
+    TcShape sh = choose_shape(ncols, mtiles, (int)(s.ldk / TC_BK), sm_count);
+    const int P = s.pieces;
+    if (P < 1 || P > kMaxPieces) return cudaErrorInvalidValue;
+    // three pieces: chunked accumulation (TcArgs::flush), which needs three
+    // BN-column TMEM regions (BN <= 128 of the 512 columns) and no K split
+    const bool flush = P == 3;
+    if (flush && (sh.BN > 128 || sh.ksplit > 1)) {
+        sh.ntn = (ncols + 127) / 128;
+        sh.BN = ((ncols + sh.ntn - 1) / sh.ntn + 31) / 32 * 32;
+        sh.ksplit = 1;
+    }
     const int BN = sh.BN;
     const int S_pad = (s.S + 31) / 32 * 32;
-    const bool x3 = s.Rlo != nullptr;
-    if (x3 && (!s.Ylo || !s.Ylo_out)) return cudaErrorInvalidValue;
+    for (int p = 0; p < P; ++p)
+        if (!s.R[p] || !s.Y[p] || !s.Y_out[p]) return cudaErrorInvalidValue;
+    // K per ring stage: 64 (128-byte rows); with three pieces 32 (64-byte
+    // rows), which keeps three stages of the widest tile in shared memory
+    const int bk = P == 3 ? 32 : TC_BK;
 
-    CUtensorMap mRhi, mRlo, mYhi, mYlo;
-    if (!make_map(&mRhi, s.Rhi, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mYhi, s.Yhi, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
-    if (x3) {
-        if (!make_map(&mRlo, s.Rlo, s.ldk, s.rows_pad, s.ldk, TC_BK, TC_BM)) return cudaErrorInvalidValue;
-        if (!make_map(&mYlo, s.Ylo, s.ldk, S_pad, s.ldk, TC_BK, BN)) return cudaErrorInvalidValue;
-    } else {
-        mRlo = mRhi;
-        mYlo = mYhi;
+    TcMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    for (int p = 0; p < P; ++p) {
+        if (!make_map(&maps.R[p], s.R[p], s.ldk, s.rows_pad, s.ldk, bk, TC_BM))
+            return cudaErrorInvalidValue;
+        if (!make_map(&maps.Y[p], s.Y[p], s.ldk, S_pad, s.ldk, bk, BN)) return cudaErrorInvalidValue;
     }
-    const uint32_t stage_bytes = (uint32_t)(TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (x3 ? 2u : 1u);
-    // barriers, slot, flag, red, staged G of two warps
-    const size_t tail = 2 * 8 * 16 + 16 + 16 + 4 * 256 * 4 + 2 * 32 * 32 * 4;
+    for (int p = P; p < kMaxPieces; ++p) {
+        maps.R[p] = maps.R[0];
+        maps.Y[p] = maps.Y[0];
+    }
+    const uint32_t stage_bytes = (uint32_t)(TC_BM * bk * 2 + BN * bk * 2) * (uint32_t)P;
+    // barriers, slot, flag and red; then (gst) the staged G of two warps
+    const size_t tail_min = 2 * 8 * 16 + 16 + 16 + 4 * 256 * 4;
+    const size_t stash = 2 * 32 * 32 * 4;
     const size_t max_smem = 227 * 1024;
-    int stages = (int)((max_smem - 1024 - tail) / stage_bytes);
+    int gst = 1;
+    int stages = (int)((max_smem - 1024 - tail_min - stash) / stage_bytes);
+    const int stages_nogst = (int)((max_smem - 1024 - tail_min) / stage_bytes);
+    if (stages < 3 && stages_nogst > stages) {  // a deeper ring is worth more than the stash
+        gst = 0;
+        stages = stages_nogst;
+    }
+    const size_t tail = tail_min + (gst ? stash : 0);
     if (stages > 8) stages = 8;
     if (stages < 2) return cudaErrorInvalidValue;
     // epilogue operand area (after the split-K receive buffer, if any)
@@ -897,8 +1072,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.Yprev = s.Yprev;
     a.Yprev2 = s.Yprev2;
     a.Ynew = s.Ynew;
-    a.Yhi_out = s.Yhi_out;
-    a.Ylo_out = s.Ylo_out;
+    for (int p = 0; p < kMaxPieces; ++p) a.Yout.p[p] = p < P ? s.Y_out[p] : nullptr;
     a.n = s.n;
     a.ldk = s.ldk;
     a.S = s.S;
@@ -907,24 +1081,26 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.col_end = col_end;
     a.BN = BN;
     a.stages = stages;
-    a.nkb = (int)(s.ldk / TC_BK);
-    a.x3 = x3 ? 1 : 0;
+    a.nkb = (int)(s.ldk / bk);
+    a.pieces = P;
+    a.bk = bk;
+    a.gst = gst;
+    a.flush = flush ? 1 : 0;
     a.ksplit = sh.ksplit;
-    // L2 residency: the rows the power method keeps (same budget; bf16x3 streams R_hi and R_lo)
-    a.keep_rows = l2_keep_rows(s.rows_pad, s.ldk * 2 * (x3 ? 2 : 1));
-    CUtensorMap mYp, mYp2;
+    // L2 residency: the rows the power method keeps (same budget; split modes stream every piece)
+    a.keep_rows = l2_keep_rows(s.rows_pad, s.ldk * 2 * P);
     if (epi_tma) {
-        epi_tma = make_map(&mYp, s.Yprev, s.n, s.S, s.n, TC_BM, 32, true) &&
-                  make_map(&mYp2, s.Yprev2, s.n, s.S, s.n, TC_BM, 32, true);
+        epi_tma = make_map(&maps.Yp, s.Yprev, s.n, s.S, s.n, TC_BM, 32, true) &&
+                  make_map(&maps.Yp2, s.Yprev2, s.n, s.S, s.n, TC_BM, 32, true);
     }
     if (!epi_tma) {
-        mYp = mRhi;
-        mYp2 = mRhi;
+        maps.Yp = maps.R[0];
+        maps.Yp2 = maps.R[0];
     }
     a.epi_tma = epi_tma ? 1 : 0;
     a.ops_off = (uint32_t)ops_off;
     a.body = (uint32_t)body;
-    a.tmem_cols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+    a.tmem_cols = flush ? 512u : BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
     a.cols = s.cols;
     a.sc = s.sc;
     a.P = s.P;
@@ -951,7 +1127,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, k_tc_step, mRhi, mRlo, mYhi, mYlo, mYp, mYp2, a);
+    return cudaLaunchKernelEx(&cfg, k_tc_step, maps, a);
 }
 
 }  // namespace vne

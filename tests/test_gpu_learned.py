@@ -120,9 +120,16 @@ def test_training_reduces_error_on_held_out_spectra():
     X, t = data["features"][:4096], data["target"][:4096]
     loss0, _ = learned.mlp_gradient(theta0, X, t)
     loss1, _ = learned.mlp_gradient(theta, X, t)
-    # the targets carry the probe noise of H_16, which no network predicts:
-    # the loss falls to that floor, the held-out bias below is what shrinks
-    assert loss1 < 0.9 * loss0
+    # The targets carry the probe noise of H_16, which no function of the
+    # spectrum predicts.  Its variance is half the mean squared difference of
+    # two targets of the same spectra drawn with other probe seeds; the
+    # network must remove at least half of the loss above that floor.
+    sub = {k: np.asarray(v)[:4096] for k, v in train_spec.items()}
+    sub2 = dict(sub, seed=(sub["seed"] ^ np.uint64(0x9E3779B97F4A7C15)).astype(np.uint64))
+    t2 = learned.spectral_samples(sub2, s=s)["target"]
+    floor = 0.5 * float(((t - t2).double() ** 2).mean())
+    assert loss1 < loss0
+    assert loss0 - loss1 >= 0.5 * (loss0 - floor), (loss0, loss1, floor)
     for n_lo, n_hi in ((1024, 4096), (8192, 8192)):
         test = learned.spectral_samples(synth.learned_sample_params(1000, 99, n_lo, n_hi), s=s)
         corr = learned.mlp_forward(theta, test["features"]).double()
