@@ -300,16 +300,8 @@ struct TcArgs {
     int64_t n, ldk;
     int S, s;
     int col0, col_end;  // active columns [col0, col_end)
-    int BN, stages, nkb, pieces;
-    int bk;      // K per ring stage: 64 (128-byte swizzle) or 32 (64-byte swizzle)
+    int BN, stages, nkb;
     int gst;     // 1: warps 4 and 5 stage the first G chunk of warps 0 and 1 in smem
-    // 1: chunked accumulation.  The tensor cores' FP32 accumulation truncates
-    // toward zero, a bias that grows with the number of MMAs summed into one
-    // accumulator.  Each ring stage is accumulated afresh in one of two TMEM
-    // buffers (columns [0, BN) and [BN, 2BN)), its small correction products
-    // first, and warps 4-7 add it with round-to-nearest FP32 adds into a
-    // running sum in columns [2BN, 3BN), which the epilogue reads.
-    int flush;
     int ksplit;  // 2: a CTA pair (cluster along z) splits K and swaps half accumulators
     int64_t keep_rows;  // row tiles starting below this load R evict-last (kept in L2)
     int epi_tma;       // 1: Y_{t-1}, Y_{t-2} of the CTA's own chunks arrive by TMA into smem
@@ -330,15 +322,27 @@ struct TcMaps {
     CUtensorMap Yp, Yp2;
 };
 
+// P: bf16 pieces of R and Y (1, 2 or 3), a template parameter so that each
+// precision's issue loop and epilogue are straight-line code.  P < 3 uses BK =
+// 64.  P = 3 uses BK = 32 and chunked accumulation: the tensor cores' FP32
+// accumulation truncates toward zero, a bias that grows with the number of
+// MMAs summed into one accumulator (measured: -8e-6 relative in R Y at
+// n = 8192 with six products into one accumulator).  So each ring stage is
+// accumulated afresh in one of two TMEM buffers (columns [0, BN) and [BN,
+// 2BN)), its small correction products first while the accumulator is small,
+// and warps 4-7 add it with round-to-nearest FP32 adds into a running sum in
+// columns [2BN, 3BN), which the epilogue reads (bias then ~4e-8).
+template <int P>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_step(const __grid_constant__ TcMaps maps, const TcArgs a) {
+    constexpr int BK = P == 3 ? 32 : 64;
+    constexpr bool FLUSH = P == 3;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned carve-out: [stages][A_0 .. A_{P-1} | B_0 .. B_{P-1}] then barriers
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
-    const int P = a.pieces;
-    const uint32_t bytesA = TC_BM * (uint32_t)a.bk * 2;
-    const uint32_t bytesB = (uint32_t)a.BN * (uint32_t)a.bk * 2;
+    const uint32_t bytesA = TC_BM * (uint32_t)BK * 2;
+    const uint32_t bytesB = (uint32_t)a.BN * (uint32_t)BK * 2;
     const uint32_t stage_bytes = (uint32_t)P * (bytesA + bytesB);
     uint8_t* tail = smem + a.body;  // barriers etc. after both the ring and the operand area
     uint64_t* full_bar = reinterpret_cast<uint64_t*>(tail);
@@ -410,8 +414,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint8_t* sA = smem + (size_t)st * stage_bytes;
         const int kb = kb_begin + i;
         mbar_expect_tx(&full_bar[st], stage_bytes);  // whole tiles (A and B) arrive here
+#pragma unroll
         for (int p = 0; p < P; ++p)
-            tma_load_2d_hint(sA + p * bytesA, &maps.R[p], &full_bar[st], kb * a.bk, m0, pol_R);
+            tma_load_2d_hint(sA + p * bytesA, &maps.R[p], &full_bar[st], kb * BK, m0, pol_R);
     };
     // R is written before the steps start and never by a step, so the A tiles
     // of the first ring round are requested before waiting on the previous
@@ -443,8 +448,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 load_A(i);
             }
             uint8_t* sB = smem + (size_t)st * stage_bytes + P * bytesA;
+#pragma unroll
             for (int p = 0; p < P; ++p)
-                tma_load_2d_hint(sB + p * bytesB, &maps.Y[p], &full_bar[st], kb * a.bk, n0, pol_Y);
+                tma_load_2d_hint(sB + p * bytesB, &maps.Y[p], &full_bar[st], kb * BK, n0, pol_Y);
             issued_kb = i + 1;
         }
         if (timed_out) {
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t aA = smem_u32(smem + (size_t)st * stage_bytes);
             const uint32_t aB = aA + (uint32_t)P * bytesA;
-            if (a.flush) {
+            if (FLUSH) {
                 // this stage is one chunk, accumulated afresh in buffer i & 1
                 // once the summing warps have taken its previous contents
                 const int b = i & 1;
@@ -480,29 +486,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t dcol = tmem_base + (uint32_t)(b * a.BN);
                 // the small products first, while the accumulator is small
-                if (a.bk == 32)
-                    issue_stage<3, 2, true>(dcol, aA, bytesA, aB, bytesB, 32, idesc, 0u);
-                else
-                    issue_stage<3, 4, true>(dcol, aA, bytesA, aB, bytesB, 64, idesc, 0u);
+                issue_stage<P, BK / 16, true>(dcol, aA, bytesA, aB, bytesB, BK, idesc, 0u);
                 tc_commit(&accf_bar[b]);
                 tc_commit(&empty_bar[st]);
                 continue;
             }
-            const uint32_t acc0 = i != 0 ? 1u : 0u;
-            if (P == 1)
-                issue_stage<1, 4, false>(tmem_base, aA, bytesA, aB, bytesB, 64, idesc, acc0);
-            else if (P == 2)
-                issue_stage<2, 4, false>(tmem_base, aA, bytesA, aB, bytesB, 64, idesc, acc0);
-            else if (a.bk == 32)
-                issue_stage<3, 2, false>(tmem_base, aA, bytesA, aB, bytesB, 32, idesc, acc0);
-            else
-                issue_stage<3, 4, false>(tmem_base, aA, bytesA, aB, bytesB, 64, idesc, acc0);
+            issue_stage<P, BK / 16, false>(tmem_base, aA, bytesA, aB, bytesB, BK, idesc,
+                                           i != 0 ? 1u : 0u);
             // frees the ring slot once these MMAs finish
             tc_commit(&empty_bar[st]);
         }
         if (timed_out) *abort_flag = 1;
         tc_commit(accum_bar);  // all issued MMAs (possibly none) complete -> arrive
-    } else if (a.flush && warp >= 4 && rank_ok) {
+    } else if (FLUSH && warp >= 4 && rank_ok) {
         // ---------------- chunk sums (flush) ----------------
         // warp 4 + g reads TMEM lanes 32g..32g+31: the rows of lane group g
         const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
@@ -599,11 +595,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (threadIdx.x == 0) mbar_wait(accum_bar, 0u, &never);
     }
     // flush: the summing warps have finished (their TMEM stores are complete)
-    if (a.flush) named_bar_sync(2, TC_THREADS);
+    if (FLUSH) named_bar_sync(2, TC_THREADS);
     bool aborted = (*abort_flag != 0) || !have_acc;
     tc_fence_after();
     __syncwarp();
-    const uint32_t zcol = a.flush ? (uint32_t)(2 * a.BN) : 0u;  // columns holding Z
+    const uint32_t zcol = FLUSH ? (uint32_t)(2 * a.BN) : 0u;  // columns holding Z
 
     // Y_{t-1} and Y_{t-2} of this CTA's own chunks, [chunk][2][32 cols][128 rows]
     // FP32 in smem, by TMA: the operand ring is idle now, and the copies overlap
@@ -702,13 +698,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t o0 = (int64_t)cbase * a.ldk + row;
 #pragma unroll
             for (int k = 0; k < kMaxPieces; ++k)
-                ysh.p[k] = k < a.pieces ? a.Yout.p[k] + o0 : nullptr;
+                ysh.p[k] = k < P ? a.Yout.p[k] + o0 : nullptr;
             if (all_tay)
-                epi_chunk_uniform<0>(r, g, ob, yn, ysh, a.pieces, a.n, a.ldk, fa, finvu, row_ok, v);
+                epi_chunk_uniform<0>(r, g, ob, yn, ysh, P, a.n, a.ldk, fa, finvu, row_ok, v);
             else if (!three_term)
-                epi_chunk_uniform<1>(r, g, ob, yn, ysh, a.pieces, a.n, a.ldk, fa, finvu, row_ok, v);
+                epi_chunk_uniform<1>(r, g, ob, yn, ysh, P, a.n, a.ldk, fa, finvu, row_ok, v);
             else
-                epi_chunk_uniform<2>(r, g, ob, yn, ysh, a.pieces, a.n, a.ldk, fa, finvu, row_ok, v);
+                epi_chunk_uniform<2>(r, g, ob, yn, ysh, P, a.n, a.ldk, fa, finvu, row_ok, v);
         } else {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -728,7 +724,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 y = fmaf(-z, finvu, ypf(q));
             }
             a.Ynew[idx] = y;
-            store_pieces(y, a.Yout, a.pieces, (int64_t)c * a.ldk + row);
+            store_pieces(y, a.Yout, P, (int64_t)c * a.ldk + row);
         }
         }
 #pragma unroll
@@ -1014,7 +1010,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     TcShape sh = choose_shape(ncols, mtiles, (int)(s.ldk / TC_BK), sm_count);
     const int P = s.pieces;
     if (P < 1 || P > kMaxPieces) return cudaErrorInvalidValue;
-    // three pieces: chunked accumulation (TcArgs::flush), which needs three
+    // three pieces: chunked accumulation (k_tc_step<3>), which needs three
     // BN-column TMEM regions (BN <= 128 of the 512 columns) and no K split
     const bool flush = P == 3;
     if (flush && (sh.BN > 128 || sh.ksplit > 1)) {
@@ -1082,10 +1078,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.BN = BN;
     a.stages = stages;
     a.nkb = (int)(s.ldk / bk);
-    a.pieces = P;
-    a.bk = bk;
     a.gst = gst;
-    a.flush = flush ? 1 : 0;
     a.ksplit = sh.ksplit;
     // L2 residency: the rows the power method keeps (same budget; split modes stream every piece)
     a.keep_rows = l2_keep_rows(s.rows_pad, s.ldk * 2 * P);
@@ -1106,12 +1099,13 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.P = s.P;
     a.t = s.t;
 
-    static size_t smem_set = 0;  // raised as needed, never lowered
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    void (*kern)(TcMaps, TcArgs) = P == 1 ? k_tc_step<1> : P == 2 ? k_tc_step<2> : k_tc_step<3>;
+    static size_t smem_set[kMaxPieces + 1] = {0, 0, 0, 0};  // raised as needed, never lowered
+    if (smem > smem_set[P]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        smem_set = smem;
+        smem_set[P] = smem;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)mtiles, (unsigned)sh.ntn, (unsigned)sh.ksplit);
@@ -1127,7 +1121,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, k_tc_step, maps, a);
+    return cudaLaunchKernelEx(&cfg, kern, maps, a);
 }
 
 }  // namespace vne
