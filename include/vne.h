@@ -124,7 +124,15 @@ typedef struct vne_matrix {
  *   u_scale      : c in u = min{1, c * p1~}; the algorithms print c = 6, the
  *                  experiments of Section 6 use c = 1 and c = 6.  0 means 1.
  *   u_override   : > 0 skips the power method and uses this u.
- *   check_trace  : nonzero: reject R with |tr R - 1| > 1e-6 (VNE_ERR_NOT_UNIT_TRACE). */
+ *   check_trace  : nonzero: reject R with |tr R - 1| > 1e-6 (VNE_ERR_NOT_UNIT_TRACE).
+ *   probe_offset : j0 >= 0, the first probe of the call in the seed's stream:
+ *                  the call draws probes j0 .. j0+s-1 (entry (i, j) uses
+ *                  counter (j0+j)*n + i) and its moments_out column j belongs
+ *                  to probe j0+j.  The estimate is a mean of per-probe
+ *                  quadratic forms (Lemma thm:trace), so an s-probe estimate
+ *                  can be split across calls or GPUs by probe range and
+ *                  recombined with vne_combine_moments; the power method does
+ *                  not depend on j0.  0 for a single call. */
 typedef struct vne_params {
     int32_t m;
     int32_t s;
@@ -137,6 +145,7 @@ typedef struct vne_params {
     double u_override;
     int32_t check_trace;
     int32_t reserved;
+    int64_t probe_offset;
 } vne_params;
 
 typedef struct vne_handle vne_handle;
@@ -174,6 +183,24 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
                             double* H_cheb, double* H_taylor,
                             double* moments_cheb, double* moments_taylor,
                             double* u_out, void* stream);
+
+/* The final combination of Algorithms 1b and 1a from per-probe moments:
+ * H_cheb = -(1/s) sum_j sum_k alpha_k mu[k, j] (Lemma lem:prior coefficients
+ * on [0, u]) and H_taylor = ln(1/u) + (1/s) sum_j sum_{k=1}^m tau[k, j] / k,
+ * with the same device kernel and summation order as a single estimator
+ * call.  For an estimate split by probe range (vne_params.probe_offset)
+ * across calls or GPUs: gather the calls' moments_out in probe order, and the
+ * result equals the single call's whenever the per-probe moments do.
+ *   m, s          : degree and total number of probes (>= 1).
+ *   u             : the interval end the moments were taken at (0 < u <= 1).
+ *   moments_cheb  : host, (m+1)*s doubles, row k = moment k of every probe, or NULL.
+ *   moments_taylor: host, the same for Algorithm 1a, or NULL (not both NULL).
+ *   H_cheb, H_taylor: host outputs for the arrays given (the other may be NULL).
+ * Errors: VNE_ERR_INVALID_ARG (sizes, NULLs), VNE_ERR_BAD_INTERVAL (u),
+ * VNE_ERR_NONFINITE.  Synchronises `stream`. */
+vne_status vne_combine_moments(vne_handle* h, int32_t m, int32_t s, double u,
+                               const double* moments_cheb, const double* moments_taylor,
+                               double* H_cheb, double* H_taylor, void* stream);
 
 /* Many density matrices of uneven sizes in one call (Algorithms 1a/1b with
  * alg:power, applied to each).  Rs[i] (DEVICE memory, any layout and dtype a

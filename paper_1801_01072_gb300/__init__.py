@@ -30,7 +30,7 @@ from ._lib import VneError
 
 __all__ = ["entropy_chebyshev", "entropy_taylor", "entropy_both", "lambda_max", "probe_block",
            "entropy_projection", "sketch_block", "ProjectionResult", "entropy_batched", "autotune",
-           "Handle", "Result", "BothResult", "VneError", "suggest_m", "load"]
+           "Handle", "Result", "BothResult", "VneError", "suggest_m", "load", "combine_moments"]
 
 
 def load():
@@ -149,8 +149,10 @@ def _matrix(R, layout: str):
     return mat, R, device
 
 
-def _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace):
+def _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace,
+            probe_offset=0):
     p = _lib.VneParams()
+    p.probe_offset = int(probe_offset)
     p.m = int(m)
     p.s = int(s)
     p.probe = _lib.PROBE[probe]
@@ -177,10 +179,11 @@ def _dptr(a):
 
 
 def _estimate(fn_name, R, m, s, seed, probe, precision, power_iters, power_trials, u_scale,
-              u, check_trace, moments, layout, stream):
+              u, check_trace, moments, layout, stream, probe_offset=0):
     mat, keep, dev = _matrix(R, layout)
     h = _handle(dev)
-    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace)
+    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace,
+                probe_offset)
     H = C.c_double()
     uo = C.c_double()
     mom = np.zeros((m + 1, s), dtype=np.float64) if moments else None
@@ -194,29 +197,36 @@ def _estimate(fn_name, R, m, s, seed, probe, precision, power_iters, power_trial
 def entropy_chebyshev(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
                       precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
                       u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
-                      moments: bool = False, layout: str = "dense", stream=None) -> Result:
-    """Algorithm 1b: -(1/s) sum_j g_j^T f_m(R) g_j (Section 3)."""
+                      moments: bool = False, layout: str = "dense", stream=None,
+                      probe_offset: int = 0) -> Result:
+    """Algorithm 1b: -(1/s) sum_j g_j^T f_m(R) g_j (Section 3).  probe_offset j0:
+    the probes are j0 .. j0+s-1 of the seed's stream."""
     return _estimate("vne_entropy_chebyshev", R, m, s, seed, probe, precision, power_iters,
-                     power_trials, u_scale, u, check_trace, moments, layout, stream)
+                     power_trials, u_scale, u, check_trace, moments, layout, stream,
+                     probe_offset)
 
 
 def entropy_taylor(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
                    precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
                    u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
-                   moments: bool = False, layout: str = "dense", stream=None) -> Result:
+                   moments: bool = False, layout: str = "dense", stream=None,
+                   probe_offset: int = 0) -> Result:
     """Algorithm 1a: ln u^-1 + (1/s) sum_j sum_k g_j^T R (I - R/u)^k g_j / k (Section 2)."""
     return _estimate("vne_entropy_taylor", R, m, s, seed, probe, precision, power_iters,
-                     power_trials, u_scale, u, check_trace, moments, layout, stream)
+                     power_trials, u_scale, u, check_trace, moments, layout, stream,
+                     probe_offset)
 
 
 def entropy_both(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
                  precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
                  u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
-                 moments: bool = False, layout: str = "dense", stream=None) -> BothResult:
+                 moments: bool = False, layout: str = "dense", stream=None,
+                 probe_offset: int = 0) -> BothResult:
     """Algorithms 1a and 1b on the same probes and u, sharing every pass over R."""
     mat, keep, dev = _matrix(R, layout)
     h = _handle(dev)
-    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace)
+    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, check_trace,
+                probe_offset)
     Hc, Ht, uo = C.c_double(), C.c_double(), C.c_double()
     mc = np.zeros((m + 1, s)) if moments else None
     mt = np.zeros((m + 1, s)) if moments else None
@@ -225,6 +235,30 @@ def entropy_both(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
     h.check(st, "vne_entropy_both")
     del keep
     return BothResult(Hc.value, Ht.value, uo.value, mc, mt)
+
+
+def combine_moments(m: int, s: int, u: float, moments_chebyshev=None, moments_taylor=None,
+                    device: int = 0, stream=None):
+    """The final combination of Algorithms 1b / 1a from per-probe moments
+    ((m+1) x s, probe order), on the device with the single call's kernel.
+    Returns (H_chebyshev, H_taylor), None for an estimator not given."""
+    h = _handle(device)
+    arrs = []
+    for mom in (moments_chebyshev, moments_taylor):
+        if mom is None:
+            arrs.append(None)
+            continue
+        a = np.ascontiguousarray(np.asarray(mom, dtype=np.float64))
+        if a.shape != (m + 1, s):
+            raise ValueError(f"moments must be (m+1, s) = {(m + 1, s)}, got {a.shape}")
+        arrs.append(a)
+    Hc, Ht = C.c_double(), C.c_double()
+    st = h.lib.vne_combine_moments(h.h, int(m), int(s), float(u),
+                                   arrs[0].ctypes.data if arrs[0] is not None else None,
+                                   arrs[1].ctypes.data if arrs[1] is not None else None,
+                                   C.byref(Hc), C.byref(Ht), _stream(device, stream))
+    h.check(st, "vne_combine_moments")
+    return (Hc.value if arrs[0] is not None else None, Ht.value if arrs[1] is not None else None)
 
 
 def entropy_batched(Rs, m: int, s: int, seed: int = 0, probe: str = "rademacher",

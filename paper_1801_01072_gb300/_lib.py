@@ -30,7 +30,7 @@ class VneParams(C.Structure):
                 ("precision", C.c_int32), ("seed", C.c_uint64), ("power_iters", C.c_int32),
                 ("power_trials", C.c_int32), ("u_scale", C.c_double),
                 ("u_override", C.c_double), ("check_trace", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("probe_offset", C.c_int64)]
 
 
 class VneError(RuntimeError):
@@ -63,6 +63,8 @@ SIGNATURES = [
     ("vne_tc_autotune", C.c_int,
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), C.c_int32, C.c_void_p, _D, C.c_void_p]),
     ("vne_tc_shape", C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p]),
+    ("vne_combine_moments", C.c_int,
+     [_H, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, _D, _D, C.c_void_p]),
     ("vne_selftest_timeout", C.c_int, [_H, C.c_void_p]),
     ("vne_lambda_max", C.c_int, [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, C.c_void_p]),
     ("vne_lambda_max_static", C.c_int,

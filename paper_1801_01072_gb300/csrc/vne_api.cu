@@ -221,6 +221,10 @@ vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
     }
     if (mode != MODE_POWER) {
         if (p->m < 1 || p->s < 1) return VNE_ERR_INVALID_ARG;
+        // probe counters (j0 + j) n + i, doubled for the Gaussian pairs, stay below 2^63
+        if (p->probe_offset < 0 || p->probe_offset > ((int64_t)1 << 40) ||
+            (double)(p->probe_offset + p->s) * (double)R->n * 2.0 > 9.0e18)
+            return VNE_ERR_INVALID_ARG;
         if (p->m > 100000) return VNE_ERR_INVALID_ARG;
         const int S = (mode == MODE_BOTH) ? 2 * p->s : p->s;
         if (R->layout == VNE_DIA) {
@@ -454,21 +458,22 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             if (f64)
                 c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, 0, 0,
                                                      n, S, s, p->probe, p->seed, P, 256, c.st,
-                                                     R.n));
+                                                     R.n, p->probe_offset));
             else
                 c.launched(launch_dense_init<float>((float*)G, (float*)Yb0, sh[0], pieces, ldk, n, S, s,
                                                     p->probe, p->seed, P, rows_per_tile0, c.st,
-                                                    R.n));
+                                                    R.n, p->probe_offset));
         } else {
             const int Wd = (s + 63) / 64;
             if (f64)
                 c.launched(launch_dia_init<double>((double*)G, bits, Wd,
                                                    bits ? nullptr : (double*)Yb0, n, S, s,
-                                                   p->probe, p->seed, P, rows_per_tile0, c.st));
+                                                   p->probe, p->seed, P, rows_per_tile0, c.st,
+                                                   p->probe_offset));
             else
                 c.launched(launch_dia_init<float>((float*)G, bits, Wd, bits ? nullptr : (float*)Yb0,
                                                   n, S, s, p->probe, p->seed, P, rows_per_tile0,
-                                                  c.st));
+                                                  c.st, p->probe_offset));
         }
         void* Yb[3] = {Yb0, Yb1, Yb2};
         // tensor-core steps are timed as one span (consecutive launches overlap
@@ -1151,6 +1156,52 @@ vne_status vne_lambda_max(vne_handle* h, const vne_matrix* R, const vne_params* 
     Outputs o;
     o.lam = lam_out;
     return run(h, R, p, MODE_POWER, o, stream);
+}
+
+vne_status vne_combine_moments(vne_handle* h, int32_t m, int32_t s, double u,
+                               const double* moments_cheb, const double* moments_taylor,
+                               double* H_cheb, double* H_taylor, void* stream) {
+    if (!h || m < 1 || s < 1 || m > 100000) return VNE_ERR_INVALID_ARG;
+    if (!moments_cheb && !moments_taylor) return VNE_ERR_INVALID_ARG;
+    if ((moments_cheb && !H_cheb) || (moments_taylor && !H_taylor)) return VNE_ERR_INVALID_ARG;
+    if ((int64_t)(m + 1) * s > ((int64_t)1 << 31)) return VNE_ERR_INVALID_ARG;
+    if (!(u > 0.0) || !(u <= 1.0)) return VNE_ERR_BAD_INTERVAL;
+    DeviceGuard guard(h->device);
+    const size_t per = (size_t)(m + 1) * s;
+    Bump b0(nullptr);
+    b0.take<double>(SC_COUNT);
+    b0.take<double>(per);
+    b0.take<double>(per);
+    vne_status vs = ensure_ws(h, b0.off + 4096);
+    if (vs != VNE_OK) return vs;
+    Bump b1(h->ws);
+    double* sc = b1.take<double>(SC_COUNT);
+    double* mc = b1.take<double>(per);
+    double* mt = b1.take<double>(per);
+    Call c{h, (cudaStream_t)stream};
+    c.chk(cudaMemsetAsync(sc, 0, SC_COUNT * sizeof(double), c.st));
+    if (moments_cheb)
+        c.chk(cudaMemcpyAsync(mc, moments_cheb, per * sizeof(double), cudaMemcpyHostToDevice, c.st));
+    if (moments_taylor)
+        c.chk(cudaMemcpyAsync(mt, moments_taylor, per * sizeof(double), cudaMemcpyHostToDevice,
+                              c.st));
+    if (c.ok()) c.launched(launch_set_u(sc, u, c.st));
+    if (c.ok())
+        c.launched(launch_combine_final(s, m, moments_cheb ? mc : nullptr,
+                                        moments_taylor ? mt : nullptr, sc, c.st));
+    if (c.ok())
+        c.chk(cudaMemcpyAsync(h->host_sc, sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                              c.st));
+    c.chk(cudaStreamSynchronize(c.st));
+    if (!c.ok()) {
+        cudaGetLastError();
+        return map_err(h, c.err);
+    }
+    const vne_status fs = slot_status(h->host_sc, 0);
+    if (fs != VNE_OK) return fs;
+    if (moments_cheb) *H_cheb = h->host_sc[SC_H_CHEB];
+    if (moments_taylor) *H_taylor = h->host_sc[SC_H_TAYLOR];
+    return VNE_OK;
 }
 
 vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k, int32_t s,

@@ -76,6 +76,13 @@ __global__ void k_combine_final(int s, int m, int cheb, int taylor, const double
     }
 }
 
+cudaError_t launch_combine_final(int s, int m, const double* mom_cheb, const double* mom_taylor,
+                                 double* sc, cudaStream_t st) {
+    k_combine_final<<<1, 256, 0, st>>>(s, m, mom_cheb != nullptr, mom_taylor != nullptr, mom_cheb,
+                                       mom_taylor, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine(Partials P, int s, int m, int cheb_c0, int tay_c0, double* mom_cheb,
                            double* mom_taylor, double* sc, cudaStream_t st) {
     const int per = (m + 1) * s;

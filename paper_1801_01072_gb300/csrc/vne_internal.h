@@ -40,15 +40,17 @@ cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint
 // (the lower half of the probes [g; 0] of a Hermitian embedding).
 // Ysh[k], k < pieces (pieces 0: none): the bf16 pieces of Y0 (see launch_tc_step).
 template <typename T>
+// Probe j of the call is probe j0 + j of the seed's stream.
 cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                              int rows_per_tile, cudaStream_t st, int64_t probe_n);
+                              int rows_per_tile, cudaStream_t st, int64_t probe_n, int64_t j0);
 // Banded layout [row][column] (row stride S).  Rademacher probes are packed
 // as bits (bit j%64 of word j/64 of row i set when g_j[i] = -1; W words per
 // row); Gaussian probes are stored as values G[i*s + j].
 template <typename T>
 cudaError_t launch_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
-                            uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st);
+                            uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st,
+                            int64_t j0);
 
 // ---- conversions / checks (vne_prep.cu) --------------------------------------
 cudaError_t launch_dense_convert_f64(const void* src, int src_dtype, int64_t n, int64_t ld,
@@ -206,5 +208,9 @@ cudaError_t launch_wait_never(double* sc, cudaStream_t st);
 // the FP64 estimates into sc.
 cudaError_t launch_combine(Partials P, int s, int m, int cheb_c0, int tay_c0, double* mom_cheb,
                            double* mom_taylor, double* sc, cudaStream_t st);
+// Only the final stage: the estimates from per-probe moments already in
+// mom_cheb / mom_taylor (either may be NULL) and u in sc.
+cudaError_t launch_combine_final(int s, int m, const double* mom_cheb, const double* mom_taylor,
+                                 double* sc, cudaStream_t st);
 
 }  // namespace vne

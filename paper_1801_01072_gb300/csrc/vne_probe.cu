@@ -35,14 +35,15 @@ struct Pieces {
 };
 template <typename T>
 __global__ void k_dense_init(T* G, T* Y0, Pieces Ysh, int pieces, int64_t ldk, int64_t n, int S,
-                             int s, int kind, uint64_t seed, Partials P, int64_t probe_n) {
+                             int s, int kind, uint64_t seed, Partials P, int64_t probe_n,
+                             int64_t j0) {
     __shared__ double sh[32];
     const int j = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double g = 0.0;
     if (i < n) {
         if (i < probe_n) {
-            const uint64_t e = (uint64_t)j * (uint64_t)probe_n + (uint64_t)i;
+            const uint64_t e = (uint64_t)(j0 + j) * (uint64_t)probe_n + (uint64_t)i;
             if (sizeof(T) == 4 && kind == 1) g = (double)gaussian_f32(seed, e);
             else g = probe_value(kind, seed, e);
         }
@@ -72,7 +73,7 @@ __global__ void k_dense_init(T* G, T* Y0, Pieces Ysh, int pieces, int64_t ldk, i
 template <typename T>
 cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                              int rows_per_tile, cudaStream_t st, int64_t probe_n) {
+                              int rows_per_tile, cudaStream_t st, int64_t probe_n, int64_t j0) {
     if (pieces < 0 || pieces > kMaxPieces || (pieces > 0 && !Ysh)) return cudaErrorInvalidValue;
     Pieces ps{};
     for (int k = 0; k < pieces; ++k) {
@@ -81,21 +82,21 @@ cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces
     }
     dim3 grid((unsigned)((n + rows_per_tile - 1) / rows_per_tile), (unsigned)s);
     k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, ps, pieces, ldk, n, S, s, kind, seed, P,
-                                                    probe_n);
+                                                    probe_n, j0);
     return cudaGetLastError();
 }
 template cudaError_t launch_dense_init<double>(double*, double*, __nv_bfloat16* const*, int,
                                                int64_t, int64_t, int, int, int, uint64_t, Partials,
-                                               int, cudaStream_t, int64_t);
+                                               int, cudaStream_t, int64_t, int64_t);
 template cudaError_t launch_dense_init<float>(float*, float*, __nv_bfloat16* const*, int,
                                               int64_t, int64_t, int, int, int, uint64_t, Partials,
-                                              int, cudaStream_t, int64_t);
+                                              int, cudaStream_t, int64_t, int64_t);
 
 // Banded layout: a block of 8 warps owns a tile of rows_per_tile rows; each
 // warp walks rows w, w+8, ... of the tile and lane l covers probes l, l+32, ...
 template <typename T>
 __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
-                           uint64_t seed, Partials P, int rows_per_tile) {
+                           uint64_t seed, Partials P, int rows_per_tile, int64_t j0) {
     __shared__ double sh[8][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nchunk = (s + 31) >> 5;  // <= 8
@@ -115,7 +116,7 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
                 // Rademacher signs straight from the hash bit (no FP64 on this path)
                 T gt = (T)0;
                 if (j < s) {
-                    const uint64_t e = (uint64_t)j * (uint64_t)n + (uint64_t)i;
+                    const uint64_t e = (uint64_t)(j0 + j) * (uint64_t)n + (uint64_t)i;
                     if (kind == 0) gt = (splitmix_out(seed, e) >> 63) ? (T)-1 : (T)1;
                     else gt = (T)gaussian(seed, e);
                 }
@@ -146,15 +147,16 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
 
 template <typename T>
 cudaError_t launch_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
-                            uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st) {
+                            uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st,
+                            int64_t j0) {
     if (s > 256 || W > 4) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)((n + rows_per_tile - 1) / rows_per_tile);
-    k_dia_init<T><<<grid, 256, 0, st>>>(G, bits, W, Y0, n, S, s, kind, seed, P, rows_per_tile);
+    k_dia_init<T><<<grid, 256, 0, st>>>(G, bits, W, Y0, n, S, s, kind, seed, P, rows_per_tile, j0);
     return cudaGetLastError();
 }
 template cudaError_t launch_dia_init<double>(double*, uint64_t*, int, double*, int64_t, int, int,
-                                             int, uint64_t, Partials, int, cudaStream_t);
+                                             int, uint64_t, Partials, int, cudaStream_t, int64_t);
 template cudaError_t launch_dia_init<float>(float*, uint64_t*, int, float*, int64_t, int, int, int,
-                                            uint64_t, Partials, int, cudaStream_t);
+                                            uint64_t, Partials, int, cudaStream_t, int64_t);
 
 }  // namespace vne
