@@ -196,6 +196,22 @@ vne_status slot_status(const double* hs, int check_trace) {
     return VNE_OK;
 }
 
+// The persistent power method needs cooperative launches (every CTA resident).
+bool power_sym_enabled(const vne_handle* h) {
+    static int env = -1;
+    if (env < 0) {
+        const char* e = getenv("VNE_POWER_SYM");
+        env = (e && e[0] == '0') ? 0 : 1;
+    }
+    if (!env) return false;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return coop != 0;
+}
+
 vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
     if (!R || !p) return VNE_ERR_INVALID_ARG;
     if (R->n < 1 || !R->data) return VNE_ERR_INVALID_ARG;
@@ -305,6 +321,11 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     else if (pieces == 1) pw_rdt = 2;
     else pw_rdt = (!cplx && R.dtype == VNE_F64) ? 0 : 1;
     const int pw_xdouble = dense ? (pw_rdt == 0 ? 1 : 0) : (f64 ? 1 : 0);
+    // bf16 R, one trial, a single call: every product in one persistent
+    // launch over the upper triangle (VNE_POWER_SYM=0: one launch per product)
+    const bool use_sym = do_power && dense && pw_rdt == 2 && q == 1 && n >= 2048 && !out.ws &&
+                         !out.measure && power_sym_fits(rows_pad, h->sm_count) &&
+                         power_sym_enabled(h);
 
     // ---- workspace plan (two passes) ----
     const size_t vt = f64 ? 8 : 4;  // master / operand element size of SIMT & DIA paths
@@ -312,7 +333,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
                     double** sc, double** ppart, unsigned int** counter, void** x0, void** x1,
                     void** G, uint64_t** bits, void** Yb0, void** Yb1, void** Yb2, void** Zpart,
                     __nv_bfloat16** Sh, double** part, double** mom_c, double** mom_t,
-                    float** mws) {
+                    float** mws, void** symws) {
         *sc = b.take<double>(SC_COUNT);
         *mws = out.mlp ? b.take<float>(64 + mlp_workspace_floats(1)) : nullptr;
         *counter = b.take<unsigned int>(64);
@@ -334,6 +355,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         const size_t xs = pw_xdouble ? 8 : 4;
         *x0 = b.take<char>((size_t)n * q * xs);
         *x1 = b.take<char>((size_t)n * q * xs);
+        *symws = use_sym ? b.take<char>((size_t)power_sym_scratch_bytes(rows_pad)) : nullptr;
         *G = *Yb0 = *Yb1 = *Yb2 = *Zpart = nullptr;
         *bits = nullptr;
         *Sh = nullptr;
@@ -353,7 +375,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         *mom_c = b.take<double>((size_t)(m + 1) * s);
         *mom_t = b.take<double>((size_t)(m + 1) * s);
     };
-    void *Rcopy, *Rop, *x0, *x1, *G, *Yb0, *Yb1, *Yb2, *Zpart;
+    void *Rcopy, *Rop, *x0, *x1, *G, *Yb0, *Yb1, *Yb2, *Zpart, *symws;
     __nv_bfloat16 *Rpc[kMaxPieces], *Sh;
     double *sc, *ppart, *part, *mom_c, *mom_t;
     float* mws;
@@ -362,7 +384,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     {
         Bump b0(nullptr);
         plan(b0, &Rcopy, &Rop, Rpc, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
-             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
+             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws, &symws);
         if (out.measure) {
             *out.measured = b0.off + 4096;
             return VNE_OK;
@@ -375,7 +397,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         }
         Bump b1(base);
         plan(b1, &Rcopy, &Rop, Rpc, &sc, &ppart, &counter, &x0, &x1, &G, &bits, &Yb0, &Yb1,
-             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws);
+             &Yb2, &Zpart, &Sh, &part, &mom_c, &mom_t, &mws, &symws);
     }
     h->ev_used = 0;
     h->pending.clear();
@@ -427,7 +449,11 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         // the products are timed as one span: an event between two of them
         // would stop the next one from starting early (programmatic launch)
         c.prof_begin();
-        for (int it = 0; it <= p->power_iters && c.ok(); ++it) {
+        if (use_sym) {
+            c.launched(launch_power_sym(Rpc[0], n, rows_pad, ldk, (const float*)x0, p->power_iters,
+                                        sc, symws, u_scale, h->sm_count, c.st));
+        }
+        for (int it = 0; it <= p->power_iters && c.ok() && !use_sym; ++it) {
             const int fin = it == p->power_iters;
             if (dense)
                 c.launched(launch_power_step_dense(Rp, pw_rdt, n, ldp, xa, xb, pw_xdouble, q, sc,

@@ -429,6 +429,409 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
     power_finish<float>(acc, 1, partial, counter, sc, final_step, u_scale);
 }
 
+// ---------------------------------------------------------------------------
+// All t+1 products of the power method in one persistent launch (bf16 R, one
+// trial), reading only the upper triangle of the symmetric R.
+//
+// The products y = R x_hat differ only in x, and each launch of the per-
+// product kernels above pays a fixed ramp and tail (measured ~13-16 us per
+// product at n = 5792 and 8192, whether R came from L2 or HBM).  Here one
+// cooperative launch runs every product: R is cut into 128 x 128 tiles (I, K)
+// with I <= K, which the CTAs take round-robin; tile (I, K) adds R_IK x_K to
+// y_I (row part) and, off the diagonal, R_IK^T x_I to y_K (column part, by
+// symmetry R_KI = R_IK^T).  The upper triangle is half of R (67 MB of bf16 at
+// n = 8192, which fits in L2 with an evict-last hint), and the TMA ring runs
+// on across products, since R does not change.  A product is:
+//   x_hat into shared memory (the whole vector, scaled by 1/||x||);
+//   the CTA's tiles, each writing its two partial vectors;
+//   grid barrier; CTA c sums blocks c, c+G, ... from their nb partials in a
+//   fixed order (deterministic) and writes y_b and the block's y.y (and,
+//   after the last product, x_hat.y and x_hat.x_hat) in FP64;
+//   grid barrier; every CTA forms 1/||y|| from the block sums.
+// Every wait is bounded (kWaitNs): on expiry the CTA sets FLAG_TIMEOUT, waits
+// (bounded) for its copies in flight and returns.
+// ---------------------------------------------------------------------------
+constexpr int kSymT = 128;                        // tile edge
+constexpr int kSymMaxStages = 4;                  // ring depth (deeper measured no faster)
+constexpr int kSymThreads = 256;                  // 8 warps, 16 tile rows each (16 warps: slower)
+constexpr int kSymWarps = kSymThreads / 32;
+constexpr uint32_t kSymTileBytes = kSymT * kSymT * 2;
+constexpr int kSymMaxTiles = 512;                 // tiles per CTA (tile list in smem)
+constexpr int64_t kSymMaxRows = 16384;            // x_hat in shared memory (64 KB)
+
+struct SymArgs {
+    int64_t n;
+    int nb;          // 128-row blocks of the padded matrix
+    int ntile;       // nb (nb + 1) / 2
+    int t;           // products 0..t (the last one gives the Rayleigh quotient)
+    int stages;      // ring depth (<= kSymMaxStages)
+    const float* x0; // start vector, n entries
+    float* ybuf;     // 2 x nb*128 iterates, by product parity
+    float* part;     // ntile x 2 x 128 partial vectors (row part, column part)
+    unsigned* bar;   // grid barrier counter (zero at launch)
+    double* normb;   // nb x 3 block sums (y.y, x_hat.y, x_hat.x_hat)
+    double* sc;
+    double u_scale;
+};
+
+__device__ __forceinline__ int sym_row_start(int I, int nb) { return I * nb - (I * (I - 1)) / 2; }
+
+__device__ __forceinline__ void sym_tma_tile(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                             int x, int y, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier (all CTAs resident: cooperative launch); false on
+// timeout, with flag_sh set.
+__device__ __forceinline__ bool sym_grid_sync(unsigned* bar, unsigned want, int* flag_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const uint64_t t0 = globaltimer();
+        for (uint32_t it = 0;; ++it) {
+            if (ld_acquire_u32(bar) >= want) break;
+            if ((it & 63u) == 63u && globaltimer() - t0 > kWaitNs) {
+                *flag_sh = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    return *flag_sh == 0;
+}
+
+// sum over the CTA of one value per thread, fixed order (result in every thread)
+__device__ __forceinline__ double sym_block_sum(double v, double* red) {
+    v = block_sum(v, red);  // valid in thread 0
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = v;
+    __syncthreads();
+    v = red[0];
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_constant__ CUtensorMap mapR,
+                                                      const SymArgs a) {
+    extern __shared__ __align__(1024) uint8_t sraw[];
+    uint8_t* ring = sraw + ((1024u - (smem_u32(sraw) & 1023u)) & 1023u);
+    const int NS = a.stages;
+    float* xsm = reinterpret_cast<float*>(ring + (size_t)NS * kSymTileBytes);  // nb*128
+    __shared__ uint64_t full[kSymMaxStages];
+    __shared__ float colsm[2][kSymWarps][kSymT];  // per-warp column partials (two tiles); group sums
+    __shared__ int flag_sh;
+    __shared__ double red_sh[kSymWarps];
+    __shared__ uint32_t tl[kSymMaxTiles];  // this CTA's tiles: (I << 16) | K
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int nb = a.nb;
+    const int rows = nb * kSymT;
+    const int mine = c < a.ntile ? (a.ntile - c + G - 1) / G : 0;
+    for (int j = tid; j < mine; j += blockDim.x) {
+        const int tau = c + j * G;
+        int lo = 0, hi = nb - 1;  // the row I whose tiles hold tau
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sym_row_start(mid, nb) <= tau) lo = mid;
+            else hi = mid - 1;
+        }
+        tl[j] = ((uint32_t)lo << 16) | (uint32_t)(lo + (tau - sym_row_start(lo, nb)));
+    }
+    if (tid == 0) {
+        for (int st = 0; st < NS; ++st) mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapR)) : "memory");
+        flag_sh = 0;
+    }
+    __syncthreads();
+    const int total = (a.t + 1) * mine;
+    uint64_t pol = 0;
+    if (tid == 0) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    auto issue = [&](int item) {
+        const int st = item % NS;
+        const uint32_t tk = tl[item % mine];
+        mbar_expect_tx(&full[st], kSymTileBytes);
+        sym_tma_tile(ring + (size_t)st * kSymTileBytes, &mapR, &full[st],
+                     (int)(tk & 0xFFFFu) * kSymT, (int)(tk >> 16) * kSymT, pol);
+    };
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < NS && issued < total; ++issued) issue(issued);
+
+    float inv = (float)(1.0 / sqrt((double)a.n));  // ||x_0||^2 = n
+    bool ok = true;
+    int consumed = 0;
+    for (int p = 0; p <= a.t && ok; ++p) {
+        const float* xsrc = p == 0 ? a.x0 : a.ybuf + (size_t)((p - 1) & 1) * rows;
+        float* ydst = a.ybuf + (size_t)(p & 1) * rows;
+        // x_hat of this product, whole vector, in shared memory
+        if (p == 0) {
+            for (int i = tid; i < rows; i += blockDim.x) xsm[i] = i < a.n ? a.x0[i] * inv : 0.f;
+        } else {
+            const float4* s4 = reinterpret_cast<const float4*>(xsrc);
+            float4* d4 = reinterpret_cast<float4*>(xsm);
+            for (int i = tid; i < rows / 4; i += blockDim.x) {
+                float4 v = __ldcg(s4 + i);
+                v.x *= inv; v.y *= inv; v.z *= inv; v.w *= inv;
+                d4[i] = v;
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < mine; ++j) {
+            const int item = p * mine + j;
+            const int st = item % NS;
+            const uint32_t tk = tl[j];
+            const int I = (int)(tk >> 16), K = (int)(tk & 0xFFFFu);
+            if (!mbar_wait(&full[st], (uint32_t)(item / NS) & 1u, &flag_sh)) flag_sh = 1;
+            const __nv_bfloat16* tile =
+                reinterpret_cast<const __nv_bfloat16*>(ring + (size_t)st * kSymTileBytes);
+            const float4 xk = *reinterpret_cast<const float4*>(xsm + K * kSymT + 4 * lane);
+            const float* xi_row = xsm + I * kSymT + 16 * w;
+            float rp[16];
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int row = 16 * w + r;
+                const uint2 raw = *reinterpret_cast<const uint2*>(tile + row * kSymT + 4 * lane);
+                const float2 f01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+                const float2 f23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+                float v = f01.x * xk.x;
+                v = fmaf(f01.y, xk.y, v);
+                v = fmaf(f23.x, xk.z, v);
+                rp[r] = fmaf(f23.y, xk.w, v);
+                const float xi = xi_row[r];
+                c0 = fmaf(f01.x, xi, c0);
+                c1 = fmaf(f01.y, xi, c1);
+                c2 = fmaf(f23.x, xi, c2);
+                c3 = fmaf(f23.y, xi, c3);
+            }
+            // row sums over the 32 lanes: fold lane bit 4, then a transpose-
+            // reduce over bits 3..0, after which lane l holds row 16w + (l & 15)
+#pragma unroll
+            for (int r = 0; r < 16; ++r) rp[r] += __shfl_xor_sync(0xffffffffu, rp[r], 16);
+#pragma unroll
+            for (int o = 8; o >= 1; o >>= 1) {
+                const bool upper = (lane & o) != 0;
+#pragma unroll
+                for (int k = 0; k < o; ++k) {
+                    const float send = upper ? rp[k] : rp[k + o];
+                    const float keep = upper ? rp[k + o] : rp[k];
+                    rp[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            const bool diag = I == K;
+            // column partials of this tile in colsm[j & 1]: the tile after the
+            // next writes that buffer again only after its own barrier below,
+            // which every thread passes after this tile's sums
+            float (*cs)[kSymT] = colsm[j & 1];
+            if (!diag) *reinterpret_cast<float4*>(&cs[w][4 * lane]) = make_float4(c0, c1, c2, c3);
+            __syncthreads();  // stage st read by every warp; column partials in smem
+            if (flag_sh) {  // a wait gave up (uniform after the barrier)
+                ok = false;
+                break;
+            }
+            ++consumed;
+            if (tid == 0 && issued < total) issue(issued++);
+            float* pr = a.part + (size_t)(c + j * G) * 2 * kSymT;
+            if (lane < 16) pr[16 * w + lane] = rp[0];
+            if (!diag && tid < kSymT) {
+                float sum = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < kSymWarps; ++ww) sum += cs[ww][tid];
+                pr[kSymT + tid] = sum;
+            }
+        }
+        if (!ok) break;
+        // every partial of product p is written
+        if (!sym_grid_sync(a.bar, (unsigned)(2 * p + 1) * (unsigned)G, &flag_sh)) {
+            ok = false;
+            break;
+        }
+        // blocks b = c, c + G, ...: the nb contributions (row parts of tiles
+        // (b, b..nb-1), then column parts of tiles (0..b-1, b)); group g (warp
+        // g) sums contributions g, g+8, ... with float4 loads, then the eight
+        // group sums are added in group order
+        for (int b = c; b < nb; b += G) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e0 = w; e0 < nb; e0 += 8 * kSymWarps) {
+                float4 v[8];  // eight loads in flight, summed in order e0, e0 + 16, ...
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = e0 + kSymWarps * u;
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < nb) {
+                        const float* src = e < nb - b
+                            ? a.part + (size_t)(sym_row_start(b, nb) + e) * 2 * kSymT
+                            : a.part + (size_t)(sym_row_start(e - (nb - b), nb) + (nb - e)) * 2 * kSymT +
+                                  kSymT;
+                        v[u] = __ldcg(reinterpret_cast<const float4*>(src) + lane);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    acc.x += v[u].x; acc.y += v[u].y; acc.z += v[u].z; acc.w += v[u].w;
+                }
+            }
+            *reinterpret_cast<float4*>(&colsm[0][w][4 * lane]) = acc;
+            __syncthreads();
+            double yy = 0.0, xy = 0.0, xx = 0.0;
+            if (tid < kSymT) {
+                float v = 0.f;
+#pragma unroll
+                for (int g = 0; g < kSymWarps; ++g) v += colsm[0][g][tid];
+                const int gi = b * kSymT + tid;
+                ydst[gi] = v;
+                yy = (double)v * (double)v;
+                const double xh = (double)xsm[gi];
+                xy = xh * (double)v;
+                xx = xh * xh;
+            }
+            yy = sym_block_sum(yy, red_sh);
+            if (p == a.t) {
+                xy = sym_block_sum(xy, red_sh);
+                xx = sym_block_sum(xx, red_sh);
+            }
+            if (tid == 0) {
+                a.normb[(size_t)b * 3 + 0] = yy;
+                a.normb[(size_t)b * 3 + 1] = xy;
+                a.normb[(size_t)b * 3 + 2] = xx;
+            }
+            __syncthreads();  // colsm reused
+        }
+        // every block of product p is final
+        if (!sym_grid_sync(a.bar, (unsigned)(2 * p + 2) * (unsigned)G, &flag_sh)) {
+            ok = false;
+            break;
+        }
+        if (p < a.t) {
+            double part = 0.0;  // ||y||^2 from the block sums (fixed order)
+            for (int b = tid; b < nb; b += blockDim.x) part += __ldcg(a.normb + (size_t)b * 3);
+            inv = (float)(1.0 / sqrt(sym_block_sum(part, red_sh)));
+        }
+    }
+    if (!ok) {
+        // drain: the copies issued and not consumed, each on its own stage
+        if (tid == 0) {
+            volatile int never = 0;
+            for (int item = consumed; item < issued; ++item)
+                mbar_wait(&full[item % NS], (uint32_t)(item / NS) & 1u, &never);
+            atomicOr(reinterpret_cast<unsigned long long*>(&a.sc[SC_FLAGS]),
+                     (unsigned long long)FLAG_TIMEOUT);
+        }
+        return;
+    }
+    if (c == 0) {
+        // Rayleigh quotient of the last iterate (Algorithm alg:power)
+        double yy = 0.0, xy = 0.0, xx = 0.0;
+        for (int b = tid; b < nb; b += blockDim.x) {
+            yy += __ldcg(a.normb + (size_t)b * 3 + 0);
+            xy += __ldcg(a.normb + (size_t)b * 3 + 1);
+            xx += __ldcg(a.normb + (size_t)b * 3 + 2);
+        }
+        yy = sym_block_sum(yy, red_sh);
+        xy = sym_block_sum(xy, red_sh);
+        xx = sym_block_sum(xx, red_sh);
+        if (tid == 0) {
+            a.sc[SC_NORM + 0] = yy;
+            a.sc[SC_NORM + 1] = xy;
+            a.sc[SC_NORM + 2] = xx;
+            const double lam = xy / xx;
+            const double u = fmin(1.0, a.u_scale * lam);
+            a.sc[SC_LAM] = lam;
+            a.sc[SC_U] = u;
+            if (!isfinite(lam) || !(u > 0.0) || !isfinite(u))
+                *reinterpret_cast<unsigned long long*>(&a.sc[SC_FLAGS]) |= FLAG_BAD_INTERVAL;
+        }
+    }
+}
+
+int64_t power_sym_scratch_bytes(int64_t rows_pad) {
+    const int64_t nb = rows_pad / kSymT;
+    const int64_t ntile = nb * (nb + 1) / 2;
+    return ntile * 2 * kSymT * 4 + 2 * rows_pad * 4 + nb * 3 * 8 + 4 * 256;
+}
+
+bool power_sym_fits(int64_t rows_pad, int sm_count) {
+    if (rows_pad % kSymT != 0 || rows_pad > kSymMaxRows || sm_count < 1) return false;
+    const int64_t nb = rows_pad / kSymT, ntile = nb * (nb + 1) / 2;
+    const int64_t G = ntile < sm_count ? ntile : sm_count;
+    return (ntile + G - 1) / G <= kSymMaxTiles;
+}
+
+cudaError_t launch_power_sym(const __nv_bfloat16* R, int64_t n, int64_t rows_pad, int64_t ldk,
+                             const float* x0, int t, double* sc, void* scratch,
+                             double u_scale, int sm_count, cudaStream_t st) {
+    if (!power_sym_fits(rows_pad, sm_count) || (ldk % 8) != 0 || t < 0)
+        return cudaErrorInvalidValue;
+    const int nb = (int)(rows_pad / kSymT);
+    const int ntile = nb * (nb + 1) / 2;
+    const int G = ntile < sm_count ? ntile : sm_count;
+    alignas(64) CUtensorMap map;
+    if (!tma_map_bf16_plain(&map, R, ldk, rows_pad, ldk, kSymT, kSymT)) return cudaErrorInvalidValue;
+    char* p = static_cast<char*>(scratch);
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    SymArgs a;
+    a.n = n;
+    a.nb = nb;
+    a.ntile = ntile;
+    a.t = t;
+    a.x0 = x0;
+    a.part = reinterpret_cast<float*>(take((size_t)ntile * 2 * kSymT * 4));
+    a.ybuf = reinterpret_cast<float*>(take((size_t)2 * rows_pad * 4));
+    a.bar = reinterpret_cast<unsigned*>(take(256));
+    a.normb = reinterpret_cast<double*>(take((size_t)nb * 3 * 8));
+    a.sc = sc;
+    a.u_scale = u_scale;
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    static int static_smem = -1;
+    if (static_smem < 0) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_power_sym);
+        if (e != cudaSuccess) return e;
+        static_smem = (int)fa.sharedSizeBytes;
+    }
+    const int64_t room = 227 * 1024 - 1024 - static_smem - rows_pad * 4;
+    int stages = (int)(room / kSymTileBytes);
+    if (stages > kSymMaxStages) stages = kSymMaxStages;
+    if (stages < 2) return cudaErrorInvalidValue;
+    a.stages = stages;
+    const size_t smem = 1024 + (size_t)stages * kSymTileBytes + (size_t)rows_pad * 4;
+    static size_t attr = 0;
+    if (smem > attr) {
+        e = cudaFuncSetAttribute(k_power_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(kSymThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barrier needs it
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_power_sym, map, a);
+}
+
 cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_t ld,
                                     const void* x, void* y, int xdouble, int q, double* sc,
                                     double* partial, unsigned int* counter, int final_step,

@@ -831,20 +831,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows,
-                     int64_t row_stride_elems, int box_inner, int box_rows, bool fp32 = false) {
+                     int64_t row_stride_elems, int box_inner, int box_rows, bool fp32 = false,
+                     bool no_swizzle = false) {
     // small cache: consecutive steps reuse the same few operand buffers
     struct Entry {
         const void* base;
         int64_t inner, rows, stride;
         int bi, br;
-        bool fp32;
+        bool fp32, nosw;
         CUtensorMap map;
     };
     static Entry cache[16];
     static int next = 0;
     for (const Entry& e : cache)
         if (e.base == base && e.inner == inner && e.rows == rows && e.stride == row_stride_elems &&
-            e.bi == box_inner && e.br == box_rows && e.fp32 == fp32) {
+            e.bi == box_inner && e.br == box_rows && e.fp32 == fp32 && e.nosw == no_swizzle) {
             *map = e.map;
             return true;
         }
@@ -855,11 +856,11 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t 
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     // bf16 operand tiles: the swizzle matches the row length (box_inner * 2 bytes)
-    const CUtensorMapSwizzle sw = fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE
+    const CUtensorMapSwizzle sw = (fp32 || no_swizzle) ? CU_TENSOR_MAP_SWIZZLE_NONE
                                   : box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                   : box_inner * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                          : CU_TENSOR_MAP_SWIZZLE_NONE;
-    if (!fp32 && sw == CU_TENSOR_MAP_SWIZZLE_NONE) return false;
+    if (!fp32 && !no_swizzle && sw == CU_TENSOR_MAP_SWIZZLE_NONE) return false;
     CUresult r = enc(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                      2, const_cast<void*>(base), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
@@ -867,8 +868,14 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t 
     if (r != CUDA_SUCCESS) return false;
     Entry& e = cache[next];
     next = (next + 1) % 16;
-    e = Entry{base, inner, rows, row_stride_elems, box_inner, box_rows, fp32, *map};
+    e = Entry{base, inner, rows, row_stride_elems, box_inner, box_rows, fp32, no_swizzle, *map};
     return true;
+}
+
+bool tma_map_bf16_plain(void* map_out, const void* base, int64_t inner, int64_t rows,
+                        int64_t row_stride_elems, int box_inner, int box_rows) {
+    return make_map(static_cast<CUtensorMap*>(map_out), base, inner, rows, row_stride_elems,
+                    box_inner, box_rows, false, true);
 }
 
 // Tile shape of one step.  BN: probe columns per CTA (multiple of 32, <= 256);

@@ -309,3 +309,22 @@ def test_bounded_wait_times_out_and_context_survives():
     R, p, _ = synth.dense_exp(64, 10.0, seed=1)
     res = vne.entropy_chebyshev(dev(R), 6, 4, seed=1, precision="f64")
     assert np.isfinite(res.H)
+
+
+def _bf16_round(a):
+    """Round to bf16 (through FP32, round-to-nearest-even), as the library's
+    conversion of R does; returns FP64."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [2048, 2049, 4100])
+def test_power_method_bf16_persistent_against_oracle(n):
+    """The BF16 path's power method (all products in one launch over the upper
+    triangle of the bf16 copy of R) against Algorithm alg:power in FP64 on the
+    same bf16-rounded R: only the FP32 summation order differs."""
+    R, p, _ = synth.dense_exp(n, n / 12.0, seed=70 + n)
+    lam = vne.lambda_max(dev(R), power_iters=30, seed=3, precision="bf16")
+    ref, _ = O.power_method(_bf16_round(R), rng.power_start(n, 1, 3), 30)
+    assert rel(lam, ref) < 2e-6, (lam, ref)
