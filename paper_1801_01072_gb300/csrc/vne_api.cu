@@ -303,7 +303,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             rows_per_tile0 = tc_tile_m();
             ntiles = ntiles0 = (int)(rows_pad / tc_tile_m());
         } else {
-            dia_grid = dia_step_grid(f64, D, n, S, h->sm_count);
+            dia_grid = dia_step_grid(f64, D, n, S, s, h->sm_count);
             if (dia_grid < 1) return VNE_ERR_UNSUPPORTED;
             ntiles = dia_grid;
             rows_per_tile0 = 4096;

@@ -303,7 +303,8 @@ static int grid_hb(int64_t n, int ncols, int sm_count) {
 
 // Persistent grid of the banded step (resident CTAs x SMs, capped by the
 // number of row chunks); the caller sizes the moment partials with it.
-int dia_step_grid(int is_double, int D, int64_t n, int ncols, int sm_count) {
+int dia_step_grid(int is_double, int D, int64_t n, int ncols, int s, int sm_count) {
+    (void)s;  // the kernel does not depend on the probe count beyond ncols
     const int hb = dia_supported_halfbw(D);
     if (is_double) {
         switch (hb) {

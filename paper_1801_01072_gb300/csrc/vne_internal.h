@@ -123,7 +123,7 @@ cudaError_t launch_dia_step(const T* vals, int64_t ld, int D, int64_t n, const T
                             int S, int s, StepCols cols, const double* sc, Partials P, int t,
                             int nblocks, cudaStream_t st);
 int dia_supported_halfbw(int D);  // the compiled window >= D-1, or -1
-int dia_step_grid(int is_double, int D, int64_t n, int ncols, int sm_count);
+int dia_step_grid(int is_double, int D, int64_t n, int ncols, int s, int sm_count);
 
 // ---- dense tensor-core recurrence (vne_tc.cu) -------------------------------------
 // R and Y are each a sum of `pieces` bf16 matrices (1: BF16; 2: bf16x3; 3:

@@ -153,7 +153,7 @@ def test_dense_f32_parity():
 
 @pytest.mark.parametrize("n,hb", [(1, 1), (2, 1), (17, 2), (300, 4), (1000, 8), (5000, 16),
                                   (100_003, 16), (273, 16), (545, 16)])
-@pytest.mark.parametrize("s", [1, 3, 64])
+@pytest.mark.parametrize("s", [1, 2, 3, 64])
 def test_dia_f32_parity(n, hb, s):
     vals = synth.band_diag_dominant(n, half_bw=min(hb, max(n - 1, 0)) or 1, seed=n,
                                     dtype=np.float32)
