@@ -280,7 +280,9 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
     import paper_1801_01072_gb300 as vne
 
     n, k, s = w["n"], w["k"], w["s"]
-    prec = args.precision if args.precision in ("f32", "f64") else "f32"
+    # R Pi on the tensor cores (bf16x3) unless a CUDA-core precision is asked for
+    prec = args.precision if args.precision in ("f32", "f64", "bf16x3", "bf16x6") else "bf16x3"
+    tc = prec.startswith("bf16")
     Rd = torch.as_tensor(Rh).to(dev)
     seed = w["seed"] + 1000 * rank
 
@@ -312,7 +314,7 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
         dist.barrier()
     n_launch = h.launch_count() - n_launch0
     ms = ev0.elapsed_time(ev1)
-    k_ms, k_n = h.profile_read(1)
+    k_ms, k_n = h.profile_read(0 if tc else 1)
     h.profile(False)
     t = torch.tensor([ms], device=dev)
     if world > 1:
@@ -341,18 +343,30 @@ def run_gpu_projection(args, w, Rh, p, world, rank, local, dev):
         return
 
     pk, pk_src = peaks()
-    # FP32 (or FP64) SIMT product R Pi: 2 n^2 s flops per launch.  Peak of the
-    # FP32 pipes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (FP64: 1.25 TFLOP/s).
-    flops = 2.0 * n * n * s * (q + 1) * args.steps   # q + 1 products R X with s columns
+    # the products R X: 2 n^2 s algorithmic flops per product (q + 1 products).
+    # Tensor cores (bf16x3 / bf16x6): against the measured BF16 burst peak (the
+    # split modes issue 3 / 6 MMAs per algorithmic product, reported beside);
+    # CUDA cores: FP32 152 SMs x 128 lanes x 2 flops x 2.07 GHz, FP64 nominal.
+    flops = 2.0 * n * n * s * (q + 1) * args.steps
     achieved = flops / (k_ms / 1e3) / 1e12 if k_ms > 0 else None
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == "f32" else 1.25
-    traffic = profiled_traffic("k_simt_step_f32_lowrank_n8192_k64.md", "vne_dense_simt.cu") \
-        if (prec == "f32" and args.workload == "lowrank_n8192_k64") else None
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "kernel": "k_simt_step", "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
-            "peak_source": "derived: FP32 lanes x 2 x max SM clock" if prec == "f32"
-            else "nominal FP64"}
+    if tc:
+        peak = peak_value(pk, "bf16_tflops", "bf16_tflops_sustained")
+        mma = {"bf16x3": 3, "bf16x6": 6}[prec]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if (achieved and peak) else None, "traffic": None,
+                "kernel": "k_tc_step (plain product)", "launches": k_n,
+                "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
+                "mma_tflops_issued": achieved * mma if achieved else None,
+                "peak_source": pk_src + " bf16 burst"}
+    else:
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == "f32" else 1.25
+        traffic = profiled_traffic("k_simt_step_f32_lowrank_n8192_k64.md", "vne_dense_simt.cu") \
+            if (prec == "f32" and args.workload == "lowrank_n8192_k64") else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "kernel": "k_simt_step", "launches": k_n, "avg_launch_us": k_ms / max(k_n, 1) * 1e3,
+                "peak_source": "derived: FP32 lanes x 2 x max SM clock" if prec == "f32"
+                else "nominal FP64"}
     cpu = None
     if world == 1 and not args.skip_cpu:
         t_cpu, desc, threads = oracle_projection_time(w, Rh)
@@ -1298,7 +1312,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dense_powerlaw_n8192", choices=list(synth.WORKLOADS))
     ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "bf16x6", "f64", "f32"],
-                    help="recurrence arithmetic; the projection workload runs f32 unless f64")
+                    help="recurrence arithmetic; the projection workloads run bf16x3 unless f32, "
+                         "f64 or bf16x6 is given")
     ap.add_argument("--cpu-probes", type=int, default=16)
     ap.add_argument("--ref-probes", type=int, default=4)
     ap.add_argument("--skip-cpu", action="store_true")

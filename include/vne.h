@@ -322,8 +322,15 @@ enum { VNE_SKETCH_GAUSSIAN = 0, VNE_SKETCH_SRHT = 1, VNE_SKETCH_COUNT = 2 };
  *                  plus the tail t ln((n-k)/t), t = 1 - sum theta (the rest
  *                  of the unit trace spread evenly); p_out gets theta.
  *   precision    : VNE_PREC_F64 or VNE_PREC_F32: arithmetic of Pi and of the
- *                  product R Pi.  The Gram matrix R~^T R~, its eigenvalues
- *                  (Householder tridiagonalisation + bisection) and H~ are FP64.
+ *                  product R Pi on the CUDA cores.  VNE_PREC_BF16X3 /
+ *                  VNE_PREC_BF16X6: Pi in FP32, the products R Pi (and R Q_j)
+ *                  on the tensor cores with R and Pi split into two / three
+ *                  bf16 pieces and FP32 accumulation (the recurrence's split
+ *                  modes), FP32 results.  VNE_PREC_BF16 is unsupported (its
+ *                  rounding would cost the p~ accuracy).  The Gram matrix
+ *                  R~^T R~ (compensated FP32 sums for FP32 results), its
+ *                  eigenvalues (Householder tridiagonalisation + bisection) and
+ *                  H~ are FP64.
  *   R            : VNE_DENSE only.
  *   H_out        : host, 1 double.   p_out : host, k doubles (descending), or NULL.
  * Singular values come from the eigenvalues of R~^T R~: the top-k values have

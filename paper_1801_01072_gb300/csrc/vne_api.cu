@@ -620,14 +620,80 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     return VNE_OK;
 }
 
+// R X on the tensor cores for the projection paths (Algorithm alg:EN and the
+// block-Krylov extension): X and the result FP32 [cols][n]; R and X are split
+// into `pieces` bf16 pieces (2: bf16x3, 3: bf16x6) and the step kernel runs
+// with the plain-product epilogue.
+struct TcProduct {
+    int pieces = 0;
+    int64_t n = 0, rows_pad = 0, ldk = 0;
+    int S_pad = 0;
+    __nv_bfloat16* Rp[kMaxPieces] = {};
+    __nv_bfloat16* Xp[kMaxPieces] = {};
+    double* sc = nullptr;
+    double* part = nullptr;
+    void plan(Bump& b, int pieces_, int64_t n_, int cols) {
+        pieces = pieces_;
+        n = n_;
+        if (!pieces) return;
+        rows_pad = round_up(n, tc_tile_m());
+        ldk = round_up(n, tc_tile_k());
+        S_pad = (int)round_up(cols, 32);
+        for (int k = 0; k < pieces; ++k) {
+            Rp[k] = b.take<__nv_bfloat16>((size_t)rows_pad * ldk);
+            Xp[k] = b.take<__nv_bfloat16>((size_t)S_pad * ldk);
+        }
+        sc = b.take<double>(SC_COUNT);
+        part = b.take<double>((size_t)2 * (rows_pad / tc_tile_m()) * cols);
+    }
+    // once per call: R in pieces, u = 1 in the scalar block (read, unused)
+    void prepare(Call& c, const void* Rdata, int dtype, int64_t ld) {
+        c.chk(cudaMemsetAsync(sc, 0, SC_COUNT * sizeof(double), c.st));
+        c.launched(launch_dense_convert_bf16(Rdata, dtype, n, ld, Rp, pieces, rows_pad, ldk, c.st));
+        if (c.ok()) c.launched(launch_set_u(sc, 1.0, c.st));
+    }
+    void product(Call& c, const float* X, float* dst, int cols) {
+        if (!c.ok()) return;
+        c.launched(launch_convert_bf16_rect(X, VNE_F32, cols, n, n, Xp, pieces, S_pad, ldk, c.st));
+        if (!c.ok()) return;
+        TcStep a{};
+        a.pieces = pieces;
+        for (int k = 0; k < pieces; ++k) {
+            a.R[k] = Rp[k];
+            a.Y[k] = Xp[k];
+            a.Y_out[k] = Xp[k];  // not written by the plain product
+        }
+        a.G = dst;
+        a.Yprev = dst;
+        a.Yprev2 = dst;
+        a.Ynew = dst;
+        a.n = n;
+        a.rows_pad = rows_pad;
+        a.ldk = ldk;
+        a.S = cols;
+        a.s = cols;
+        a.split = 1;
+        a.cols = StepCols{0, 0, 0, cols, EPI_PLAIN};
+        a.sc = sc;
+        const int nt = (int)(rows_pad / tc_tile_m());
+        a.P = Partials{part, nt, nt, cols};
+        a.t = 1;
+        c.prof_begin();
+        c.launched(launch_tc_step(a, c.h->sm_count, c.st));
+        c.prof_end(0);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Random projection (Algorithm alg:EN): sketch -> R Pi -> Gram -> eigenvalues
 // -> top-k singular values and H~.
 // ---------------------------------------------------------------------------
 template <typename T>
 vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int kind,
-                          uint64_t seed, double* H_out, double* p_out, cudaStream_t st) {
+                          uint64_t seed, double* H_out, double* p_out, cudaStream_t st,
+                          int pieces = 0) {
     Call c{h, st};
+    TcProduct tcp;
     const int64_t n = R.n;
     const int want = sizeof(T) == 8 ? VNE_F64 : VNE_F32;
     const int splitk = dense_simt_splitk(n, s, h->sm_count, (int)sizeof(T));
@@ -636,10 +702,11 @@ vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int 
                     double** C, double** W, double** de, double** ev, double** out) {
         *Rcopy = R.memory == VNE_MEM_HOST ? b.take<char>((size_t)n * R.ld * elt_size(R.dtype))
                                           : nullptr;
-        *Rop = R.dtype != want ? b.take<T>((size_t)n * n) : nullptr;
+        *Rop = (R.dtype != want && !pieces) ? b.take<T>((size_t)n * n) : nullptr;
         *Pi = b.take<T>((size_t)n * s);
-        *Zpart = b.take<T>((size_t)splitk * s * n);
-        *Z = splitk > 1 ? b.take<T>((size_t)s * n) : *Zpart;
+        *Zpart = b.take<T>((size_t)(pieces ? 1 : splitk) * s * n);
+        *Z = (splitk > 1 && !pieces) ? b.take<T>((size_t)s * n) : *Zpart;
+        tcp.plan(b, pieces, n, s);
         *part = b.take<double>((size_t)chunks * s * s);
         *C = b.take<double>((size_t)s * s);
         *W = b.take<double>((size_t)s * s);
@@ -677,13 +744,18 @@ vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int 
         ldr = n;
     }
     if (c.ok()) c.launched(launch_sketch<T>(Pi, n, s, kind, seed, h->sm_count, st));
-    if (c.ok()) {
-        c.prof_begin();
-        c.launched(launch_dense_simt_step<T>(Rk, ldr, n, Pi, Zpart, s, 0, s, splitk, st));
-        c.prof_end(1);
+    if (pieces) {
+        if (c.ok()) tcp.prepare(c, Rdata, R.dtype, R.ld);
+        tcp.product(c, (const float*)Pi, (float*)Z, s);
+    } else {
+        if (c.ok()) {
+            c.prof_begin();
+            c.launched(launch_dense_simt_step<T>(Rk, ldr, n, Pi, Zpart, s, 0, s, splitk, st));
+            c.prof_end(1);
+        }
+        if (c.ok() && splitk > 1)
+            c.launched(launch_split_sum<T>(Zpart, splitk, (int64_t)s * n, Z, h->sm_count, st));
     }
-    if (c.ok() && splitk > 1)
-        c.launched(launch_split_sum<T>(Zpart, splitk, (int64_t)s * n, Z, h->sm_count, st));
     if (c.ok()) c.launched(launch_gram<T>(Z, n, s, chunks, part, C, st));
     if (c.ok()) c.launched(launch_sym_eigvals(C, s, k, W, de, de + s, ev, st));
     if (c.ok()) c.launched(launch_proj_combine(ev, k, out, st));
@@ -708,8 +780,10 @@ vne_status run_projection(vne_handle* h, const vne_matrix& R, int k, int s, int 
 // ---------------------------------------------------------------------------
 template <typename T>
 vne_status run_krylov(vne_handle* h, const vne_matrix& R, int k, int b, int q, int kind,
-                      uint64_t seed, double* H_out, double* p_out, cudaStream_t st) {
+                      uint64_t seed, double* H_out, double* p_out, cudaStream_t st,
+                      int pieces = 0) {
     Call c{h, st};
+    TcProduct tcp;
     const int64_t n = R.n;
     const int want = sizeof(T) == 8 ? VNE_F64 : VNE_F32;
     const int N = q * b;
@@ -722,10 +796,11 @@ vne_status run_krylov(vne_handle* h, const vne_matrix& R, int k, int b, int q, i
                     double** lref) {
         *Rcopy = R.memory == VNE_MEM_HOST ? bp.take<char>((size_t)n * R.ld * elt_size(R.dtype))
                                           : nullptr;
-        *Rop = R.dtype != want ? bp.take<T>((size_t)n * n) : nullptr;
+        *Rop = (R.dtype != want && !pieces) ? bp.take<T>((size_t)n * n) : nullptr;
         *Pi = bp.take<T>((size_t)n * b);
         *V = bp.take<T>((size_t)n * b);
-        *Zpart = bp.take<T>((size_t)splitk * b * n);
+        *Zpart = bp.take<T>((size_t)(pieces ? 1 : splitk) * b * n);
+        tcp.plan(bp, pieces, n, b);
         *K = bp.take<T>((size_t)N * n);
         *W = bp.take<T>((size_t)N * n);
         *part = bp.take<double>((size_t)chunks * N * N);
@@ -772,9 +847,14 @@ vne_status run_krylov(vne_handle* h, const vne_matrix& R, int k, int b, int q, i
         Rk = Rop;
         ldr = n;
     }
+    if (pieces && c.ok()) tcp.prepare(c, Rdata, R.dtype, R.ld);
     // dst = R X (X stored [b][n])
     auto product = [&](const T* X, T* dst) {
         if (!c.ok()) return;
+        if (pieces) {
+            tcp.product(c, (const float*)X, (float*)dst, b);
+            return;
+        }
         c.prof_begin();
         c.launched(launch_dense_simt_step<T>(Rk, ldr, n, X, Zpart, b, 0, b, splitk, st));
         c.prof_end(1);
@@ -1240,10 +1320,12 @@ vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k,
     if (R->layout != VNE_DENSE && R->layout != VNE_DIA) return VNE_ERR_INVALID_ARG;
     if (s < 1 || k < 1 || (krylov_iters <= 0 && k > s)) return VNE_ERR_INVALID_ARG;
     if (sketch < VNE_SKETCH_GAUSSIAN || sketch > VNE_SKETCH_COUNT) return VNE_ERR_INVALID_ARG;
-    if (precision < VNE_PREC_F64 || precision > VNE_PREC_BF16X3 || krylov_iters < 0)
+    if (precision < VNE_PREC_F64 || precision > VNE_PREC_BF16X6 || krylov_iters < 0)
         return VNE_ERR_INVALID_ARG;
-    if (R->layout != VNE_DENSE || s > 512 || precision > VNE_PREC_F32 || is_complex(R->dtype))
+    if (R->layout != VNE_DENSE || s > 512 || precision == VNE_PREC_BF16 || is_complex(R->dtype))
         return VNE_ERR_UNSUPPORTED;
+    // the split modes run R Pi (and R Q_j) on the tensor cores, FP32 results
+    const int pieces = precision == VNE_PREC_BF16X3 ? 2 : precision == VNE_PREC_BF16X6 ? 3 : 0;
     if ((int64_t)s * R->n > ((int64_t)1 << 40)) return VNE_ERR_UNSUPPORTED;
     if (krylov_iters > 0) {
         if (s > 64 || (int64_t)krylov_iters * s > 512) return VNE_ERR_UNSUPPORTED;
@@ -1255,11 +1337,12 @@ vne_status vne_entropy_projection(vne_handle* h, const vne_matrix* R, int32_t k,
             return run_krylov<double>(h, *R, k, s, krylov_iters, sketch, seed, H_out, p_out,
                                       (cudaStream_t)stream);
         return run_krylov<float>(h, *R, k, s, krylov_iters, sketch, seed, H_out, p_out,
-                                 (cudaStream_t)stream);
+                                 (cudaStream_t)stream, pieces);
     }
     if (precision == VNE_PREC_F64)
         return run_projection<double>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
-    return run_projection<float>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream);
+    return run_projection<float>(h, *R, k, s, sketch, seed, H_out, p_out, (cudaStream_t)stream,
+                                 pieces);
 }
 
 vne_status vne_entropy_chebyshev_learned(vne_handle* h, const vne_matrix* R, const vne_params* p,

@@ -24,7 +24,8 @@ struct Partials {
 //   CHEB1 : Y_1 = a Z - G              (a = 2/u), moment g^T Y_1
 //   CHEB  : Y_t = 2(a Z - Y_{t-1}) - Y_{t-2},      moment g^T Y_t
 //   TAYLOR: Y_t = Y_{t-1} - Z / u,                 moment g^T Z  (= tau_{t-1})
-enum EpiKind { EPI_NONE = 0, EPI_CHEB1 = 1, EPI_CHEB = 2, EPI_TAYLOR = 3 };
+//   PLAIN : Y_t = Z (the plain product, tensor-core step only; no moments)
+enum EpiKind { EPI_NONE = 0, EPI_CHEB1 = 1, EPI_CHEB = 2, EPI_TAYLOR = 3, EPI_PLAIN = 4 };
 
 struct StepCols {
     // columns [c0, c0+ncheb) are Chebyshev, [t0, t0+ntay) are Taylor
@@ -62,6 +63,11 @@ cudaError_t launch_dense_convert_f32(const void* src, int src_dtype, int64_t n, 
 cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
                                       __nv_bfloat16* const* out, int pieces, int64_t rows_pad,
                                       int64_t ldk, cudaStream_t st);
+// The same split of a rectangular block: rows x cols entries src[i*ld + k],
+// zero padded to rows_pad x ldk.
+cudaError_t launch_convert_bf16_rect(const void* src, int src_dtype, int64_t rows, int64_t cols,
+                                     int64_t ld, __nv_bfloat16* const* out, int pieces,
+                                     int64_t rows_pad, int64_t ldk, cudaStream_t st);
 cudaError_t launch_dia_convert(const void* src, int src_dtype, int64_t n, int64_t ld, int D,
                                void* dst, int dst_dtype, cudaStream_t st);
 // [[B, -C], [C, B]] of the Hermitian R = B + iC (complex dtype 2 or 3, n x n,

@@ -88,8 +88,8 @@ struct BfPieces {
     __nv_bfloat16* p[kMaxPieces];
 };
 template <int PIECES>
-__global__ void k_dense_convert_bf16(const void* src, int dtype, int64_t n, int64_t ld,
-                                     BfPieces out, int64_t rows_pad, int64_t ldk) {
+__global__ void k_dense_convert_bf16(const void* src, int dtype, int64_t nrows, int64_t ncols,
+                                     int64_t ld, BfPieces out, int64_t rows_pad, int64_t ldk) {
     const int64_t groups = ldk / 8;
     const int64_t total = rows_pad * groups;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -99,7 +99,7 @@ __global__ void k_dense_convert_bf16(const void* src, int dtype, int64_t n, int6
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t k = k0 + q;
-            const bool in = i < n && k < n;
+            const bool in = i < nrows && k < ncols;
             if (PIECES < 3) {
                 const float v = in ? (float)load_entry(src, dtype, i * ld + k) : 0.f;
                 const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -122,10 +122,11 @@ __global__ void k_dense_convert_bf16(const void* src, int dtype, int64_t n, int6
     }
 }
 
-cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
-                                      __nv_bfloat16* const* out, int pieces, int64_t rows_pad,
-                                      int64_t ldk, cudaStream_t st) {
-    if (ldk % 8 != 0 || pieces < 1 || pieces > kMaxPieces || !out) return cudaErrorInvalidValue;
+cudaError_t launch_convert_bf16_rect(const void* src, int src_dtype, int64_t rows, int64_t cols,
+                                     int64_t ld, __nv_bfloat16* const* out, int pieces,
+                                     int64_t rows_pad, int64_t ldk, cudaStream_t st) {
+    if (ldk % 8 != 0 || pieces < 1 || pieces > kMaxPieces || !out || rows > rows_pad || cols > ldk)
+        return cudaErrorInvalidValue;
     BfPieces ps{};
     for (int c = 0; c < pieces; ++c) {
         if (!out[c]) return cudaErrorInvalidValue;
@@ -133,12 +134,18 @@ cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n,
     }
     const unsigned g = grid_for(rows_pad * (ldk / 8));
     if (pieces == 1)
-        k_dense_convert_bf16<1><<<g, 256, 0, st>>>(src, src_dtype, n, ld, ps, rows_pad, ldk);
+        k_dense_convert_bf16<1><<<g, 256, 0, st>>>(src, src_dtype, rows, cols, ld, ps, rows_pad, ldk);
     else if (pieces == 2)
-        k_dense_convert_bf16<2><<<g, 256, 0, st>>>(src, src_dtype, n, ld, ps, rows_pad, ldk);
+        k_dense_convert_bf16<2><<<g, 256, 0, st>>>(src, src_dtype, rows, cols, ld, ps, rows_pad, ldk);
     else
-        k_dense_convert_bf16<3><<<g, 256, 0, st>>>(src, src_dtype, n, ld, ps, rows_pad, ldk);
+        k_dense_convert_bf16<3><<<g, 256, 0, st>>>(src, src_dtype, rows, cols, ld, ps, rows_pad, ldk);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n, int64_t ld,
+                                      __nv_bfloat16* const* out, int pieces, int64_t rows_pad,
+                                      int64_t ldk, cudaStream_t st) {
+    return launch_convert_bf16_rect(src, src_dtype, n, n, ld, out, pieces, rows_pad, ldk, st);
 }
 
 __global__ void k_dia_convert(const void* src, int sdt, int64_t n, int64_t ld, int D, void* dst,

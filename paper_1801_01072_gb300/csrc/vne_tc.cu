@@ -246,7 +246,8 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
 // row: branch-free, so the shared-memory reads, updates and stores of the 32
 // columns can be scheduled together.  KIND 0: Taylor, Y_t = Y_{t-1} - Z/u,
 // moment g Z; 1: first Chebyshev step, Y_1 = (2/u) Z - G; 2: three-term
-// Chebyshev step, Y_t = 2((2/u) Z - Y_{t-1}) - Y_{t-2}; moment g Y_t for both.
+// Chebyshev step, Y_t = 2((2/u) Z - Y_{t-1}) - Y_{t-2}; moment g Y_t for both;
+// 3: the plain product, Y_t = Z (no moment, no bf16 pieces).
 // ob: Y_{t-1} of the chunk in smem ([32 cols][128 rows], Y_{t-2} 32*128 floats
 // later); yn / ysh[k]: this row's entry of the chunk's first column in Y_t and
 // in its bf16 pieces k < pieces.
@@ -278,6 +279,9 @@ __device__ __forceinline__ void epi_chunk_uniform(const uint32_t* r, const float
         } else if (KIND == 1) {
             y[q] = fmaf(fa, z, -g[q]);
             v[q] = g[q] * y[q];
+        } else if (KIND == 3) {
+            y[q] = z;
+            v[q] = 0.f;
         } else {
             y[q] = 2.f * fmaf(fa, z, -ob[q * TC_BM]) - ob[(32 + q) * TC_BM];
             v[q] = g[q] * y[q];
@@ -287,7 +291,7 @@ __device__ __forceinline__ void epi_chunk_uniform(const uint32_t* r, const float
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             yn[q * n] = y[q];
-            store_pieces(y[q], ysh, pieces, q * ldk);
+            if (KIND != 3) store_pieces(y[q], ysh, pieces, q * ldk);
         }
     }
 }
@@ -332,7 +336,9 @@ struct TcMaps {
 // 2BN)), its small correction products first while the accumulator is small,
 // and warps 4-7 add it with round-to-nearest FP32 adds into a running sum in
 // columns [2BN, 3BN), which the epilogue reads (bias then ~4e-8).
-template <int P>
+// PLAIN: the plain product Y_t = Z (cols.cheb_kind == EPI_PLAIN), compiled
+// separately so that the recurrence instances keep their register budget.
+template <int P, bool PLAIN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_step(const __grid_constant__ TcMaps maps, const TcArgs a) {
     constexpr int BK = P == 3 ? 32 : 64;
@@ -550,6 +556,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int ck_first = ck_lo + chalf;
     const int cb0 = a.cols.cheb_c0, cb1 = a.cols.cheb_c0 + a.cols.ncheb;
     const bool three_term = a.cols.cheb_kind == EPI_CHEB;
+    constexpr bool plain = PLAIN;  // Y_t = Z: no G, no Y_{t-1}, no moments
     // G of the 32 columns of chunk ck at this thread's row (0 outside the
     // active columns); the columns map to consecutive probes unless the chunk
     // wraps past s.
@@ -562,7 +569,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int q = 0; q < 32; ++q) {
             const int c = cbase + q;
             g[q] = 0.f;
-            if (c < a.col_end && row_ok)
+            if (!plain && c < a.col_end && row_ok)
                 g[q] = nowrap ? __ldg(gcol + (int64_t)q * a.n)
                               : __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
         }
@@ -613,8 +620,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int o0 = c0 > cb0 ? c0 : cb0, o1 = c1 < cb1 ? c1 : cb1;
         const int ncheb = o1 > o0 ? o1 - o0 : 0;
         const int nall = c1 > c0 ? c1 - c0 : 0;
-        n1 = (nall > ncheb) || (ncheb > 0 && three_term);
-        n2 = ncheb > 0 && three_term;
+        n1 = !plain && ((nall > ncheb) || (ncheb > 0 && three_term));
+        n2 = !plain && ncheb > 0 && three_term;
     };
     if (a.epi_tma && !aborted && threadIdx.x == 0) {
         uint32_t bytes = 0;
@@ -699,7 +706,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < kMaxPieces; ++k)
                 ysh.p[k] = k < P ? a.Yout.p[k] + o0 : nullptr;
-            if (all_tay)
+            if (plain)
+                epi_chunk_uniform<3>(r, g, ob, yn, ysh, P, a.n, a.ldk, fa, finvu, row_ok, v);
+            else if (all_tay)
                 epi_chunk_uniform<0>(r, g, ob, yn, ysh, P, a.n, a.ldk, fa, finvu, row_ok, v);
             else if (!three_term)
                 epi_chunk_uniform<1>(r, g, ob, yn, ysh, P, a.n, a.ldk, fa, finvu, row_ok, v);
@@ -719,12 +728,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!three_term) y = fmaf(fa, z, -g[q]);
                 else y = 2.f * fmaf(fa, z, -ypf(q)) - yp2f(q);
                 v[q] = g[q] * y;
+            } else if (plain) {
+                y = z;
             } else {
                 v[q] = g[q] * z;
                 y = fmaf(-z, finvu, ypf(q));
             }
             a.Ynew[idx] = y;
-            store_pieces(y, a.Yout, P, (int64_t)c * a.ldk + row);
+            if (!plain) store_pieces(y, a.Yout, P, (int64_t)c * a.ldk + row);
         }
         }
 #pragma unroll
@@ -781,8 +792,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (c >= a.col_end || !row_ok) continue;
                 const bool cheb = c >= cb0 && c < cb1;
                 const int64_t idx = (int64_t)c * a.n + row;
-                if (!cheb || three_term) yp[q] = __ldg(a.Yprev + idx);
-                if (cheb && three_term) yp2[q] = __ldg(a.Yprev2 + idx);
+                if (!plain && (!cheb || three_term)) yp[q] = __ldg(a.Yprev + idx);
+                if (!plain && cheb && three_term) yp2[q] = __ldg(a.Yprev2 + idx);
             }
             tmem_wait_ld();
             finish_chunk(
@@ -1106,13 +1117,18 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     a.P = s.P;
     a.t = s.t;
 
-    void (*kern)(TcMaps, TcArgs) = P == 1 ? k_tc_step<1> : P == 2 ? k_tc_step<2> : k_tc_step<3>;
-    static size_t smem_set[kMaxPieces + 1] = {0, 0, 0, 0};  // raised as needed, never lowered
-    if (smem > smem_set[P]) {
+    const bool plain = s.cols.cheb_kind == EPI_PLAIN;
+    if (plain && P == 1) return cudaErrorInvalidValue;  // plain products use the split modes
+    void (*kern)(TcMaps, TcArgs) =
+        plain ? (P == 2 ? k_tc_step<2, true> : k_tc_step<3, true>)
+              : (P == 1 ? k_tc_step<1, false> : P == 2 ? k_tc_step<2, false> : k_tc_step<3, false>);
+    const int ki = plain ? 3 + P : P;
+    static size_t smem_set[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // raised as needed, never lowered
+    if (smem > smem_set[ki]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        smem_set[P] = smem;
+        smem_set[ki] = smem;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)mtiles, (unsigned)sh.ntn, (unsigned)sh.ksplit);

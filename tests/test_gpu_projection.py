@@ -9,6 +9,8 @@ to about sqrt(eps) * p~_1 absolute, so tolerances are on H~ (relative) and
 on p~_i relative to p~_1:
   FP64 path   H~ 1e-9,  p~ 1e-9 p~_1
   FP32 path   H~ 1e-4,  p~ 1e-4 p~_1   (FP32 products R Pi, FP64 Gram)
+  bf16x3      H~ 1e-4,  p~ 1e-4 p~_1   (R Pi on the tensor cores, two bf16 pieces)
+  bf16x6      H~ 2e-5,  p~ 2e-5 p~_1   (three pieces, chunked FP32 accumulation)
 """
 import numpy as np
 import pytest
@@ -23,7 +25,7 @@ vne = pytest.importorskip("paper_1801_01072_gb300")
 INVALID_ARG, UNSUPPORTED = 1, 8  # vne_status codes
 
 KINDS = ["gaussian", "srht", "countsketch"]
-TOL = {"f64": 1e-9, "f32": 1e-4}
+TOL = {"f64": 1e-9, "f32": 1e-4, "bf16x3": 1e-4, "bf16x6": 2e-5}
 
 
 def dev(x):
@@ -72,6 +74,17 @@ def test_projection_f32_and_f32_storage(kind):
     check(got, OP.estimate_projection(R32.astype(np.float64), k, s, kind, seed=11), "f64")
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n,k,s", [(300, 10, 33), (1000, 24, 100), (600, 16, 64), (129, 8, 250)])
+def test_projection_tensor_core_product(prec, kind, n, k, s):
+    """R Pi on the tensor cores (plain-product epilogue), ragged n and s."""
+    R, p, _ = synth.dense_lowrank(n, k, tau=k / 4, seed=n + k)
+    ref = OP.estimate_projection(R, k, s, kind, seed=5)
+    got = vne.entropy_projection(dev(R), k, s, kind, seed=5, precision=prec)
+    check(got, ref, prec)
+
+
 def test_projection_full_rank_spectrum():
     # not the rank-k setting of the theorem: parity still holds step by step
     R, p, _ = synth.dense_exp(256, 30.0, seed=3)
@@ -88,7 +101,7 @@ def test_projection_largest_sketch_uses_global_scratch():
     check(got, OP.estimate_projection(R, k, s, "gaussian", seed=4), "f64")
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("prec", ["f32", "f64", "bf16x3", "bf16x6"])
 def test_projection_bench_workload_full_size(prec):
     w = synth.WORKLOADS["lowrank_n8192_k64"]
     R, p, _ = synth.dense_lowrank(w["n"], w["k"], w["tau"], w["seed"])
@@ -170,7 +183,7 @@ def test_krylov_recovers_rank_k_exactly(kind):
     assert abs(got.H - H) <= 1e-9 * H
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("n,b,q,k", [(256, 16, 3, 24), (500, 32, 2, 40), (129, 8, 4, 20)])
 def test_krylov_parity_full_rank(prec, n, b, q, k):
     R, p, _ = synth.dense_exp(n, 30.0, seed=n)
@@ -181,11 +194,12 @@ def test_krylov_parity_full_rank(prec, n, b, q, k):
     check_krylov(got, ref, 1e-9 if prec == "f64" else 1e-4)
 
 
-def test_krylov_bench_shape():
+@pytest.mark.parametrize("prec", ["f32", "bf16x3", "bf16x6"])
+def test_krylov_bench_shape(prec):
     # block 64, 4 iterations, top-64 Ritz values on the n = 8192 rank-64 matrix
     w = synth.WORKLOADS["lowrank_n8192_k64"]
     R, p, _ = synth.dense_lowrank(w["n"], w["k"], w["tau"], w["seed"])
-    got = vne.entropy_projection(dev(R), 64, 64, "gaussian", seed=1, precision="f32",
+    got = vne.entropy_projection(dev(R), 64, 64, "gaussian", seed=1, precision=prec,
                                  krylov_iters=4)
     # FP32 products: errors of ~1e-5 of theta_1 on the smallest Ritz values
     assert np.abs(got.p - p).max() <= 1e-4 * p[0]
