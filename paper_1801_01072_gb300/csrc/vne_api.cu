@@ -313,19 +313,22 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     const int power_blocks = dense ? (int)std::min<int64_t>((n + 7) / 8, 8 * h->sm_count)
                                    : 4 * h->sm_count;
     // Arithmetic of the power-method products (dense): the FP64/FP32 paths use
-    // their own; BF16 streams bf16 R; the split modes (bf16x3, bf16x6) keep
-    // lambda_max and u in the input's precision (FP64 for an FP64 R; the FP32
+    // their own; BF16 uses bf16 R.  The split modes (bf16x3, bf16x6) use
+    // R_0 + R_1 (16 significant bits, exact FP32 sums) in the persistent
+    // kernel, else R in its input precision (FP64 for an FP64 R; the FP32
     // embedding of a complex R), so that u does not carry bf16 rounding.
-    int pw_rdt;  // 0 FP64 R, 1 FP32 R, 2 bf16 piece 0
+    int pw_rdt;  // 0 FP64 R, 1 FP32 R, 2 bf16 pieces
     if (!tc) pw_rdt = f64 ? 0 : 1;
     else if (pieces == 1) pw_rdt = 2;
     else pw_rdt = (!cplx && R.dtype == VNE_F64) ? 0 : 1;
-    const int pw_xdouble = dense ? (pw_rdt == 0 ? 1 : 0) : (f64 ? 1 : 0);
-    // bf16 R, one trial, a single call: every product in one persistent
+    // bf16 pieces, one trial, a single call: every product in one persistent
     // launch over the upper triangle (VNE_POWER_SYM=0: one launch per product)
-    const bool use_sym = do_power && dense && pw_rdt == 2 && q == 1 && n >= 2048 && !out.ws &&
+    const bool use_sym = do_power && dense && tc && q == 1 && n >= 2048 && !out.ws &&
                          !out.measure && power_sym_fits(rows_pad, h->sm_count) &&
                          power_sym_enabled(h);
+    const int sym_pieces = pieces >= 2 ? 2 : 1;
+    if (use_sym) pw_rdt = 2;
+    const int pw_xdouble = dense ? (pw_rdt == 0 ? 1 : 0) : (f64 ? 1 : 0);
 
     // ---- workspace plan (two passes) ----
     const size_t vt = f64 ? 8 : 4;  // master / operand element size of SIMT & DIA paths
@@ -450,8 +453,8 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         // would stop the next one from starting early (programmatic launch)
         c.prof_begin();
         if (use_sym) {
-            c.launched(launch_power_sym(Rpc[0], n, rows_pad, ldk, (const float*)x0, p->power_iters,
-                                        sc, symws, u_scale, h->sm_count, c.st));
+            c.launched(launch_power_sym(Rpc, sym_pieces, n, rows_pad, ldk, (const float*)x0,
+                                        p->power_iters, sc, symws, u_scale, h->sm_count, c.st));
         }
         for (int it = 0; it <= p->power_iters && c.ok() && !use_sym; ++it) {
             const int fin = it == p->power_iters;

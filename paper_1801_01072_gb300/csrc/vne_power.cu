@@ -460,6 +460,7 @@ constexpr int kSymMaxTiles = 512;                 // tiles per CTA (tile list in
 constexpr int64_t kSymMaxRows = 16384;            // x_hat in shared memory (64 KB)
 
 struct SymArgs {
+    int pieces;      // 1: R = piece 0; 2: R = piece 0 + piece 1 (the sum is exact in FP32)
     int64_t n;
     int nb;          // 128-row blocks of the padded matrix
     int ntile;       // nb (nb + 1) / 2
@@ -522,12 +523,18 @@ __device__ __forceinline__ double sym_block_sum(double v, double* red) {
     return v;
 }
 
-__global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_constant__ CUtensorMap mapR,
+struct SymMaps {
+    CUtensorMap R[2];
+};
+
+__global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_constant__ SymMaps maps,
                                                       const SymArgs a) {
     extern __shared__ __align__(1024) uint8_t sraw[];
     uint8_t* ring = sraw + ((1024u - (smem_u32(sraw) & 1023u)) & 1023u);
     const int NS = a.stages;
-    float* xsm = reinterpret_cast<float*>(ring + (size_t)NS * kSymTileBytes);  // nb*128
+    const int NP = a.pieces;
+    const uint32_t stage_bytes = (uint32_t)NP * kSymTileBytes;  // the pieces' tiles, one after the other
+    float* xsm = reinterpret_cast<float*>(ring + (size_t)NS * stage_bytes);  // nb*128
     __shared__ uint64_t full[kSymMaxStages];
     __shared__ float colsm[2][kSymWarps][kSymT];  // per-warp column partials (two tiles); group sums
     __shared__ int flag_sh;
@@ -552,7 +559,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
     if (tid == 0) {
         for (int st = 0; st < NS; ++st) mbar_init(&full[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapR)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.R[0])) : "memory");
         flag_sh = 0;
     }
     __syncthreads();
@@ -562,9 +569,10 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
     auto issue = [&](int item) {
         const int st = item % NS;
         const uint32_t tk = tl[item % mine];
-        mbar_expect_tx(&full[st], kSymTileBytes);
-        sym_tma_tile(ring + (size_t)st * kSymTileBytes, &mapR, &full[st],
-                     (int)(tk & 0xFFFFu) * kSymT, (int)(tk >> 16) * kSymT, pol);
+        mbar_expect_tx(&full[st], stage_bytes);
+        for (int pc = 0; pc < NP; ++pc)
+            sym_tma_tile(ring + (size_t)st * stage_bytes + (size_t)pc * kSymTileBytes, &maps.R[pc],
+                         &full[st], (int)(tk & 0xFFFFu) * kSymT, (int)(tk >> 16) * kSymT, pol);
     };
     int issued = 0;
     if (tid == 0)
@@ -596,7 +604,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
             const int I = (int)(tk >> 16), K = (int)(tk & 0xFFFFu);
             if (!mbar_wait(&full[st], (uint32_t)(item / NS) & 1u, &flag_sh)) flag_sh = 1;
             const __nv_bfloat16* tile =
-                reinterpret_cast<const __nv_bfloat16*>(ring + (size_t)st * kSymTileBytes);
+                reinterpret_cast<const __nv_bfloat16*>(ring + (size_t)st * stage_bytes);
+            const __nv_bfloat16* tile2 = tile + kSymT * kSymT;  // piece 1 (NP == 2)
             const float4 xk = *reinterpret_cast<const float4*>(xsm + K * kSymT + 4 * lane);
             const float* xi_row = xsm + I * kSymT + 16 * w;
             float rp[16];
@@ -605,8 +614,17 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
             for (int r = 0; r < 16; ++r) {
                 const int row = 16 * w + r;
                 const uint2 raw = *reinterpret_cast<const uint2*>(tile + row * kSymT + 4 * lane);
-                const float2 f01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
-                const float2 f23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+                float2 f01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+                float2 f23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+                if (NP == 2) {
+                    const uint2 r2 = *reinterpret_cast<const uint2*>(tile2 + row * kSymT + 4 * lane);
+                    const float2 g01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r2.x));
+                    const float2 g23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r2.y));
+                    f01.x += g01.x;
+                    f01.y += g01.y;
+                    f23.x += g23.x;
+                    f23.y += g23.y;
+                }
                 float v = f01.x * xk.x;
                 v = fmaf(f01.y, xk.y, v);
                 v = fmaf(f23.x, xk.z, v);
@@ -770,16 +788,19 @@ bool power_sym_fits(int64_t rows_pad, int sm_count) {
     return (ntile + G - 1) / G <= kSymMaxTiles;
 }
 
-cudaError_t launch_power_sym(const __nv_bfloat16* R, int64_t n, int64_t rows_pad, int64_t ldk,
-                             const float* x0, int t, double* sc, void* scratch,
-                             double u_scale, int sm_count, cudaStream_t st) {
-    if (!power_sym_fits(rows_pad, sm_count) || (ldk % 8) != 0 || t < 0)
+cudaError_t launch_power_sym(const __nv_bfloat16* const* R, int pieces, int64_t n,
+                             int64_t rows_pad, int64_t ldk, const float* x0, int t, double* sc,
+                             void* scratch, double u_scale, int sm_count, cudaStream_t st) {
+    if (!power_sym_fits(rows_pad, sm_count) || (ldk % 8) != 0 || t < 0 || pieces < 1 ||
+        pieces > 2)
         return cudaErrorInvalidValue;
     const int nb = (int)(rows_pad / kSymT);
     const int ntile = nb * (nb + 1) / 2;
     const int G = ntile < sm_count ? ntile : sm_count;
-    alignas(64) CUtensorMap map;
-    if (!tma_map_bf16_plain(&map, R, ldk, rows_pad, ldk, kSymT, kSymT)) return cudaErrorInvalidValue;
+    SymMaps maps;
+    for (int pc = 0; pc < 2; ++pc)
+        if (!tma_map_bf16_plain(&maps.R[pc], R[pc < pieces ? pc : 0], ldk, rows_pad, ldk, kSymT, kSymT))
+            return cudaErrorInvalidValue;
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) {
         char* q = p;
@@ -787,6 +808,7 @@ cudaError_t launch_power_sym(const __nv_bfloat16* R, int64_t n, int64_t rows_pad
         return q;
     };
     SymArgs a;
+    a.pieces = pieces;
     a.n = n;
     a.nb = nb;
     a.ntile = ntile;
@@ -808,11 +830,11 @@ cudaError_t launch_power_sym(const __nv_bfloat16* R, int64_t n, int64_t rows_pad
         static_smem = (int)fa.sharedSizeBytes;
     }
     const int64_t room = 227 * 1024 - 1024 - static_smem - rows_pad * 4;
-    int stages = (int)(room / kSymTileBytes);
+    int stages = (int)(room / ((int64_t)pieces * kSymTileBytes));
     if (stages > kSymMaxStages) stages = kSymMaxStages;
     if (stages < 2) return cudaErrorInvalidValue;
     a.stages = stages;
-    const size_t smem = 1024 + (size_t)stages * kSymTileBytes + (size_t)rows_pad * 4;
+    const size_t smem = 1024 + (size_t)stages * pieces * kSymTileBytes + (size_t)rows_pad * 4;
     static size_t attr = 0;
     if (smem > attr) {
         e = cudaFuncSetAttribute(k_power_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -829,7 +851,7 @@ cudaError_t launch_power_sym(const __nv_bfloat16* R, int64_t n, int64_t rows_pad
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_power_sym, map, a);
+    return cudaLaunchKernelEx(&cfg, k_power_sym, maps, a);
 }
 
 cudaError_t launch_power_step_dense(const void* R, int rdtype, int64_t n, int64_t ld,

@@ -319,6 +319,31 @@ def _bf16_round(a):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def _split2(a, fp64_residual):
+    """The first two bf16 pieces of the split modes' copy of R: bf16x3 splits
+    R rounded to FP32 (FP32 residual), bf16x6 takes the residual in FP64."""
+    if fp64_residual:
+        h = _bf16_round(a)
+        return h + _bf16_round(np.asarray(a, dtype=np.float64) - h)
+    v = np.asarray(a, dtype=np.float32).astype(np.float64)
+    h = _bf16_round(v)
+    return h + _bf16_round(v - h)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_power_method_split_modes_against_oracle(prec):
+    """The split modes' power method (the persistent kernel on the first two
+    bf16 pieces, R_0 + R_1 exact in FP32) against Algorithm alg:power in
+    FP64 on the same two-piece R, and against FP64 on R itself."""
+    n = 3000
+    R, p, _ = synth.dense_exp(n, n / 12.0, seed=77)
+    lam = vne.lambda_max(dev(R), power_iters=30, seed=3, precision=prec)
+    ref, _ = O.power_method(_split2(R, prec == "bf16x6"), rng.power_start(n, 1, 3), 30)
+    assert rel(lam, ref) < 2e-6, (lam, ref)
+    exact, _ = O.power_method(R, rng.power_start(n, 1, 3), 30)
+    assert rel(lam, exact) < 1e-6, (lam, exact)
+
+
 @pytest.mark.parametrize("n", [2048, 2049, 4100])
 def test_power_method_bf16_persistent_against_oracle(n):
     """The BF16 path's power method (all products in one launch over the upper

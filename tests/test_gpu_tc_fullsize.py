@@ -11,11 +11,8 @@ GPU's own power method, then evaluate the oracle at the same u:
     the others): each moment mu[k, j], tau[k, j], and the per-probe forms
     q_j = -sum_k alpha_k mu[k, j] (Algorithm 1b) and
     t_j = sum_{k>=1} tau[k, j] / k (Algorithm 1a);
-  - the estimate over all 128 probes.  The FP64, bf16x3 and bf16x6 paths
-    share the FP64 power method, whose u agrees with the oracle's to 1e-12;
-    their estimates are compared with the oracle's at the oracle's u (the
-    difference this makes is far below every tolerance), the BF16 path's at
-    its own u.
+  - the estimate over all 128 probes, at the GPU's own u (the FP64 path's u
+    equals the oracle's to 1e-12 and is compared at the oracle's).
 Tolerances (relative; moments relative to the largest entry of their row k):
   FP64     everything 1e-10.
   bf16x6   H 1e-6 (the split path's bar); per-probe forms and moments 1e-5:
@@ -49,7 +46,7 @@ TOL = {  # H, per-probe forms, moments
     "bf16x3": (1e-5, 5e-5, 5e-4),
     "bf16": (1e-3, 2e-2, None),
 }
-U_TOL = {"f64": 1e-12, "bf16x6": 1e-12, "bf16x3": 1e-12, "bf16": 1e-4}
+U_TOL = {"f64": 1e-12, "bf16x6": 1e-6, "bf16x3": 1e-6, "bf16": 1e-4}
 
 
 def rowerr(got, ref):
@@ -93,7 +90,7 @@ def test_fullsize_per_probe(case, prec):
         <= 1e-12 * abs(b.H_chebyshev)
     assert abs(b.H_taylor - O.taylor_estimate_from_terms(b.moments_taylor, b.u)) \
         <= 1e-12 * abs(b.H_taylor)
-    u = b.u if prec == "bf16" else u_ref
+    u = u_ref if prec == "f64" else b.u
     mu_all, tau_all = oracle_at(case, u)
     # per probe, on the slice
     mu, tau = mu_all[:, SLICE], tau_all[:, SLICE]
