@@ -196,14 +196,18 @@ vne_status slot_status(const double* hs, int check_trace) {
     return VNE_OK;
 }
 
-// The persistent power method needs cooperative launches (every CTA resident).
-bool power_sym_enabled(const vne_handle* h) {
+// The persistent power method (VNE_POWER_SYM=0: one launch per product).
+bool power_sym_enabled() {
     static int env = -1;
     if (env < 0) {
         const char* e = getenv("VNE_POWER_SYM");
         env = (e && e[0] == '0') ? 0 : 1;
     }
-    if (!env) return false;
+    return env != 0;
+}
+
+// Its single-launch form needs cooperative launches (every CTA resident).
+bool coop_launch_ok(const vne_handle* h) {
     int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) != cudaSuccess) {
         cudaGetLastError();
@@ -321,11 +325,14 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     if (!tc) pw_rdt = f64 ? 0 : 1;
     else if (pieces == 1) pw_rdt = 2;
     else pw_rdt = (!cplx && R.dtype == VNE_F64) ? 0 : 1;
-    // bf16 pieces, one trial, a single call: every product in one persistent
-    // launch over the upper triangle (VNE_POWER_SYM=0: one launch per product)
-    const bool use_sym = do_power && dense && tc && q == 1 && n >= 2048 && !out.ws &&
-                         !out.measure && power_sym_fits(rows_pad, h->sm_count) &&
-                         power_sym_enabled(h);
+    // bf16 pieces, one trial: the products over the upper triangle, in one
+    // persistent launch for a single call, phase by phase (plain launches on a
+    // quarter of the SMs, the same bits) in a batched call, which shares the
+    // GPU with the calls on its other streams
+    const bool sym_phased = out.ws != nullptr || out.measure || !coop_launch_ok(h);
+    const int sym_grid = sym_phased ? std::max(1, h->sm_count / 4) : h->sm_count;
+    const bool use_sym = do_power && dense && tc && q == 1 && n >= 2048 &&
+                         power_sym_fits(rows_pad, sym_grid) && power_sym_enabled();
     const int sym_pieces = pieces >= 2 ? 2 : 1;
     if (use_sym) pw_rdt = 2;
     const int pw_xdouble = dense ? (pw_rdt == 0 ? 1 : 0) : (f64 ? 1 : 0);
@@ -454,7 +461,9 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         c.prof_begin();
         if (use_sym) {
             c.launched(launch_power_sym(Rpc, sym_pieces, n, rows_pad, ldk, (const float*)x0,
-                                        p->power_iters, sc, symws, u_scale, h->sm_count, c.st));
+                                        p->power_iters, sc, symws, u_scale, sym_grid, sym_phased,
+                                        c.st));
+            if (sym_phased) h->launches += 2 * p->power_iters + 2;
         }
         for (int it = 0; it <= p->power_iters && c.ok() && !use_sym; ++it) {
             const int fin = it == p->power_iters;

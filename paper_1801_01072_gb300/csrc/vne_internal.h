@@ -97,16 +97,18 @@ cudaError_t launch_power_step_dense(const void* R, int rdtype /*0 f64,1 f32,2 bf
                                     double* sc, double* partial, unsigned int* counter,
                                     int final_step, double u_scale, int nblocks_cap,
                                     cudaStream_t st);
-// All t+1 products of the power method in one cooperative launch, R the sum
-// of `pieces` (1 or 2) bf16 pieces R[k] (rows_pad x ldk, symmetric; only the
-// upper-triangle 128 x 128 tiles are read), one trial, x0 the start vector;
-// writes SC_LAM, SC_U and SC_NORM as the per-product kernels do.
-// scratch: power_sym_scratch_bytes(rows_pad).
+// All t+1 products of the power method, R the sum of `pieces` (1 or 2) bf16
+// pieces R[k] (rows_pad x ldk, symmetric; only the upper-triangle 128 x 128
+// tiles are read), one trial, x0 the start vector; writes SC_LAM, SC_U and
+// SC_NORM as the per-product kernels do.  One cooperative launch of `grid`
+// CTAs, or (phased) 2t + 3 plain launches, one per phase, with the same
+// result bits for any grid.  scratch: power_sym_scratch_bytes(rows_pad).
 int64_t power_sym_scratch_bytes(int64_t rows_pad);
-bool power_sym_fits(int64_t rows_pad, int sm_count);  // size limits of launch_power_sym
+bool power_sym_fits(int64_t rows_pad, int grid);  // size limits of launch_power_sym
 cudaError_t launch_power_sym(const __nv_bfloat16* const* R, int pieces, int64_t n,
                              int64_t rows_pad, int64_t ldk, const float* x0, int t, double* sc,
-                             void* scratch, double u_scale, int sm_count, cudaStream_t st);
+                             void* scratch, double u_scale, int grid, bool phased,
+                             cudaStream_t st);
 cudaError_t launch_power_step_dia(const void* vals, int rdtype /*0 f64,1 f32*/, int64_t n,
                                   int64_t ld, int D, const void* x, void* y, int q, double* sc,
                                   double* partial, unsigned int* counter, int final_step,

@@ -448,6 +448,12 @@ __global__ void __launch_bounds__(256, 1) k_power_dense_bf16_stream(
 //   fixed order (deterministic) and writes y_b and the block's y.y (and,
 //   after the last product, x_hat.y and x_hat.x_hat) in FP64;
 //   grid barrier; every CTA forms 1/||y|| from the block sums.
+// The same kernel also runs phase by phase (SymArgs::phase >= 0), one launch
+// per phase and no grid barrier, for calls that share the GPU with others
+// (batched calls): phase 2p = the tiles of product p, 2p + 1 = its block
+// sums, 2t + 2 = the Rayleigh quotient.  Every value is computed by the same
+// code in the same order in both modes and whatever the grid size, so the
+// two give the same bits.
 // Every wait is bounded (kWaitNs): on expiry the CTA sets FLAG_TIMEOUT, waits
 // (bounded) for its copies in flight and returns.
 // ---------------------------------------------------------------------------
@@ -473,6 +479,7 @@ struct SymArgs {
     double* normb;   // nb x 3 block sums (y.y, x_hat.y, x_hat.x_hat)
     double* sc;
     double u_scale;
+    int phase;       // -1: every phase in one cooperative launch; else the one phase to run
 };
 
 __device__ __forceinline__ int sym_row_start(int I, int nb) { return I * nb - (I * (I - 1)) / 2; }
@@ -545,7 +552,12 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
     const int G = gridDim.x, c = blockIdx.x;
     const int nb = a.nb;
     const int rows = nb * kSymT;
-    const int mine = c < a.ntile ? (a.ntile - c + G - 1) / G : 0;
+    const bool coop = a.phase < 0;
+    const int p_lo = coop ? 0 : a.phase >> 1;
+    const int p_hi = coop ? a.t : min(a.phase >> 1, a.t);
+    const bool tiles_on = (coop || (a.phase & 1) == 0) && p_lo <= p_hi;
+    const bool sums_on = coop || (a.phase & 1) == 1;
+    const int mine = tiles_on && c < a.ntile ? (a.ntile - c + G - 1) / G : 0;
     for (int j = tid; j < mine; j += blockDim.x) {
         const int tau = c + j * G;
         int lo = 0, hi = nb - 1;  // the row I whose tiles hold tau
@@ -563,7 +575,9 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
         flag_sh = 0;
     }
     __syncthreads();
-    const int total = (a.t + 1) * mine;
+    // 1/||x|| of product p_lo's input, stored by its tile phase for its sum phase
+    float* inv_slot = reinterpret_cast<float*>(a.bar + 1);
+    const int total = tiles_on && p_hi >= p_lo ? (p_hi - p_lo + 1) * mine : 0;
     uint64_t pol = 0;
     if (tid == 0) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     auto issue = [&](int item) {
@@ -579,13 +593,25 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
         for (; issued < NS && issued < total; ++issued) issue(issued);
 
     float inv = (float)(1.0 / sqrt((double)a.n));  // ||x_0||^2 = n
+    if (!coop && p_lo > 0 && p_lo <= a.t) {
+        if (tiles_on) {  // from the block sums of product p_lo - 1, as below
+            double part = 0.0;
+            for (int b = tid; b < nb; b += blockDim.x) part += __ldcg(a.normb + (size_t)b * 3);
+            inv = (float)(1.0 / sqrt(sym_block_sum(part, red_sh)));
+            if (c == 0 && tid == 0) *inv_slot = inv;
+        } else {
+            inv = __ldcg(inv_slot);
+        }
+    }
     bool ok = true;
     int consumed = 0;
-    for (int p = 0; p <= a.t && ok; ++p) {
+    for (int p = p_lo; p <= p_hi && ok; ++p) {
         const float* xsrc = p == 0 ? a.x0 : a.ybuf + (size_t)((p - 1) & 1) * rows;
         float* ydst = a.ybuf + (size_t)(p & 1) * rows;
-        // x_hat of this product, whole vector, in shared memory
-        if (p == 0) {
+        // x_hat of this product, whole vector, in shared memory (the sums use
+        // it only after the last product)
+        if (!tiles_on && p != a.t) {
+        } else if (p == 0) {
             for (int i = tid; i < rows; i += blockDim.x) xsm[i] = i < a.n ? a.x0[i] * inv : 0.f;
         } else {
             const float4* s4 = reinterpret_cast<const float4*>(xsrc);
@@ -597,8 +623,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
             }
         }
         __syncthreads();
-        for (int j = 0; j < mine; ++j) {
-            const int item = p * mine + j;
+        for (int j = 0; j < mine && tiles_on; ++j) {
+            const int item = (p - p_lo) * mine + j;
             const int st = item % NS;
             const uint32_t tk = tl[j];
             const int I = (int)(tk >> 16), K = (int)(tk & 0xFFFFu);
@@ -672,8 +698,9 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
             }
         }
         if (!ok) break;
+        if (!sums_on) break;
         // every partial of product p is written
-        if (!sym_grid_sync(a.bar, (unsigned)(2 * p + 1) * (unsigned)G, &flag_sh)) {
+        if (coop && !sym_grid_sync(a.bar, (unsigned)(2 * p + 1) * (unsigned)G, &flag_sh)) {
             ok = false;
             break;
         }
@@ -728,6 +755,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
             }
             __syncthreads();  // colsm reused
         }
+        if (!coop) break;
         // every block of product p is final
         if (!sym_grid_sync(a.bar, (unsigned)(2 * p + 2) * (unsigned)G, &flag_sh)) {
             ok = false;
@@ -750,7 +778,7 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
         }
         return;
     }
-    if (c == 0) {
+    if (c == 0 && (coop || a.phase == 2 * a.t + 2)) {
         // Rayleigh quotient of the last iterate (Algorithm alg:power)
         double yy = 0.0, xy = 0.0, xx = 0.0;
         for (int b = tid; b < nb; b += blockDim.x) {
@@ -781,22 +809,22 @@ int64_t power_sym_scratch_bytes(int64_t rows_pad) {
     return ntile * 2 * kSymT * 4 + 2 * rows_pad * 4 + nb * 3 * 8 + 4 * 256;
 }
 
-bool power_sym_fits(int64_t rows_pad, int sm_count) {
-    if (rows_pad % kSymT != 0 || rows_pad > kSymMaxRows || sm_count < 1) return false;
+bool power_sym_fits(int64_t rows_pad, int grid) {
+    if (rows_pad % kSymT != 0 || rows_pad > kSymMaxRows || grid < 1) return false;
     const int64_t nb = rows_pad / kSymT, ntile = nb * (nb + 1) / 2;
-    const int64_t G = ntile < sm_count ? ntile : sm_count;
+    const int64_t G = ntile < grid ? ntile : grid;
     return (ntile + G - 1) / G <= kSymMaxTiles;
 }
 
 cudaError_t launch_power_sym(const __nv_bfloat16* const* R, int pieces, int64_t n,
                              int64_t rows_pad, int64_t ldk, const float* x0, int t, double* sc,
-                             void* scratch, double u_scale, int sm_count, cudaStream_t st) {
-    if (!power_sym_fits(rows_pad, sm_count) || (ldk % 8) != 0 || t < 0 || pieces < 1 ||
-        pieces > 2)
+                             void* scratch, double u_scale, int grid, bool phased,
+                             cudaStream_t st) {
+    if (!power_sym_fits(rows_pad, grid) || (ldk % 8) != 0 || t < 0 || pieces < 1 || pieces > 2)
         return cudaErrorInvalidValue;
     const int nb = (int)(rows_pad / kSymT);
     const int ntile = nb * (nb + 1) / 2;
-    const int G = ntile < sm_count ? ntile : sm_count;
+    const int G = ntile < grid ? ntile : grid;
     SymMaps maps;
     for (int pc = 0; pc < 2; ++pc)
         if (!tma_map_bf16_plain(&maps.R[pc], R[pc < pieces ? pc : 0], ldk, rows_pad, ldk, kSymT, kSymT))
@@ -820,7 +848,8 @@ cudaError_t launch_power_sym(const __nv_bfloat16* const* R, int pieces, int64_t 
     a.normb = reinterpret_cast<double*>(take((size_t)nb * 3 * 8));
     a.sc = sc;
     a.u_scale = u_scale;
-    cudaError_t e = cudaMemsetAsync(a.bar, 0, 4, st);
+    a.phase = -1;
+    cudaError_t e = phased ? cudaSuccess : cudaMemsetAsync(a.bar, 0, 4, st);
     if (e != cudaSuccess) return e;
     static int static_smem = -1;
     if (static_smem < 0) {
@@ -846,6 +875,17 @@ cudaError_t launch_power_sym(const __nv_bfloat16* const* R, int pieces, int64_t 
     cfg.blockDim = dim3(kSymThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
+    if (phased) {  // one plain launch per phase: tiles (ring), block sums, Rayleigh quotient
+        for (int ph = 0; ph <= 2 * t + 2 && e == cudaSuccess; ++ph) {
+            const bool tiles = (ph & 1) == 0 && ph <= 2 * t;
+            a.phase = ph;
+            a.stages = tiles ? stages : 0;
+            cfg.gridDim = dim3(ph == 2 * t + 2 ? 1u : (unsigned)G);
+            cfg.dynamicSmemBytes = tiles ? smem : 1024 + (size_t)rows_pad * 4;
+            e = cudaLaunchKernelEx(&cfg, k_power_sym, maps, a);
+        }
+        return e;
+    }
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barrier needs it
     at[0].val.cooperative = 1;

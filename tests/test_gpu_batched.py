@@ -88,3 +88,18 @@ def test_autotune_picks_a_candidate_and_results_hold():
     G = rng.probes(1024, 32, 2, "gaussian")
     ref = O.chebyshev_estimate_from_moments(O.chebyshev_moments(R, G, res.u, 10), res.u)
     assert abs(res.H - ref) <= 1e-3 * abs(ref)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_batched_large_matrices_equal_single_calls(precision):
+    """n >= 2048: the single calls run the power method's products in one
+    cooperative launch, the batched call phase by phase on a smaller grid;
+    the bits agree (every sum has a fixed order whatever the grid)."""
+    sizes = [2048, 2300, 3001, 700, 4096]
+    ms = mats(sizes, seed0=80)
+    m, s, seed = 10, 8, 5
+    hc, _, u = vne.entropy_batched([t for t, _, _ in ms], m, s, seed=seed, probe="gaussian",
+                                   precision=precision)
+    for i, (t, R, p) in enumerate(ms):
+        one = vne.entropy_chebyshev(t, m, s, seed=seed, probe="gaussian", precision=precision)
+        assert (hc[i], u[i]) == (one.H, one.u), (i, sizes[i], hc[i], one.H, u[i], one.u)
