@@ -112,16 +112,67 @@ def make_workload(name):
 # --------------------------------------------------------------------------
 
 class Clocks:
+    """SM clocks and clock-event reasons sampled during the timed region:
+    NVML queries (read-only) every 5 ms from a helper thread, matched to the
+    CUDA device by PCI bus id; nvidia-smi at 200 ms when NVML is missing."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_slowdown"}
 
-    def __init__(self, device_index=0):
+    def __init__(self, device_index=0, period_s=0.005):
         self.p = None
+        self.th = None
+        self.nv = None
+        self.samples = []
+        self.period = period_s
         self.path = os.path.join(tempfile.gettempdir(), f"vne_clocks_{os.getpid()}.csv")
         self.dev = device_index
 
+    def _nvml(self):
+        import ctypes as C
+        try:
+            lib = C.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = C.c_void_p()
+            ok = False
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(self.dev)
+                bus = "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(h)) == 0
+            except Exception:
+                ok = False
+            if not ok and lib.nvmlDeviceGetHandleByIndex_v2(self.dev, C.byref(h)) != 0:
+                return None
+            rs = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            return lib, h, rs
+        except Exception:
+            return None
+
+    def _loop(self):
+        import ctypes as C
+        lib, h, rs = self.nv
+        clk, mx, why = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0 and
+                    rs(h, C.byref(why)) == 0):
+                self.samples.append((clk.value, mx.value, why.value))
+            self.stop.wait(self.period)
+
     def __enter__(self):
+        import threading
+        self.nv = self._nvml()
+        if self.nv is not None:
+            self.stop = threading.Event()
+            self.th = threading.Thread(target=self._loop, daemon=True)
+            self.th.start()
+            return self
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -133,6 +184,9 @@ class Clocks:
         return self
 
     def __exit__(self, *a):
+        if self.th is not None:
+            self.stop.set()
+            self.th.join(timeout=5)
         if self.p is not None:
             self.p.terminate()
             try:
@@ -142,26 +196,36 @@ class Clocks:
             self.f.close()
 
     def summary(self):
-        if self.p is None or not os.path.exists(self.path):
-            return None
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1].split()[0]))
-                mx.append(float(parts[2].split()[0]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        if self.th is not None:
+            for c, m, w in self.samples:
+                sm.append(float(c))
+                mx.append(float(m))
+                for bit, nm in self.REASONS.items():
+                    if w & bit:
+                        reasons.add(nm)
+            src = f"NVML every {self.period * 1e3:.0f} ms"
+        else:
+            if self.p is None or not os.path.exists(self.path):
+                return None
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1].split()[0]))
+                    mx.append(float(parts[2].split()[0]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            src = "nvidia-smi every 200 ms"
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm), "source": src}
 
 
 # --------------------------------------------------------------------------

@@ -22,7 +22,8 @@
 //   warp 0 lane 0 : TMA producer over a ring of `stages` buffers
 //   warp 1        : TMEM allocation; lane 0 issues tcgen05.mma (M=128, N=BN,
 //                   K=16 per instruction) and commits to the ring's "empty"
-//                   barriers and finally to the "accumulator full" barrier
+//                   barriers, finally to the "accumulator full" barrier and
+//                   (split K) to the peer's "ring idle" barrier
 //   all 8 warps   : epilogue; warp w reads TMEM lanes 32*(w%4).. (its 32 rows)
 //                   and the column chunks of parity w/4.
 // Every wait on an mbarrier is bounded by a %globaltimer deadline; on
@@ -103,6 +104,14 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
+        : "memory");
+}
+// Commit whose arrival goes to the mbarrier at a shared::cluster address (a
+// peer CTA's, from mapa) once this thread's MMAs are done.
+__device__ __forceinline__ void tc_commit_remote(uint32_t cluster_addr) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            cluster_addr)
         : "memory");
 }
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -355,14 +364,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t* empty_bar = full_bar + a.stages;
     uint64_t* accum_bar = empty_bar + a.stages;
     uint64_t* epi_bar = accum_bar + 1;  // epilogue operands landed
-    uint64_t* idle_bar = epi_bar + 1;   // split K: the peer's ring is idle (1 arrival)
+    uint64_t* idle_bar = epi_bar + 1;   // split K: the peer's receive area is idle (1 arrival)
     uint64_t* recv_bar = idle_bar + 1;  // split K: the peer's half has landed (1 per warp)
     uint64_t* accf_bar = recv_bar + 1;  // flush: TMEM buffer b holds a finished chunk [2]
     uint64_t* acce_bar = accf_bar + 2;  // flush: buffer b has been added to the sum [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce_bar + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][BN]
-    float* gstash = red + 4 * a.BN;                         // [2 warps][32 cols][32 lanes]
+    float* gstash = red + 4 * a.BN;  // [2 chunks][2 warps][32 cols][32 lanes]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM;
@@ -397,6 +406,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.R[0])) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.Y[0])) : "memory");
+        // the epilogue's maps too: an unfetched map costs its first copy ~1 us
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.Yp)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.Yp2)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -504,6 +516,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (timed_out) *abort_flag = 1;
         tc_commit(accum_bar);  // all issued MMAs (possibly none) complete -> arrive
+        if (a.ksplit > 1) {
+            // Split K: the peer writes its half of the accumulator into this
+            // ring once these MMAs are done; the commit's arrival in the
+            // peer's barrier says so as soon as they are (a thread's arrive
+            // after the accumulator wait was measured 0.45 us slower).  A CTA
+            // that stopped early signals with a plain arrive instead.
+            const uint32_t rb = mapa_peer(smem_u32(idle_bar), (uint32_t)(1 - kz));
+            if (!timed_out && rank_ok) tc_commit_remote(rb);
+            else mbar_remote_arrive(rb);
+        }
     } else if (FLUSH && warp >= 4 && rank_ok) {
         // ---------------- chunk sums (flush) ----------------
         // warp 4 + g reads TMEM lanes 32g..32g+31: the rows of lane group g
@@ -574,21 +596,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                               : __ldg(a.G + (int64_t)(c % a.s) * a.n + row);
         }
     };
-    // G does not depend on this step: the first chunk's values are requested
-    // now, so their latency hides behind the mainloop.  Warps 0 and 1 come
-    // here only at the mainloop's end (their lane 0 produces and issues), so
-    // warps 4 and 5, which own the same rows, stage those warps' first chunk
-    // in shared memory; loads still in flight in warps 0 and 1 would hold up
-    // their next shared-memory access and the cluster barrier behind it.
-    // (Without room for that stash, gst = 0, warps 0 and 1 load their own.)
+    // G does not depend on this step: the values of a warp's first two chunks
+    // are requested now, so their latency hides behind the mainloop (measured:
+    // 0.7 us per launch for the second chunk's).  Warps 0 and 1 come here only
+    // at the mainloop's end (their lane 0 produces and issues), so warps 4 and
+    // 5, which own the same rows, stage those warps' two chunks in shared
+    // memory; loads still in flight in warps 0 and 1 would hold up their next
+    // shared-memory access and the cluster barrier behind it.  (Without room
+    // for that stash, gst = 0, warps 0 and 1 load their own.)
     float gv[32];
     if ((warp >= 2 || !a.gst) && ck_first < ck_hi) load_g(ck_first, gv);
+    float g2[32];
+    const bool early2 = (warp >= 2 || a.gst) && ck_first + 2 < ck_hi;
+    if (early2 && warp >= 2) load_g(ck_first + 2, g2);
     if (a.gst && (warp == 4 || warp == 5)) {
-        float gs[32];
-        load_g(ck_lo, gs);  // ck_lo < ck_hi: every CTA owns at least one chunk
-        float* dst = gstash + (warp - 4) * 32 * 32 + lane;
+        // ck_lo < ck_hi: every CTA owns at least one chunk
+        for (int j = 0; j < 2 && ck_lo + 2 * j < ck_hi; ++j) {
+            float gs[32];
+            load_g(ck_lo + 2 * j, gs);
+            float* dst = gstash + (j * 2 + warp - 4) * 32 * 32 + lane;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) dst[q * 32] = gs[q];
+            for (int q = 0; q < 32; ++q) dst[q * 32] = gs[q];
+        }
         named_bar_arrive(1, 128);
     }
 
@@ -606,6 +635,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool aborted = (*abort_flag != 0) || !have_acc;
     tc_fence_after();
     __syncwarp();
+    const uint32_t peer = (uint32_t)(1 - kz);
     const uint32_t zcol = FLUSH ? (uint32_t)(2 * a.BN) : 0u;  // columns holding Z
 
     // Y_{t-1} and Y_{t-2} of this CTA's own chunks, [chunk][2][32 cols][128 rows]
@@ -643,22 +673,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // Receive buffer of the split-K exchange: float4 slot (chunk*8 + q)*128 + r
     // holds columns 4q..4q+3 of row r, so a warp's 16-byte stores and loads
     // cover 512 contiguous bytes.
-    // The pair signals through mbarriers in each other's shared memory: thread
-    // 0 tells the peer that this ring is idle (its MMAs are complete), every
-    // warp tells it when its part of the half has been written.  Both signals
-    // are sent also by a CTA that aborted, and every CTA waits for the peer's
-    // writes before it leaves, so no wait depends on the other CTA's state.
+    // The pair signals through mbarriers in each other's shared memory: the
+    // MMA issuer's commit says that the receive area is idle; every warp says
+    // when its part of the half has been written (a release arrive after its
+    // stores).  Both signals are sent also by a CTA that aborted, and every
+    // CTA waits for the peer's writes before it leaves, so no wait depends on
+    // the other CTA's state.
     const float4* recv = reinterpret_cast<const float4*>(smem);
     if (a.ksplit > 1) {
-        const uint32_t peer = (uint32_t)(1 - kz);
-        if (threadIdx.x == 0) mbar_remote_arrive(mapa_peer(smem_u32(idle_bar), peer));
+        // the first chunk for the peer is read from TMEM while its signal is awaited
+        const int ck0 = (int)peer * half + chalf, ck_end = (int)peer * half + half;
+        uint32_t r[32];
+        if (!aborted && ck0 < ck_end) {
+            TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck0 * 32), r);
+            tmem_wait_ld();
+        }
         const bool peer_idle = mbar_wait_cluster(idle_bar, 0u);
         if (!aborted && peer_idle) {
             const uint32_t rbase = mapa_peer(smem_u32(smem), peer);
-            for (int ck = (int)peer * half + chalf; ck < (int)peer * half + half; ck += 2) {
-                uint32_t r[32];
-                TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck * 32), r);
-                tmem_wait_ld();
+            for (int ck = ck0; ck < ck_end; ck += 2) {
+                if (ck != ck0) {
+                    TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck * 32), r);
+                    tmem_wait_ld();
+                }
                 const uint32_t dst =
                     rbase + (uint32_t)(((ck - (int)peer * half) * 8 * TC_BM + rg * 32 + lane) * 16);
 #pragma unroll
@@ -751,10 +788,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         red[rg * a.BN + ck * 32 + lane] = v[0];
     };
     if (a.gst && warp < 2) {
-        named_bar_sync(1, 128);  // warps 4 and 5 have staged this warp's first G chunk
+        named_bar_sync(1, 128);  // warps 4 and 5 have staged this warp's G chunks
         const float* src = gstash + warp * 32 * 32 + lane;
 #pragma unroll
         for (int q = 0; q < 32; ++q) gv[q] = src[q * 32];
+        if (early2) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) g2[q] = src[2 * 32 * 32 + q * 32];
+        }
     }
     if (!aborted && ops_ready) {
         // operands in smem; the next chunk's G is requested while this one runs
@@ -762,8 +803,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t r[32];
             TMEM_LD32(tmem_base + ((uint32_t)(rg * 32) << 16) + zcol + (uint32_t)(ck * 32), r);
             const bool more = ck + 2 < ck_hi;
+            const bool have_early = early2 && ck == ck_first;
             float gn[32];
-            if (more) load_g(ck + 2, gn);
+            if (more && !have_early) load_g(ck + 2, gn);
             const float* ob = ops + (size_t)((ck - ck_lo) * 2) * 32 * TC_BM + rg * 32 + lane;
             tmem_wait_ld();
             finish_chunk(
@@ -771,7 +813,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 [&](int q) { return ob[32 * TC_BM + q * TC_BM]; });
             if (more) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) gv[q] = gn[q];
+                for (int q = 0; q < 32; ++q) gv[q] = have_early ? g2[q] : gn[q];
             }
         }
     } else if (!aborted) {
@@ -1058,7 +1100,7 @@ cudaError_t launch_tc_step(const TcStep& s, int sm_count, cudaStream_t st) {
     const uint32_t stage_bytes = (uint32_t)(TC_BM * bk * 2 + BN * bk * 2) * (uint32_t)P;
     // barriers, slot, flag and red; then (gst) the staged G of two warps
     const size_t tail_min = 2 * 8 * 16 + 16 + 16 + 4 * 256 * 4;
-    const size_t stash = 2 * 32 * 32 * 4;
+    const size_t stash = 2 * 2 * 32 * 32 * 4;  // [2 chunks][2 warps][32 cols][32 lanes]
     const size_t max_smem = 227 * 1024;
     int gst = 1;
     int stages = (int)((max_smem - 1024 - tail_min - stash) / stage_bytes);
