@@ -1149,11 +1149,14 @@ def run_gpu(args):
         achieved = bytes_est * args.steps / (k_ms / 1e3) / 1e9 if k_ms > 0 else None
         peak = peak_value(pk, "hbm_gbs")
         # DRAM bytes of one general step at n = 2e6 (ncu), scaled to this n
-        tr = profiled_traffic("k_dia_step_band_n2e6.md", "vne_dia.cu")
+        # (the FP32 path with s = 64 runs the bulk-copy kernel of vne_dia_tma.cu)
+        kname = "k_dia_step_tma" if prec == "f32" else "k_dia_step"
+        tr = profiled_traffic("k_dia_step_tma_band_n2e6.md", "vne_dia_tma.cu") \
+            if prec == "f32" else None
         traffic = int(tr * n / 2e6) if tr else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if (achieved and peak) else None, "traffic": traffic,
-                "kernel": "k_dia_step", "launches": k_n,
+                "kernel": kname, "launches": k_n,
                 "avg_launch_us": k_ms / max(k_n, 1) * 1e3, "peak_source": pk_src + " hbm"}
 
     cpu = None

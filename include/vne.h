@@ -175,6 +175,24 @@ vne_status vne_entropy_taylor(vne_handle* h, const vne_matrix* R, const vne_para
                               double* H_out, double* moments_out, double* u_out,
                               void* stream);
 
+/* Algorithms 1b and 1a on probes the caller gives, instead of the seed's
+ * stream (Lemma thm:trace holds for any probe law with E[g g^T] = I; a single
+ * probe g gives the quadratic form g^T f(R) g of Section 3 / Section 2, which
+ * is how edge cases such as a unit vector or an eigenvector are checked).
+ *   G : device, s probe vectors as an n x s row-major block (G[i*s + j] =
+ *       g_j[i]), FP64 when p->precision is VNE_PREC_F64, else FP32 (the
+ *       type of the path's probe block); n is R's order (for a complex R, its
+ *       complex order).  Caller-owned, read during the call only.
+ * Everything else as in vne_entropy_chebyshev / vne_entropy_taylor: p->probe
+ * and p->probe_offset are ignored, p->seed still seeds the power method.
+ * G == NULL returns VNE_ERR_INVALID_ARG. */
+vne_status vne_entropy_chebyshev_probes(vne_handle* h, const vne_matrix* R, const void* G,
+                                        const vne_params* p, double* H_out, double* moments_out,
+                                        double* u_out, void* stream);
+vne_status vne_entropy_taylor_probes(vne_handle* h, const vne_matrix* R, const void* G,
+                                     const vne_params* p, double* H_out, double* moments_out,
+                                     double* u_out, void* stream);
+
 /* Both estimators on the same R, probes and u: one power method, and the two
  * recurrences share every pass over R (their probe blocks are placed side by
  * side, 2s columns).  Outputs as in the two calls above (moment buffers may be

@@ -30,7 +30,7 @@ from ._lib import VneError
 
 __all__ = ["entropy_chebyshev", "entropy_taylor", "entropy_both", "lambda_max", "probe_block",
            "entropy_projection", "sketch_block", "ProjectionResult", "entropy_batched", "autotune",
-           "Handle", "Result", "BothResult", "VneError", "suggest_m", "load", "combine_moments"]
+           "Handle", "Result", "BothResult", "entropy_with_probes", "VneError", "suggest_m", "load", "combine_moments"]
 
 
 def load():
@@ -215,6 +215,41 @@ def entropy_taylor(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",
     return _estimate("vne_entropy_taylor", R, m, s, seed, probe, precision, power_iters,
                      power_trials, u_scale, u, check_trace, moments, layout, stream,
                      probe_offset)
+
+
+def entropy_with_probes(R, G, m: int, method: str = "chebyshev", seed: int = 0,
+                        precision: str = "f64", power_iters: int = 30, power_trials: int = 1,
+                        u_scale: float = 1.0, u: float | None = None, check_trace: bool = False,
+                        moments: bool = False, layout: str = "dense", stream=None) -> Result:
+    """Algorithm 1b (method "chebyshev") or 1a ("taylor") on the caller's
+    probes: G is a CUDA tensor of shape (n, s) (column j = probe g_j), float64
+    for precision "f64", else float32.  seed only seeds the power method."""
+    import torch
+
+    if method not in ("chebyshev", "taylor"):
+        raise ValueError(method)
+    if not (isinstance(G, torch.Tensor) and G.is_cuda and G.dim() == 2):
+        raise ValueError("G must be a 2-D CUDA tensor (n, s)")
+    want = torch.float64 if precision == "f64" else torch.float32
+    if G.dtype != want:
+        raise ValueError(f"G must be {want} for precision {precision!r}")
+    G = G.contiguous()
+    mat, keep, dev = _matrix(R, layout)
+    if G.shape[0] != mat.n:
+        raise ValueError("G must have one row per row of R")
+    s = G.shape[1]
+    h = _handle(dev)
+    p = _params(m, s, seed, "rademacher", precision, power_iters, power_trials, u_scale, u,
+                check_trace)
+    H = C.c_double()
+    uo = C.c_double()
+    mom = np.zeros((m + 1, s), dtype=np.float64) if moments else None
+    fn = "vne_entropy_chebyshev_probes" if method == "chebyshev" else "vne_entropy_taylor_probes"
+    st = getattr(h.lib, fn)(h.h, C.byref(mat), C.c_void_p(G.data_ptr()), C.byref(p), C.byref(H),
+                            _dptr(mom), C.byref(uo), _stream(dev, stream))
+    h.check(st, fn)
+    del keep
+    return Result(H.value, uo.value, mom)
 
 
 def entropy_both(R, m: int, s: int, seed: int = 0, probe: str = "rademacher",

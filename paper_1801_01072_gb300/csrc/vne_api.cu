@@ -69,6 +69,9 @@ struct Outputs {
     size_t* measured = nullptr;
     char* ws = nullptr;
     double* host_slot = nullptr;
+    // explicit probes (device, n x s row-major, FP64 for F64 precision, else
+    // FP32), replacing the seed's stream
+    const void* probes = nullptr;
 };
 
 struct DeviceGuard {
@@ -292,12 +295,26 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     const double u_scale = p->u_scale > 0.0 ? p->u_scale : 1.0;
     const int T_steps = mode == MODE_POWER ? 0 : (has_tay ? m + 1 : m);
     const int D = dense ? 0 : R.n_diags;
+    // probes drawn from the seed's stream, or the caller's block
+    const int pkind = out.probes ? PROBE_GIVEN : p->probe;
 
     // geometry of each path
     const int64_t rows_pad = tc ? round_up(n, tc_tile_m()) : n;
     const int64_t ldk = tc ? round_up(n, tc_tile_k()) : n;
     const int S_pad = (int)round_up(S, 32);
     int splitk = 1, ntiles = 1, ntiles0 = 1, dia_grid = 0;
+    // The banded operand is the caller's band when its type is the computed
+    // one (or the device copy of a host band, whose rows keep the caller's
+    // ld), else a converted copy with ld = n; the bulk-copy step needs each
+    // diagonal to start on a 16-byte boundary.
+    int dia_band_aligned = 0;
+    if (!dense) {
+        const bool same_type = R.dtype == (f64 ? VNE_F64 : VNE_F32);
+        const int64_t ld_op = same_type ? R.ld : n;
+        const bool base_ok = !same_type || R.memory == VNE_MEM_HOST ||
+                             ((uintptr_t)R.data & 15) == 0;
+        dia_band_aligned = (base_ok && (ld_op * (f64 ? 8 : 4)) % 16 == 0) ? 1 : 0;
+    }
     int rows_per_tile0 = 256;
     if (mode != MODE_POWER) {
         if (dense && !tc) {
@@ -307,7 +324,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             rows_per_tile0 = tc_tile_m();
             ntiles = ntiles0 = (int)(rows_pad / tc_tile_m());
         } else {
-            dia_grid = dia_step_grid(f64, D, n, S, s, h->sm_count);
+            dia_grid = dia_step_grid(f64, D, n, S, s, h->sm_count, dia_band_aligned);
             if (dia_grid < 1) return VNE_ERR_UNSUPPORTED;
             ntiles = dia_grid;
             rows_per_tile0 = 4096;
@@ -372,7 +389,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         *part = *mom_c = *mom_t = nullptr;
         if (mode == MODE_POWER) return;
         const size_t ms = tc ? 4 : vt;
-        if (!dense && p->probe == VNE_RADEMACHER)
+        if (!dense && pkind == VNE_RADEMACHER)
             *bits = b.take<uint64_t>((size_t)n * ((s + 63) / 64));
         else
             *G = b.take<char>((size_t)n * s * ms);
@@ -495,23 +512,25 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         if (dense) {
             if (f64)
                 c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, 0, 0,
-                                                     n, S, s, p->probe, p->seed, P, 256, c.st,
-                                                     R.n, p->probe_offset));
+                                                     n, S, s, pkind, p->seed, P, 256, c.st,
+                                                     R.n, p->probe_offset,
+                                                     (const double*)out.probes));
             else
                 c.launched(launch_dense_init<float>((float*)G, (float*)Yb0, sh[0], pieces, ldk, n, S, s,
-                                                    p->probe, p->seed, P, rows_per_tile0, c.st,
-                                                    R.n, p->probe_offset));
+                                                    pkind, p->seed, P, rows_per_tile0, c.st,
+                                                    R.n, p->probe_offset,
+                                                    (const float*)out.probes));
         } else {
             const int Wd = (s + 63) / 64;
             if (f64)
                 c.launched(launch_dia_init<double>((double*)G, bits, Wd,
                                                    bits ? nullptr : (double*)Yb0, n, S, s,
-                                                   p->probe, p->seed, P, rows_per_tile0, c.st,
-                                                   p->probe_offset));
+                                                   pkind, p->seed, P, rows_per_tile0, c.st,
+                                                   p->probe_offset, (const double*)out.probes));
             else
                 c.launched(launch_dia_init<float>((float*)G, bits, Wd, bits ? nullptr : (float*)Yb0,
-                                                  n, S, s, p->probe, p->seed, P, rows_per_tile0,
-                                                  c.st, p->probe_offset));
+                                                  n, S, s, pkind, p->seed, P, rows_per_tile0,
+                                                  c.st, p->probe_offset, (const float*)out.probes));
         }
         void* Yb[3] = {Yb0, Yb1, Yb2};
         // tensor-core steps are timed as one span (consecutive launches overlap
@@ -578,12 +597,14 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
                     c.launched(launch_dia_step<double>((const double*)Rk, ldr, D, n,
                                                        (const double*)Yp, (const double*)Yp2,
                                                        (double*)Yn, (const double*)G, bits, Wd, S,
-                                                       s, cols, sc, P, t, dia_grid, c.st));
+                                                       s, cols, sc, P, t, dia_grid, c.st,
+                                                       dia_band_aligned));
                 else
                     c.launched(launch_dia_step<float>((const float*)Rk, ldr, D, n,
                                                       (const float*)Yp, (const float*)Yp2,
                                                       (float*)Yn, (const float*)G, bits, Wd, S, s,
-                                                      cols, sc, P, t, dia_grid, c.st));
+                                                      cols, sc, P, t, dia_grid, c.st,
+                                                      dia_band_aligned));
                 c.prof_end(2);
             }
         }
@@ -989,6 +1010,30 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
     o.mom_taylor = moments_taylor;
     o.u = u_out;
     return run(h, R, p, MODE_BOTH, o, stream);
+}
+
+vne_status vne_entropy_chebyshev_probes(vne_handle* h, const vne_matrix* R, const void* G,
+                                        const vne_params* p, double* H_out, double* moments_out,
+                                        double* u_out, void* stream) {
+    if (!H_out || !G) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.H_cheb = H_out;
+    o.mom_cheb = moments_out;
+    o.u = u_out;
+    o.probes = G;
+    return run(h, R, p, MODE_CHEB, o, stream);
+}
+
+vne_status vne_entropy_taylor_probes(vne_handle* h, const vne_matrix* R, const void* G,
+                                     const vne_params* p, double* H_out, double* moments_out,
+                                     double* u_out, void* stream) {
+    if (!H_out || !G) return VNE_ERR_INVALID_ARG;
+    Outputs o;
+    o.H_taylor = H_out;
+    o.mom_taylor = moments_out;
+    o.u = u_out;
+    o.probes = G;
+    return run(h, R, p, MODE_TAYLOR, o, stream);
 }
 
 namespace {

@@ -303,8 +303,9 @@ static int grid_hb(int64_t n, int ncols, int sm_count) {
 
 // Persistent grid of the banded step (resident CTAs x SMs, capped by the
 // number of row chunks); the caller sizes the moment partials with it.
-int dia_step_grid(int is_double, int D, int64_t n, int ncols, int s, int sm_count) {
-    (void)s;  // the kernel does not depend on the probe count beyond ncols
+int dia_step_grid(int is_double, int D, int64_t n, int ncols, int s, int sm_count,
+                  int band_aligned) {
+    if (dia_tma_ok(is_double, D, n, ncols, s, band_aligned)) return dia_tma_grid(D, n, ncols, sm_count);
     const int hb = dia_supported_halfbw(D);
     if (is_double) {
         switch (hb) {
@@ -330,7 +331,12 @@ template <typename T>
 cudaError_t launch_dia_step(const T* vals, int64_t ld, int D, int64_t n, const T* Yprev,
                             const T* Yprev2, T* Ynew, const T* G, const uint64_t* bits, int Wd,
                             int S, int s, StepCols cols, const double* sc, Partials P, int t,
-                            int nblocks, cudaStream_t st) {
+                            int nblocks, cudaStream_t st, int band_aligned) {
+    if constexpr (sizeof(T) == 4) {
+        if (dia_tma_ok(0, D, n, S, s, band_aligned))
+            return launch_dia_step_tma(vals, ld, D, n, Yprev, Yprev2, Ynew, G, bits, Wd, S, s, cols,
+                                       sc, P, t, nblocks, st);
+    }
     switch (dia_supported_halfbw(D)) {
         case 1: return launch_hb<T, 1>(vals, ld, D, n, Yprev, Yprev2, Ynew, G, bits, Wd, S, s, cols, sc, P, t, nblocks, st);
         case 2: return launch_hb<T, 2>(vals, ld, D, n, Yprev, Yprev2, Ynew, G, bits, Wd, S, s, cols, sc, P, t, nblocks, st);
@@ -343,10 +349,10 @@ cudaError_t launch_dia_step(const T* vals, int64_t ld, int D, int64_t n, const T
 template cudaError_t launch_dia_step<float>(const float*, int64_t, int, int64_t, const float*,
                                             const float*, float*, const float*, const uint64_t*,
                                             int, int, int, StepCols, const double*, Partials, int,
-                                            int, cudaStream_t);
+                                            int, cudaStream_t, int);
 template cudaError_t launch_dia_step<double>(const double*, int64_t, int, int64_t, const double*,
                                              const double*, double*, const double*,
                                              const uint64_t*, int, int, int, StepCols,
-                                             const double*, Partials, int, int, cudaStream_t);
+                                             const double*, Partials, int, int, cudaStream_t, int);
 
 }  // namespace vne

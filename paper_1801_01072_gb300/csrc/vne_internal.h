@@ -40,18 +40,21 @@ cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint
 // Rows i < probe_n draw counter j*probe_n + i; rows probe_n <= i < n are zero
 // (the lower half of the probes [g; 0] of a Hermitian embedding).
 // Ysh[k], k < pieces (pieces 0: none): the bf16 pieces of Y0 (see launch_tc_step).
+// Probe j of the call is probe j0 + j of the seed's stream; kind PROBE_GIVEN
+// copies the caller's probes Gin (probe_n x s, row-major, the path's type).
+constexpr int PROBE_GIVEN = 2;
 template <typename T>
-// Probe j of the call is probe j0 + j of the seed's stream.
 cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                              int rows_per_tile, cudaStream_t st, int64_t probe_n, int64_t j0);
+                              int rows_per_tile, cudaStream_t st, int64_t probe_n, int64_t j0,
+                              const T* Gin);
 // Banded layout [row][column] (row stride S).  Rademacher probes are packed
 // as bits (bit j%64 of word j/64 of row i set when g_j[i] = -1; W words per
 // row); Gaussian probes are stored as values G[i*s + j].
 template <typename T>
 cudaError_t launch_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
                             uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st,
-                            int64_t j0);
+                            int64_t j0, const T* Gin);
 
 // ---- conversions / checks (vne_prep.cu) --------------------------------------
 cudaError_t launch_dense_convert_f64(const void* src, int src_dtype, int64_t n, int64_t ld,
@@ -130,9 +133,21 @@ template <typename T>
 cudaError_t launch_dia_step(const T* vals, int64_t ld, int D, int64_t n, const T* Yprev,
                             const T* Yprev2, T* Ynew, const T* G, const uint64_t* bits, int W,
                             int S, int s, StepCols cols, const double* sc, Partials P, int t,
-                            int nblocks, cudaStream_t st);
+                            int nblocks, cudaStream_t st, int band_aligned);
 int dia_supported_halfbw(int D);  // the compiled window >= D-1, or -1
-int dia_step_grid(int is_double, int D, int64_t n, int ncols, int s, int sm_count);
+// Grid of the banded step; band_aligned: the operand band starts on a 16-byte
+// boundary with ld a multiple of 4 (FP32), which selects the bulk-copy kernel
+// for S in {32, 64, 128}.  launch_dia_step takes the same flag.
+int dia_step_grid(int is_double, int D, int64_t n, int ncols, int s, int sm_count,
+                  int band_aligned);
+// The bulk-copy FP32 step (vne_dia_tma.cu): where it applies, its grid, and
+// its launch (Y [n][S], S in {32, 64, 128}; the arguments of launch_dia_step).
+bool dia_tma_ok(int is_double, int D, int64_t n, int S, int s, int band_aligned);
+int dia_tma_grid(int D, int64_t n, int S, int sm_count);
+cudaError_t launch_dia_step_tma(const float* vals, int64_t ld, int D, int64_t n, const float* Yprev,
+                                const float* Yprev2, float* Ynew, const float* G,
+                                const uint64_t* bits, int Wd, int S, int s, StepCols cols,
+                                const double* sc, Partials P, int t, int nblocks, cudaStream_t st);
 
 // ---- dense tensor-core recurrence (vne_tc.cu) -------------------------------------
 // R and Y are each a sum of `pieces` bf16 matrices (1: BF16; 2: bf16x3; 3:

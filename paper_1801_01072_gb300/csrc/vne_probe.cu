@@ -29,14 +29,15 @@ cudaError_t launch_probe_block_f64(double* out, int64_t n, int s, int kind, uint
 // blockIdx.y = probe j.  Writes G[j][i], Y0[c][i] for every column c = j + r*s
 // (r < S/s), the bf16 pieces of Y0 if requested (piece k = bf16 of the
 // residual of pieces 0..k-1, exact in FP32), and the slot-0 partials
-// sum_i g_j[i]^2 of each row tile.
+// sum_i g_j[i]^2 of each row tile.  kind PROBE_GIVEN takes g_j[i] from the
+// caller's block Gin[i*s + j] (probe_n x s, row-major) instead of the stream.
 struct Pieces {
     __nv_bfloat16* p[kMaxPieces];
 };
 template <typename T>
 __global__ void k_dense_init(T* G, T* Y0, Pieces Ysh, int pieces, int64_t ldk, int64_t n, int S,
                              int s, int kind, uint64_t seed, Partials P, int64_t probe_n,
-                             int64_t j0) {
+                             int64_t j0, const T* __restrict__ Gin) {
     __shared__ double sh[32];
     const int j = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -44,7 +45,8 @@ __global__ void k_dense_init(T* G, T* Y0, Pieces Ysh, int pieces, int64_t ldk, i
     if (i < n) {
         if (i < probe_n) {
             const uint64_t e = (uint64_t)(j0 + j) * (uint64_t)probe_n + (uint64_t)i;
-            if (sizeof(T) == 4 && kind == 1) g = (double)gaussian_f32(seed, e);
+            if (kind == PROBE_GIVEN) g = (double)Gin[i * s + j];
+            else if (sizeof(T) == 4 && kind == 1) g = (double)gaussian_f32(seed, e);
             else g = probe_value(kind, seed, e);
         }
         const T gt = (T)g;
@@ -73,8 +75,10 @@ __global__ void k_dense_init(T* G, T* Y0, Pieces Ysh, int pieces, int64_t ldk, i
 template <typename T>
 cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces, int64_t ldk,
                               int64_t n, int S, int s, int kind, uint64_t seed, Partials P,
-                              int rows_per_tile, cudaStream_t st, int64_t probe_n, int64_t j0) {
+                              int rows_per_tile, cudaStream_t st, int64_t probe_n, int64_t j0,
+                              const T* Gin) {
     if (pieces < 0 || pieces > kMaxPieces || (pieces > 0 && !Ysh)) return cudaErrorInvalidValue;
+    if (kind == PROBE_GIVEN && !Gin) return cudaErrorInvalidValue;
     Pieces ps{};
     for (int k = 0; k < pieces; ++k) {
         if (!Ysh[k]) return cudaErrorInvalidValue;
@@ -82,21 +86,23 @@ cudaError_t launch_dense_init(T* G, T* Y0, __nv_bfloat16* const* Ysh, int pieces
     }
     dim3 grid((unsigned)((n + rows_per_tile - 1) / rows_per_tile), (unsigned)s);
     k_dense_init<T><<<grid, rows_per_tile, 0, st>>>(G, Y0, ps, pieces, ldk, n, S, s, kind, seed, P,
-                                                    probe_n, j0);
+                                                    probe_n, j0, Gin);
     return cudaGetLastError();
 }
 template cudaError_t launch_dense_init<double>(double*, double*, __nv_bfloat16* const*, int,
                                                int64_t, int64_t, int, int, int, uint64_t, Partials,
-                                               int, cudaStream_t, int64_t, int64_t);
+                                               int, cudaStream_t, int64_t, int64_t, const double*);
 template cudaError_t launch_dense_init<float>(float*, float*, __nv_bfloat16* const*, int,
                                               int64_t, int64_t, int, int, int, uint64_t, Partials,
-                                              int, cudaStream_t, int64_t, int64_t);
+                                              int, cudaStream_t, int64_t, int64_t, const float*);
 
 // Banded layout: a block of 8 warps owns a tile of rows_per_tile rows; each
 // warp walks rows w, w+8, ... of the tile and lane l covers probes l, l+32, ...
+// kind PROBE_GIVEN reads the caller's block Gin[i*s + j].
 template <typename T>
 __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
-                           uint64_t seed, Partials P, int rows_per_tile, int64_t j0) {
+                           uint64_t seed, Partials P, int rows_per_tile, int64_t j0,
+                           const T* __restrict__ Gin) {
     __shared__ double sh[8][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nchunk = (s + 31) >> 5;  // <= 8
@@ -117,7 +123,8 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
                 T gt = (T)0;
                 if (j < s) {
                     const uint64_t e = (uint64_t)(j0 + j) * (uint64_t)n + (uint64_t)i;
-                    if (kind == 0) gt = (splitmix_out(seed, e) >> 63) ? (T)-1 : (T)1;
+                    if (kind == PROBE_GIVEN) gt = Gin[i * s + j];
+                    else if (kind == 0) gt = (splitmix_out(seed, e) >> 63) ? (T)-1 : (T)1;
                     else gt = (T)gaussian(seed, e);
                 }
                 words[q] = __ballot_sync(0xffffffffu, gt < (T)0);
@@ -148,15 +155,19 @@ __global__ void k_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S,
 template <typename T>
 cudaError_t launch_dia_init(T* G, uint64_t* bits, int W, T* Y0, int64_t n, int S, int s, int kind,
                             uint64_t seed, Partials P, int rows_per_tile, cudaStream_t st,
-                            int64_t j0) {
+                            int64_t j0, const T* Gin) {
     if (s > 256 || W > 4) return cudaErrorInvalidValue;
+    if (kind == PROBE_GIVEN && (!Gin || bits)) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)((n + rows_per_tile - 1) / rows_per_tile);
-    k_dia_init<T><<<grid, 256, 0, st>>>(G, bits, W, Y0, n, S, s, kind, seed, P, rows_per_tile, j0);
+    k_dia_init<T><<<grid, 256, 0, st>>>(G, bits, W, Y0, n, S, s, kind, seed, P, rows_per_tile, j0,
+                                        Gin);
     return cudaGetLastError();
 }
 template cudaError_t launch_dia_init<double>(double*, uint64_t*, int, double*, int64_t, int, int,
-                                             int, uint64_t, Partials, int, cudaStream_t, int64_t);
+                                             int, uint64_t, Partials, int, cudaStream_t, int64_t,
+                                             const double*);
 template cudaError_t launch_dia_init<float>(float*, uint64_t*, int, float*, int64_t, int, int, int,
-                                            uint64_t, Partials, int, cudaStream_t, int64_t);
+                                            uint64_t, Partials, int, cudaStream_t, int64_t,
+                                            const float*);
 
 }  // namespace vne

@@ -69,6 +69,11 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     # argument checks run before any CUDA call
     H = C.c_double()
     assert lib.vne_entropy_chebyshev(None, None, None, C.byref(H), None, None, None) == 1
+    # explicit probes: a NULL probe block is refused first
+    assert lib.vne_entropy_chebyshev_probes(None, None, None, None, C.byref(H), None, None,
+                                            None) == 1
+    assert lib.vne_entropy_taylor_probes(None, None, None, None, C.byref(H), None, None,
+                                         None) == 1
     assert lib.vne_create(None, 0) == 1
 
 
