@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "../../include/vne.h"
@@ -137,6 +138,28 @@ struct Call {
         h->pending.push_back({kind, count, pa, b});
     }
 };
+
+}  // namespace
+
+cudaError_t vne::set_max_dynamic_smem(const void* kernel, int bytes) {
+    struct Entry {
+        const void* fn;
+        int dev, bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> table;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& x : table)
+        if (x.fn == kernel && x.dev == dev && x.bytes >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) table.push_back({kernel, dev, bytes});
+    return e;
+}
+
+namespace {
 
 vne_status map_err(vne_handle* h, cudaError_t e) {
     if (e == cudaSuccess) return VNE_OK;

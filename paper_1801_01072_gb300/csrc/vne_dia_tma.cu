@@ -416,7 +416,7 @@ static cudaError_t launch_tma_hb(const float* vals, int64_t ld, int D, int64_t n
     if (bits && Wd > C::WDMAX) return cudaErrorInvalidValue;
     auto kern = (bits && t == 1) ? k_dia_step_tma<HB, SC, true, kDiaNT, kDiaRB>
                                  : k_dia_step_tma<HB, SC, false, kDiaNT, kDiaRB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaError_t e = set_max_dynamic_smem((const void*)kern, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     kern<<<nblocks, C::NT, C::SMEM, st>>>(vals, ld, D, n, Yprev, Yprev2, Ynew, G, bits, Wd, s, cols,
                                          const_cast<double*>(sc), P, t, nchunks);

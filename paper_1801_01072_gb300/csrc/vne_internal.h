@@ -128,6 +128,10 @@ cudaError_t launch_dense_simt_epilogue(const T* Zpart, int splitk, const T* G, c
                                        cudaStream_t st);
 int dense_simt_splitk(int64_t n, int ncols, int sm_count, int elt_bytes);
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel, device and
+// size (a process-wide table; later calls with a size already set are no-ops).
+cudaError_t set_max_dynamic_smem(const void* kernel, int bytes);
+
 // ---- banded recurrence (vne_dia.cu) --------------------------------------------
 template <typename T>
 cudaError_t launch_dia_step(const T* vals, int64_t ld, int D, int64_t n, const T* Yprev,
@@ -176,6 +180,40 @@ cudaError_t launch_tc_step(const TcStep& a, int sm_count, cudaStream_t st);
 // stored); false if the driver refuses it.
 bool tma_map_bf16_plain(void* map, const void* base, int64_t inner, int64_t rows,
                         int64_t row_stride_elems, int box_inner, int box_rows);
+// The operand map of the tensor-core steps: bf16 rows of `inner` elements,
+// box 64 (128-byte rows, 128-byte swizzle) x box_rows.
+bool tma_map_bf16_operand(void* map, const void* base, int64_t inner, int64_t rows,
+                          int64_t row_stride_elems, int box_rows);
+
+// ---- batched recurrence, one persistent launch (vne_tc_batch.cu) ---------------
+// One matrix of a batch after its prologue (bf16 R, power method, probe block):
+// the buffers of the single-call BF16 path, whose layout the steps keep.
+struct TcBatchMat {
+    const __nv_bfloat16* R;   // [rows_pad][ldk]
+    __nv_bfloat16* sh[2];     // bf16 probe blocks [S_pad][ldk]; Y_0 in sh[0]
+    const float* G;           // [s][n]
+    float* Y[3];              // FP32 masters [S][n]; Y_0 in Y[0]
+    const double* sc;         // scalar block (u)
+    double* flags;            // &sc[SC_FLAGS], raised on a timeout
+    Partials P;               // moment partials, ntiles = rows_pad / 128
+    int64_t n, rows_pad, ldk;
+    int S, s, m, T, tiles, has_cheb, has_tay;
+};
+// Work items of the queue in launch order, (matrix, step, row tile), built so
+// that every item's dependencies (all tiles of the previous step of its
+// matrix) come earlier: rounds over an active set of matrices, admitted in the
+// given order while their bf16 R fit `budget_bytes` or the round has fewer
+// than `min_tiles` tiles.  Returns the item count; items may be NULL.
+int64_t tc_batch_schedule(const TcBatchMat* mats, int count, double budget_bytes, int min_tiles,
+                          int* items);
+// Bytes of the launch's device table (maps, matrices, items, counters).
+size_t tc_batch_table_bytes(const TcBatchMat* mats, int count, int64_t n_items);
+// Fills the table in host memory `host` (pinned, tc_batch_table_bytes) for the
+// device copy `dev`, copies it, clears the counters and launches the kernel
+// on `st` (grid: 2 CTAs per SM).
+cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items, int64_t n_items,
+                            void* host, void* dev, int sm_count, cudaStream_t st);
+
 // autotuner: set (BN = 0 clears) the shape of n x ncols steps; candidates
 int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit);
 int tc_candidates(int64_t n, int ncols, int (*out)[4], int max);

@@ -9,6 +9,9 @@
 // to the scalar block.  Per-thread arithmetic uses the accumulation type of
 // the path (FP64 on the FP64 path, FP32 otherwise): FP64 throughput on this
 // part is a small fraction of FP32, so FP64 stays off the per-element path.
+#include <algorithm>
+#include <cstdlib>
+
 #include "vne_common.cuh"
 #include "vne_internal.h"
 #include "vne_ptx.cuh"
@@ -1076,6 +1079,194 @@ static void launch_power_dia_q1(int hb, int blocks, cudaStream_t st, const T* va
     }
 }
 
+// Banded FP32, one trial, fed by bulk copies: a persistent CTA (256 threads,
+// one per SM) walks a contiguous run of chunks of CH = 768 rows; one thread
+// copies each chunk's D stored diagonals (positions r0-HBA .. r0+CH-1, so that
+// both R[p, p+d] = vals[d][p] and R[p, p-e] = vals[e][p-e] are staged) and the
+// x rows r0-HBA .. r0+CH+HBA-1 into a ring of shared-memory stages, up to
+// NS-1 chunks ahead.  Each thread computes rows r0 + tid + k*256, k < 3, from
+// shared memory (consecutive lanes read consecutive words).  Chunks reaching
+// outside [0, n) are filled with bounds-checked loads.  Output and norm sums
+// as k_power_dia_q1.
+template <int HB> struct PowDiaTma {
+    static constexpr int W = HB + 1, HBA = (HB + 3) / 4 * 4;
+    static constexpr int NT = 256, RPT = 3, CH = NT * RPT;
+    static constexpr int BTP = CH + HBA, XR = CH + 2 * HBA;
+    static constexpr uint32_t B_BYTES = (uint32_t)W * BTP * 4, X_OFF = B_BYTES;
+    static constexpr uint32_t X_BYTES = (uint32_t)XR * 4;
+    static constexpr uint32_t STAGE = (X_OFF + X_BYTES + 127) / 128 * 128;
+    static constexpr int NSF = (int)((232448u - 64u - 2048u) / STAGE);
+    static constexpr int NS = NSF > 4 ? 4 : NSF;
+    static constexpr uint32_t BAR_OFF = NS * STAGE, SMEM = BAR_OFF + 64;
+    static_assert(NS >= 2 && B_BYTES % 16 == 0 && X_BYTES % 16 == 0, "stage layout");
+};
+
+template <int HB>
+__global__ void __launch_bounds__(256, 1) k_power_dia_tma(
+    const float* __restrict__ vals, int64_t n, int64_t ld, int D, const float* __restrict__ x,
+    float* __restrict__ y, double* sc, double* partial, unsigned int* counter, int final_step,
+    double u_scale, int64_t nchunks) {
+    using C = PowDiaTma<HB>;
+    constexpr int NS = C::NS;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + C::BAR_OFF);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + NS);
+    __shared__ float inv_sh[1];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(&bar[b], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int b = 0; b < NS; ++b) {  // diagonals D .. HB are never copied
+        float* bt = reinterpret_cast<float*>(smraw + b * C::STAGE);
+        for (int k = D * C::BTP + tid; k < C::W * C::BTP; k += C::NT) bt[k] = 0.f;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    load_inv_norms<float>(sc, 1, inv_sh);  // ends with __syncthreads
+    const float inv = inv_sh[0];
+
+    const int64_t per = nchunks / gridDim.x, rem = nchunks % gridDim.x;
+    const int64_t cbeg = (int64_t)blockIdx.x * per + (blockIdx.x < rem ? blockIdx.x : rem);
+    const int64_t nk = per + (blockIdx.x < rem ? 1 : 0);
+    auto interior = [&](int64_t ch) {
+        const int64_t r0 = ch * C::CH;
+        return r0 - C::HBA >= 0 && r0 + C::CH + C::HBA <= n;
+    };
+    auto issue = [&](int64_t ch, int st) {
+        unsigned char* sb = smraw + st * C::STAGE;
+        const int64_t pb = ch * C::CH - C::HBA;
+        mbar_expect_tx(&bar[st], (uint32_t)D * C::BTP * 4 + C::X_BYTES);
+        for (int d = 0; d < D; ++d)
+            bulk_load(sb + (uint32_t)d * C::BTP * 4, vals + d * ld + pb, C::BTP * 4, &bar[st]);
+        bulk_load(sb + C::X_OFF, x + pb, C::X_BYTES, &bar[st]);
+    };
+    auto fill = [&](int64_t ch, int st) {
+        unsigned char* sb = smraw + st * C::STAGE;
+        const int64_t pb = ch * C::CH - C::HBA;
+        float* bt = reinterpret_cast<float*>(sb);
+        for (int k = tid; k < D * C::BTP; k += C::NT) {
+            const int d = k / C::BTP;
+            const int64_t p = pb + (k - d * C::BTP);
+            bt[k] = (p >= 0 && p < n - d) ? vals[d * ld + p] : 0.f;
+        }
+        float* xt = reinterpret_cast<float*>(sb + C::X_OFF);
+        for (int k = tid; k < C::XR; k += C::NT) {
+            const int64_t p = pb + k;
+            xt[k] = (p >= 0 && p < n) ? x[p] : 0.f;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    };
+    uint32_t ph = 0u, pend = 0u;
+    if (tid == 0)
+        for (int k = 0; k < NS - 1 && k < nk; ++k)
+            if (interior(cbeg + k)) {
+                issue(cbeg + k, k);
+                pend |= 1u << k;
+            }
+    float acc[3] = {0.f, 0.f, 0.f};
+    bool aborted = false;
+    int st = 0;
+    for (int64_t k = 0; k < nk; ++k, st = (st + 1 == NS) ? 0 : st + 1) {
+        const int64_t ch = cbeg + k;
+        const int sn = st == 0 ? NS - 1 : st - 1;
+        if (tid == 0 && k + NS - 1 < nk && interior(ch + NS - 1)) {
+            issue(ch + NS - 1, sn);
+            pend |= 1u << sn;
+        }
+        if (interior(ch)) {
+            if (!mbar_wait(&bar[st], (ph >> st) & 1u, abort_flag)) *abort_flag = 1;
+            ph ^= 1u << st;
+            pend &= ~(1u << st);
+        } else {
+            fill(ch, st);
+        }
+        const float* bt = reinterpret_cast<const float*>(smraw + st * C::STAGE);
+        const float* xt = reinterpret_cast<const float*>(smraw + st * C::STAGE + C::X_OFF);
+#pragma unroll
+        for (int r = 0; r < C::RPT; ++r) {
+            const int li = tid + r * C::NT;     // row within the chunk
+            const int o = li + C::HBA;          // its staged position
+            const int64_t p = ch * C::CH + li;
+            float a = bt[o] * xt[o];
+            float b = 0.f;
+#pragma unroll
+            for (int d = 1; d <= HB; ++d) {
+                a = fmaf(bt[d * C::BTP + o], xt[o + d], a);
+                b = fmaf(bt[d * C::BTP + o - d], xt[o - d], b);
+            }
+            if (p < n) {
+                const float yv = (a + b) * inv;
+                y[p] = yv;
+                acc[0] = fmaf(yv, yv, acc[0]);
+                if (final_step) {
+                    const float xh = xt[o] * inv;
+                    acc[1] = fmaf(xh, yv, acc[1]);
+                    acc[2] = fmaf(xh, xh, acc[2]);
+                }
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) {
+            aborted = true;
+            break;
+        }
+    }
+    if (aborted) {
+        if (tid == 0) {
+            for (int b = 0; b < NS; ++b) {
+                if (!((pend >> b) & 1u)) continue;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&bar[b], (ph >> b) & 1u) && globaltimer() - t0 < kWaitNs) {
+                }
+            }
+            atomicOr(reinterpret_cast<unsigned long long*>(sc + SC_FLAGS),
+                     (unsigned long long)FLAG_TIMEOUT);
+        }
+        // the other blocks still count on this one in the final reduction
+    }
+    power_finish<float>(acc, 1, partial, counter, sc, final_step, u_scale);
+}
+
+// The bulk-copy product where it applies (FP32 band on 16-byte boundaries,
+// one trial); cudaErrorNotSupported otherwise.
+static cudaError_t launch_power_dia_tma(int hb, const float* vals, int64_t n, int64_t ld, int D,
+                                        const float* x, float* y, double* sc, double* partial,
+                                        unsigned int* counter, int final_step, double u_scale,
+                                        int nblocks, cudaStream_t st) {
+    if (((uintptr_t)vals & 15) || (ld & 3) || ((uintptr_t)x & 15) || nblocks < 1)
+        return cudaErrorNotSupported;
+    const char* e = getenv("VNE_DIA_TMA");
+    if (e && e[0] == '0') return cudaErrorNotSupported;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorNotSupported;
+#define VNE_POW_TMA(HBV)                                                                         \
+    {                                                                                            \
+        using C = PowDiaTma<HBV>;                                                                \
+        const int64_t nchunks = (n + C::CH - 1) / C::CH;                                         \
+        const int grid = (int)std::min<int64_t>(std::min(sms, nblocks), nchunks);               \
+        cudaError_t err = set_max_dynamic_smem((const void*)k_power_dia_tma<HBV>,                \
+                                               (int)C::SMEM);                                    \
+        if (err != cudaSuccess) return err;                                                      \
+        k_power_dia_tma<HBV><<<grid, C::NT, C::SMEM, st>>>(vals, n, ld, D, x, y, sc, partial,    \
+                                                            counter, final_step, u_scale,       \
+                                                            nchunks);                            \
+        return cudaGetLastError();                                                               \
+    }
+    switch (hb) {
+        case 1: VNE_POW_TMA(1)
+        case 2: VNE_POW_TMA(2)
+        case 4: VNE_POW_TMA(4)
+        case 8: VNE_POW_TMA(8)
+        case 16: VNE_POW_TMA(16)
+        default: return cudaErrorNotSupported;
+    }
+#undef VNE_POW_TMA
+}
+
 cudaError_t launch_power_step_dia(const void* vals, int rdtype, int64_t n, int64_t ld, int D,
                                   const void* x, void* y, int q, double* sc, double* partial,
                                   unsigned int* counter, int final_step, double u_scale,
@@ -1090,10 +1281,15 @@ cudaError_t launch_power_step_dia(const void* vals, int rdtype, int64_t n, int64
             launch_power_dia_q1<double>(hb, blocks, st, (const double*)vals, n, ld, D,
                                         (const double*)x, (double*)y, sc, partial, counter,
                                         final_step, u_scale);
-        else
+        else {
+            const cudaError_t e = launch_power_dia_tma(hb, (const float*)vals, n, ld, D,
+                                                       (const float*)x, (float*)y, sc, partial,
+                                                       counter, final_step, u_scale, nblocks, st);
+            if (e != cudaErrorNotSupported) return e;
             launch_power_dia_q1<float>(hb, blocks, st, (const float*)vals, n, ld, D,
                                        (const float*)x, (float*)y, sc, partial, counter,
                                        final_step, u_scale);
+        }
         return cudaGetLastError();
     }
     if (rdtype == 0)

@@ -1,0 +1,447 @@
+// Batched dense recurrence in one persistent launch: the Chebyshev / Taylor
+// steps (Sections 2 and 3) of many density matrices of uneven n, BF16 tensor-
+// core products with FP32 accumulation, on the buffers each matrix's prologue
+// (bf16 R, power method, probe block) left in its workspace.
+//
+// Work items are (matrix j, step t, 128-row tile i) in a queue ordered so that
+// an item's dependencies (every tile of step t-1 of matrix j) come earlier.
+// CTAs (two per SM, 192 threads) take items in queue order from one atomic
+// counter; before loading an item a CTA waits (bounded) until the counter of
+// step t-1 of its matrix reaches the matrix's tile count.  Every item an item
+// waits on was taken earlier by a CTA that does not wait on anything later,
+// so the queue always advances, resident or not.  The queue visits a bounded
+// set of matrices at a time (rounds of one step of each active matrix), so
+// each R is re-read from L2 from one step to the next.
+//
+// Roles:
+//   warp 0 lane 0 : scheduler and TMA producer: takes an item, waits on its
+//                   dependency, publishes it in one of two item slots, then
+//                   streams the item's R tile rows and the probe block's bf16
+//                   copy through a 4-stage ring;
+//   warp 1        : TMEM allocation (two accumulators of up to 64 columns);
+//                   lane 0 issues tcgen05.mma (M = 128, N = S padded to 32 or
+//                   64, K = 16) into the item's accumulator;
+//   warps 2-5     : epilogue: one row per thread (TMEM lane quarter warp % 4),
+//                   the update of the single-call path (Chebyshev three-term or
+//                   first step, Taylor), the FP32 master and its bf16 copy, the
+//                   per-tile moment partials in FP64, then the step counter.
+// Every wait is bounded (2 s); a timeout raises FLAG_TIMEOUT in the scalar
+// block of every matrix and stops the queue.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "vne_common.cuh"
+#include "vne_internal.h"
+#include "vne_ptx.cuh"
+#include "vne_tc_ptx.cuh"
+
+namespace vne {
+
+constexpr int TB_THREADS = 192;
+constexpr int TB_STAGES = 4;
+constexpr int TB_BM = 128, TB_BK = 64, TB_BNMAX = 64;
+constexpr uint32_t TB_A_BYTES = TB_BM * TB_BK * 2;     // 16 KB
+constexpr uint32_t TB_B_BYTES = TB_BNMAX * TB_BK * 2;  // 8 KB
+constexpr uint32_t TB_STAGE = TB_A_BYTES + TB_B_BYTES;  // 24 KB, a multiple of 1024
+constexpr uint32_t TB_TMEM_COLS = 2 * TB_BNMAX;
+
+struct TbSlot {
+    int j, t, i, valid;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// every matrix of the batch gets FLAG_TIMEOUT, and the queue stops
+__device__ void tb_abort(const TcBatchMat* mats, int count, int* abort_g) {
+    atomicExch(abort_g, 1);
+    for (int j = 0; j < count; ++j)
+        atomicOr(reinterpret_cast<unsigned long long*>(mats[j].flags),
+                 (unsigned long long)FLAG_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(TB_THREADS, 2)
+    k_tc_batch(const CUtensorMap* __restrict__ maps, const TcBatchMat* __restrict__ mats,
+               const int4* __restrict__ items, int n_items, int count, int* done, int tstride,
+               int* head, int* abort_g) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t* tail = smem + TB_STAGES * TB_STAGE;
+    uint64_t* full_bar = reinterpret_cast<uint64_t*>(tail);
+    uint64_t* empty_bar = full_bar + TB_STAGES;
+    uint64_t* slot_full = empty_bar + TB_STAGES;  // [2]
+    uint64_t* slot_empty = slot_full + 2;         // [2], 5 arrivals: MMA + 4 epilogue warps
+    uint64_t* acc_full = slot_empty + 2;          // [2]
+    uint64_t* acc_empty = acc_full + 2;           // [2]
+    TbSlot* slots = reinterpret_cast<TbSlot*>(acc_empty + 2);  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(slots + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* kt_issued = reinterpret_cast<int*>(tmem_slot + 2);    // ring loads issued
+    int* kt_consumed = reinterpret_cast<int*>(tmem_slot + 3);  // ring stages consumed by MMAs
+    float* red = reinterpret_cast<float*>(tmem_slot + 4);  // [4][TB_BNMAX]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TB_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&slot_full[b], 1);
+            mbar_init(&slot_empty[b], 5);
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 1);
+        }
+        *abort_flag = 0;
+        *kt_issued = 0;
+        *kt_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TB_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- scheduler + TMA producer ----------------
+            const uint64_t pol_R = policy_evict_last();
+            int kt = 0;  // ring position, continued across items
+            for (int q = 0;; ++q) {
+                const int s = q & 1;
+                bool stop = false;
+                if (!mbar_wait(&slot_empty[s], ((uint32_t)(q >> 1) & 1u) ^ 1u, abort_flag)) {
+                    tb_abort(mats, count, abort_g);
+                    stop = true;
+                }
+                int it = stop ? n_items : atomicAdd(head, 1);
+                if (ld_acquire_gpu(abort_g)) it = n_items;
+                int4 w = make_int4(0, 0, 0, 0);
+                if (it < n_items) {
+                    w = items[it];
+                    if (w.y >= 2) {  // every tile of step t-1 of matrix j
+                        const int need = mats[w.x].tiles;
+                        const int* cnt = done + (size_t)w.x * tstride + (w.y - 1);
+                        const uint64_t t0 = globaltimer();
+                        for (uint32_t spin = 0; ld_acquire_gpu(cnt) < need; ++spin) {
+                            if ((spin & 63u) == 63u) {
+                                if (ld_acquire_gpu(abort_g)) {
+                                    it = n_items;
+                                    break;
+                                }
+                                if (globaltimer() - t0 > kWaitNs) {
+                                    tb_abort(mats, count, abort_g);
+                                    it = n_items;
+                                    break;
+                                }
+                            }
+                        }
+                    }
+                    // the other CTAs' generic stores, released through the
+                    // counter, are read below by the async (TMA) proxy
+                    fence_proxy_async_global();
+                }
+                const bool valid = it < n_items;
+                slots[s] = TbSlot{w.x, w.y, w.z, valid ? 1 : 0};
+                mbar_arrive_local(&slot_full[s]);
+                if (!valid) break;
+                const TcBatchMat& M = mats[w.x];
+                const CUtensorMap* mR = maps + 3 * w.x;
+                const CUtensorMap* mY = maps + 3 * w.x + 1 + ((w.y - 1) & 1);
+                const int npad = (M.S + 31) & ~31;
+                const uint32_t bytes = TB_A_BYTES + (uint32_t)npad * TB_BK * 2;
+                const int nkb = (int)(M.ldk / TB_BK);
+                for (int kb = 0; kb < nkb; ++kb, ++kt) {
+                    const int st = kt % TB_STAGES;
+                    const uint32_t ph = (uint32_t)(kt / TB_STAGES) & 1u;
+                    if (!mbar_wait(&empty_bar[st], ph ^ 1u, abort_flag)) {
+                        tb_abort(mats, count, abort_g);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t* sA = smem + (size_t)st * TB_STAGE;
+                    mbar_expect_tx(&full_bar[st], bytes);
+                    tma_load_2d_hint(sA, mR, &full_bar[st], kb * TB_BK, w.z * TB_BM, pol_R);
+                    tma_load_2d_hint(sA + TB_A_BYTES, mY, &full_bar[st], kb * TB_BK, 0, pol_R);
+                    *kt_issued = kt + 1;
+                }
+                if (*abort_flag) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int kt = 0;
+            for (int q = 0;; ++q) {
+                const int s = q & 1, a = q & 1;
+                if (!mbar_wait(&slot_full[s], (uint32_t)(q >> 1) & 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const TbSlot sl = slots[s];
+                mbar_arrive_local(&slot_empty[s]);
+                if (!sl.valid) break;
+                const TcBatchMat& M = mats[sl.j];
+                const int npad = (M.S + 31) & ~31;
+                const uint32_t idesc = idesc_bf16(TB_BM, npad);
+                const int nkb = (int)(M.ldk / TB_BK);
+                if (!mbar_wait(&acc_empty[a], ((uint32_t)(q >> 1) & 1u) ^ 1u, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(a * TB_BNMAX);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++kt) {
+                    const int st = kt % TB_STAGES;
+                    const uint32_t ph = (uint32_t)(kt / TB_STAGES) & 1u;
+                    if (!mbar_wait(&full_bar[st], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t aA = smem_u32(smem + (size_t)st * TB_STAGE);
+                    issue_stage<1, TB_BK / 16, false>(d_tmem, aA, TB_A_BYTES, aA + TB_A_BYTES,
+                                                      (uint32_t)npad * TB_BK * 2, TB_BK, idesc,
+                                                      kb > 0 ? 1u : 0u);
+                    tc_commit(&empty_bar[st]);
+                    *kt_consumed = kt + 1;
+                }
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_commit(&acc_full[a]);
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5, 128 threads) ----------------
+        const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+        const int et = threadIdx.x - 64;
+        for (int q = 0;; ++q) {
+            const int s = q & 1, a = q & 1;
+            if (!mbar_wait(&slot_full[s], (uint32_t)(q >> 1) & 1u, abort_flag)) break;
+            const TbSlot sl = slots[s];
+            __syncwarp();
+            if (lane == 0) mbar_arrive_local(&slot_empty[s]);
+            if (!sl.valid) break;
+            const TcBatchMat& M = mats[sl.j];
+            const int t = sl.t, S = M.S, sp = M.s;
+            const int64_t n = M.n, ldk = M.ldk;
+            const int64_t row = (int64_t)sl.i * TB_BM + quarter * 32 + lane;
+            const bool row_ok = row < n;
+            const bool cheb_on = M.has_cheb && t <= M.m;
+            const int tay0 = M.has_cheb ? sp : 0;
+            const float u = (float)M.sc[SC_U];
+            const float fa = 2.f / u, finvu = 1.f / u;
+            const float* Yp = M.Y[(t - 1) % 3];
+            const float* Yp2 = M.Y[(t + 1) % 3];
+            float* Yn = M.Y[t % 3];
+            __nv_bfloat16* sh_out = M.sh[t & 1];
+            if (!mbar_wait(&acc_full[a], (uint32_t)(q >> 1) & 1u, abort_flag)) break;
+            tc_fence_after();
+            const int npad = (S + 31) & ~31;
+            uint32_t r0[32], r1[32];
+            const uint32_t taddr = tmem_base + (uint32_t)(a * TB_BNMAX) + ((uint32_t)(quarter * 32) << 16);
+            TMEM_LD32(taddr, r0);
+            if (npad > 32) TMEM_LD32(taddr + 32, r1);
+            tmem_wait_ld();
+            tc_fence_before();
+            named_bar_sync(1, 128);
+            if (et == 0) mbar_arrive_local(&acc_empty[a]);  // the accumulator is free
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+            for (int qq = 0; qq < 32; ++qq) {
+                const int c = hh * 32 + qq;
+                if (c >= S) continue;
+                const float z = __uint_as_float(hh == 0 ? r0[qq] : r1[qq]);
+                const bool is_cheb = cheb_on && c < sp;
+                const bool is_tay = M.has_tay && c >= tay0 && c < tay0 + sp;
+                float v = 0.f;
+                if (is_cheb || is_tay) {
+                    const float g = row_ok ? M.G[(size_t)(c % sp) * n + row] : 0.f;
+                    float y;
+                    if (is_cheb) {
+                        if (t == 1) {
+                            y = fmaf(fa, z, -g);
+                        } else {
+                            const float y1 = row_ok ? Yp[(size_t)c * n + row] : 0.f;
+                            const float y2 = row_ok ? Yp2[(size_t)c * n + row] : 0.f;
+                            y = 2.f * fmaf(fa, z, -y1) - y2;
+                        }
+                        v = g * y;
+                    } else {
+                        const float y1 = row_ok ? Yp[(size_t)c * n + row] : 0.f;
+                        y = fmaf(-z, finvu, y1);
+                        v = g * z;
+                    }
+                    if (row_ok) {
+                        Yn[(size_t)c * n + row] = y;
+                        sh_out[(size_t)c * ldk + row] = __float2bfloat16_rn(y);
+                    }
+                }
+                v = warp_sum(v);
+                if (lane == 0) red[quarter * TB_BNMAX + c] = v;
+            }
+            // the shadows are read by later items through the async proxy
+            fence_proxy_async_global();
+            named_bar_sync(1, 128);
+            if (et < S) {
+                const bool on = (cheb_on && et < sp) || (M.has_tay && et >= tay0 && et < tay0 + sp);
+                if (on) {
+                    double tot = 0.0;
+                    for (int w4 = 0; w4 < 4; ++w4) tot += (double)red[w4 * TB_BNMAX + et];
+                    M.P.slot(t)[(size_t)sl.i * S + et] = tot;
+                }
+            }
+            named_bar_sync(1, 128);  // partials written, red free for the next item
+            if (et == 0) {
+                __threadfence();
+                atomicAdd(done + (size_t)sl.j * tstride + t, 1);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        // copies issued but never consumed: wait (bounded) until they land
+        for (int k = *kt_consumed; k < *kt_issued; ++k) {
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(&full_bar[k % TB_STAGES], (uint32_t)(k / TB_STAGES) & 1u) &&
+                   globaltimer() - t0 < kWaitNs) {
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TB_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: the queue order, the device table and the launch.
+// ---------------------------------------------------------------------------
+
+int64_t tc_batch_schedule(const TcBatchMat* mats, int count, double budget_bytes, int min_tiles,
+                          int* items) {
+    if (!mats || count < 1) return 0;
+    std::vector<int> step((size_t)count, 0);  // next step of each active matrix, 0 = not admitted
+    std::vector<int> active;
+    int next = 0;
+    double bytes = 0.0;
+    int tiles = 0;
+    int64_t k = 0;
+    auto rbytes = [&](int j) { return 2.0 * (double)mats[j].rows_pad * (double)mats[j].ldk; };
+    while (next < count || !active.empty()) {
+        // admit in the given order while the active bf16 R fit the budget, or
+        // while a round would have fewer than min_tiles tiles
+        while (next < count && (active.empty() || bytes + rbytes(next) <= budget_bytes ||
+                                tiles < min_tiles)) {
+            active.push_back(next);
+            step[next] = 1;
+            bytes += rbytes(next);
+            tiles += mats[next].tiles;
+            ++next;
+        }
+        // one round: the next step of every active matrix, all its tiles
+        std::vector<int> keep;
+        for (int j : active) {
+            for (int i = 0; i < mats[j].tiles; ++i, ++k)
+                if (items) {
+                    items[4 * k] = j;
+                    items[4 * k + 1] = step[j];
+                    items[4 * k + 2] = i;
+                    items[4 * k + 3] = 0;
+                }
+            if (++step[j] <= mats[j].T) {
+                keep.push_back(j);
+            } else {
+                bytes -= rbytes(j);
+                tiles -= mats[j].tiles;
+            }
+        }
+        active.swap(keep);
+    }
+    return k;
+}
+
+namespace {
+// device table: [maps: 3 per matrix][matrices][items][counters: count x tstride][head, abort]
+struct TbLayout {
+    size_t maps, mats, items, done, head, total;
+    int tstride;
+};
+TbLayout tb_layout(const TcBatchMat* mats, int count, int64_t n_items) {
+    TbLayout L{};
+    int tmax = 0;
+    for (int j = 0; j < count; ++j) tmax = std::max(tmax, mats[j].T);
+    L.tstride = tmax + 1;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    L.maps = 0;
+    L.mats = up(L.maps + (size_t)3 * count * sizeof(CUtensorMap));
+    L.items = up(L.mats + (size_t)count * sizeof(TcBatchMat));
+    L.done = up(L.items + (size_t)n_items * sizeof(int4));
+    L.head = up(L.done + (size_t)count * L.tstride * sizeof(int));
+    L.total = up(L.head + 2 * sizeof(int));
+    return L;
+}
+}  // namespace
+
+size_t tc_batch_table_bytes(const TcBatchMat* mats, int count, int64_t n_items) {
+    return tb_layout(mats, count, n_items).total;
+}
+
+cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items, int64_t n_items,
+                            void* host, void* dev, int sm_count, cudaStream_t st) {
+    if (!mats || count < 1 || !items || n_items < 1 || !host || !dev) return cudaErrorInvalidValue;
+    const TbLayout L = tb_layout(mats, count, n_items);
+    char* hb = static_cast<char*>(host);
+    std::memset(hb, 0, L.total);
+    CUtensorMap* hmaps = reinterpret_cast<CUtensorMap*>(hb + L.maps);
+    for (int j = 0; j < count; ++j) {
+        const TcBatchMat& M = mats[j];
+        const int npad = (M.S + 31) & ~31;
+        if (M.S < 1 || npad > TB_BNMAX || M.ldk % TB_BK || M.rows_pad % TB_BM) return cudaErrorInvalidValue;
+        if (!tma_map_bf16_operand(&hmaps[3 * j], M.R, M.ldk, M.rows_pad, M.ldk, TB_BM) ||
+            !tma_map_bf16_operand(&hmaps[3 * j + 1], M.sh[0], M.ldk, npad, M.ldk, npad) ||
+            !tma_map_bf16_operand(&hmaps[3 * j + 2], M.sh[1], M.ldk, npad, M.ldk, npad))
+            return cudaErrorInvalidValue;
+    }
+    std::memcpy(hb + L.mats, mats, (size_t)count * sizeof(TcBatchMat));
+    std::memcpy(hb + L.items, items, (size_t)n_items * sizeof(int4));
+    cudaError_t e = cudaMemcpyAsync(dev, host, L.total, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    char* db = static_cast<char*>(dev);
+    const uint32_t smem = TB_STAGES * TB_STAGE + 2048 + 1024;
+    e = set_max_dynamic_smem((const void*)k_tc_batch, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>((int64_t)2 * sm_count, n_items);
+    k_tc_batch<<<grid, TB_THREADS, smem, st>>>(
+        reinterpret_cast<const CUtensorMap*>(db + L.maps),
+        reinterpret_cast<const TcBatchMat*>(db + L.mats), reinterpret_cast<const int4*>(db + L.items),
+        (int)n_items, count, reinterpret_cast<int*>(db + L.done), L.tstride,
+        reinterpret_cast<int*>(db + L.head), reinterpret_cast<int*>(db + L.head) + 1);
+    return cudaGetLastError();
+}
+
+}  // namespace vne
