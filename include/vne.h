@@ -175,6 +175,20 @@ vne_status vne_entropy_taylor(vne_handle* h, const vne_matrix* R, const vne_para
                               double* H_out, double* moments_out, double* u_out,
                               void* stream);
 
+/* The work queue of the batched recurrence's persistent launch (host logic
+ * only, no GPU call; the paper has no batched form).  For `count` dense
+ * matrices of orders n[i] (host array), degree m, s probes and `method`
+ * (VNE_METHOD_*), the queue holds one item per (matrix i, step t, 128-row tile)
+ * with t = 1..m (1..m+1 with a Taylor estimator), in launch order: rounds of
+ * one step of every active matrix, matrices admitted in the given order while
+ * their bf16 R (2 * round_up(n, 128) * round_up(n, 64) bytes) fit l2_mb MiB
+ * or a round has fewer than min_tiles tiles.  Every item's dependencies (all
+ * tiles of the previous step of its matrix) come earlier in the queue.
+ *   items_out : host, 4 int32 per item (i, t, tile, 0), or NULL to count.
+ * Returns the item count, or -1 on invalid arguments. */
+int64_t vne_batch_queue(const int64_t* n, int32_t count, int32_t m, int32_t s, int32_t method,
+                        double l2_mb, int32_t min_tiles, int32_t* items_out);
+
 /* Algorithms 1b and 1a on probes the caller gives, instead of the seed's
  * stream (Lemma thm:trace holds for any probe law with E[g g^T] = I; a single
  * probe g gives the quadratic form g^T f(R) g of Section 3 / Section 2, which

@@ -55,6 +55,9 @@ SIGNATURES = [
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, _D, _D, C.c_void_p]),
     ("vne_entropy_taylor", C.c_int,
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), _D, _D, _D, C.c_void_p]),
+    ("vne_batch_queue", C.c_int64,
+     [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+      C.c_void_p]),
     ("vne_entropy_chebyshev_probes", C.c_int,
      [_H, C.POINTER(VneMatrix), C.c_void_p, C.POINTER(VneParams), _D, _D, _D, C.c_void_p]),
     ("vne_entropy_taylor_probes", C.c_int,

@@ -49,6 +49,10 @@ struct vne_handle {
     std::vector<cudaEvent_t> bevents;  // [0] fork, [1] done, [2 + k] join of stream k
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_key = 0;
+    // the persistent recurrence of a batch: its table, pinned and on the device
+    char* btab_dev = nullptr;
+    char* btab_host = nullptr;
+    size_t btab_bytes = 0;
 };
 
 namespace {
@@ -67,6 +71,11 @@ struct Outputs {
     // batched calls: measure the workspace only, or enqueue into a given
     // workspace and pinned host slot without synchronising
     int measure = 0;
+    // batched persistent recurrence: phase 1 enqueues the prologue (operands,
+    // power method, probe block) and records the step buffers in *bmat;
+    // phase 2 enqueues the combine on the same workspace after the steps ran
+    int phase = 0;
+    TcBatchMat* bmat = nullptr;
     size_t* measured = nullptr;
     char* ws = nullptr;
     double* host_slot = nullptr;
@@ -452,17 +461,20 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     h->ev_used = 0;
     h->pending.clear();
 
-    c.chk(cudaMemsetAsync(sc, 0, SC_COUNT * sizeof(double), c.st));
-    c.chk(cudaMemsetAsync(counter, 0, 64 * sizeof(unsigned int), c.st));
+    const bool pro = out.phase != 2;  // the prologue runs in phases 0 and 1
+    if (pro) {
+        c.chk(cudaMemsetAsync(sc, 0, SC_COUNT * sizeof(double), c.st));
+        c.chk(cudaMemsetAsync(counter, 0, 64 * sizeof(unsigned int), c.st));
+    }
 
     // ---- matrix to the device, trace check ----
     const void* Rdata = R.data;
     if (R.memory == VNE_MEM_HOST) {
         const size_t bytes = (size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype);
-        c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
+        if (pro) c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
         Rdata = Rcopy;
     }
-    if (p->check_trace)
+    if (pro && p->check_trace)
         c.launched(launch_trace(Rdata, R.layout, R.dtype, R.n, R.ld, ppart, counter, sc, c.st));
 
     // ---- operands ----
@@ -470,15 +482,17 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     int64_t ldr = R.ld;
     if (cplx) {
         const int edt = (f64 && !tc) ? VNE_F64 : VNE_F32;
-        c.launched(launch_hermitian_embed(Rdata, R.dtype, R.n, R.ld, Rop, edt, c.st));
+        if (pro) c.launched(launch_hermitian_embed(Rdata, R.dtype, R.n, R.ld, Rop, edt, c.st));
         Rk = Rop;
         ldr = n;
-        if (tc)
+        if (tc && pro)
             c.launched(launch_dense_convert_bf16(Rop, VNE_F32, n, n, Rpc, pieces, rows_pad, ldk, c.st));
     } else if (tc && (mode != MODE_POWER || pw_rdt == 2)) {
-        c.launched(launch_dense_convert_bf16(Rdata, R.dtype, n, R.ld, Rpc, pieces, rows_pad, ldk, c.st));
+        if (pro)
+            c.launched(launch_dense_convert_bf16(Rdata, R.dtype, n, R.ld, Rpc, pieces, rows_pad, ldk, c.st));
     } else if (Rop) {
-        if (dense) {
+        if (!pro) {
+        } else if (dense) {
             if (f64) c.launched(launch_dense_convert_f64(Rdata, R.dtype, n, R.ld, (double*)Rop, c.st));
             else c.launched(launch_dense_convert_f32(Rdata, R.dtype, n, R.ld, (float*)Rop, c.st));
         } else {
@@ -489,7 +503,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     }
 
     // ---- power method (Algorithm alg:power) or the given u ----
-    if (do_power) {
+    if (pro && do_power) {
         if (pw_xdouble) c.launched(launch_power_init<double>((double*)x0, n, q, p->seed, sc, c.st));
         else c.launched(launch_power_init<float>((float*)x0, n, q, p->seed, sc, c.st));
         void* xa = x0;
@@ -516,7 +530,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
             std::swap(xa, xb);
         }
         c.prof_end(3, p->power_iters + 1);
-    } else {
+    } else if (pro) {
         c.launched(launch_set_u(sc, p->u_override > 0.0 ? p->u_override : 1.0, c.st));
     }
 
@@ -526,13 +540,16 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         // bf16 pieces of the probe blocks, double-buffered across steps: sh[b][k]
         __nv_bfloat16* sh[2][kMaxPieces] = {};
         if (tc) {
-            c.chk(cudaMemsetAsync(Sh, 0, (size_t)2 * pieces * S_pad * ldk * sizeof(__nv_bfloat16),
-                                  c.st));
+            if (pro)
+                c.chk(cudaMemsetAsync(Sh, 0,
+                                      (size_t)2 * pieces * S_pad * ldk * sizeof(__nv_bfloat16),
+                                      c.st));
             for (int b = 0; b < 2; ++b)
                 for (int k = 0; k < pieces; ++k)
                     sh[b][k] = Sh + (size_t)(b * pieces + k) * S_pad * ldk;
         }
-        if (dense) {
+        if (!pro) {
+        } else if (dense) {
             if (f64)
                 c.launched(launch_dense_init<double>((double*)G, (double*)Yb0, nullptr, 0, 0,
                                                      n, S, s, pkind, p->seed, P, 256, c.st,
@@ -556,11 +573,35 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
                                                   c.st, p->probe_offset, (const float*)out.probes));
         }
         void* Yb[3] = {Yb0, Yb1, Yb2};
+        if (out.phase == 1) {  // the batch's persistent kernel runs the steps
+            if (out.bmat && tc && pieces == 1 && dense && !cplx) {
+                TcBatchMat& b = *out.bmat;
+                b.R = Rpc[0];
+                b.sh[0] = sh[0][0];
+                b.sh[1] = sh[1][0];
+                b.G = (const float*)G;
+                for (int k = 0; k < 3; ++k) b.Y[k] = (float*)Yb[k];
+                b.sc = sc;
+                b.flags = sc + SC_FLAGS;
+                b.P = P;
+                b.n = n;
+                b.rows_pad = rows_pad;
+                b.ldk = ldk;
+                b.S = S;
+                b.s = s;
+                b.m = m;
+                b.T = T_steps;
+                b.tiles = (int)(rows_pad / tc_tile_m());
+                b.has_cheb = has_cheb ? 1 : 0;
+                b.has_tay = has_tay ? 1 : 0;
+            }
+            return c.ok() ? VNE_OK : map_err(h, c.err);
+        }
         // tensor-core steps are timed as one span (consecutive launches overlap
         // their prologues with the previous step's tail; an event between them
         // would serialise them)
-        if (tc) c.prof_begin();
-        for (int t = 1; t <= T_steps && c.ok(); ++t) {
+        if (tc && pro) c.prof_begin();
+        for (int t = 1; t <= T_steps && c.ok() && pro; ++t) {
             StepCols cols{};
             const bool cheb_on = has_cheb && t <= m;
             cols.cheb_c0 = 0;
@@ -631,7 +672,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
                 c.prof_end(2);
             }
         }
-        if (tc) c.prof_end(0, T_steps);
+        if (tc && pro) c.prof_end(0, T_steps);
         if (c.ok())
             c.launched(launch_combine(P, s, m, has_cheb ? 0 : -1, has_tay ? (has_cheb ? s : 0) : -1,
                                       mom_c, mom_t, sc, c.st));
@@ -998,6 +1039,8 @@ void vne_destroy(vne_handle* h) {
     for (cudaEvent_t e : h->bevents) cudaEventDestroy(e);
     if (h->bws) cudaFree(h->bws);
     if (h->bhost) cudaFreeHost(h->bhost);
+    if (h->btab_dev) cudaFree(h->btab_dev);
+    if (h->btab_host) cudaFreeHost(h->btab_host);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
 }
@@ -1033,6 +1076,30 @@ vne_status vne_entropy_both(vne_handle* h, const vne_matrix* R, const vne_params
     o.mom_taylor = moments_taylor;
     o.u = u_out;
     return run(h, R, p, MODE_BOTH, o, stream);
+}
+
+int64_t vne_batch_queue(const int64_t* n, int32_t count, int32_t m, int32_t s, int32_t method,
+                        double l2_mb, int32_t min_tiles, int32_t* items_out) {
+    if (!n || count < 1 || m < 1 || s < 1 || !(l2_mb > 0.0) || min_tiles < 0) return -1;
+    if (method != VNE_METHOD_TAYLOR && method != VNE_METHOD_CHEBYSHEV && method != VNE_METHOD_BOTH)
+        return -1;
+    const bool cheb = method != VNE_METHOD_TAYLOR, tay = method != VNE_METHOD_CHEBYSHEV;
+    std::vector<TcBatchMat> bm((size_t)count, TcBatchMat{});
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1) return -1;
+        TcBatchMat& b = bm[i];
+        b.n = n[i];
+        b.rows_pad = round_up(b.n, tc_tile_m());
+        b.ldk = round_up(b.n, tc_tile_k());
+        b.tiles = (int)(b.rows_pad / tc_tile_m());
+        b.s = s;
+        b.S = (cheb && tay) ? 2 * s : s;
+        b.m = m;
+        b.has_cheb = cheb ? 1 : 0;
+        b.has_tay = tay ? 1 : 0;
+        b.T = tay ? m + 1 : m;
+    }
+    return tc_batch_schedule(bm.data(), count, l2_mb * 1048576.0, min_tiles, items_out);
 }
 
 vne_status vne_entropy_chebyshev_probes(vne_handle* h, const vne_matrix* R, const void* G,
@@ -1074,6 +1141,50 @@ int batch_streams() {
         }
     }
     return k;
+}
+
+// Batches run their recurrence in one persistent launch (BF16, dense real
+// matrices, at most 64 step columns) unless VNE_BATCH_PERSISTENT=0 (read at
+// each call).  VNE_BATCH_L2_MB (bf16 R kept active at a time, default 64) and
+// VNE_BATCH_MIN_TILES (default 2 per SM) shape its queue.
+bool batch_persistent_enabled() {
+    const char* e = getenv("VNE_BATCH_PERSISTENT");
+    return !(e && e[0] == '0');
+}
+double batch_l2_budget() {
+    const char* e = getenv("VNE_BATCH_L2_MB");
+    const double v = e ? atof(e) : 64.0;
+    return (v > 0.0 ? v : 64.0) * 1048576.0;
+}
+int batch_min_tiles(int sm_count) {
+    const char* e = getenv("VNE_BATCH_MIN_TILES");
+    const int v = e ? atoi(e) : 2 * sm_count;
+    return v >= 0 ? v : 2 * sm_count;
+}
+
+// The pinned and device tables of the persistent launch (grown as needed; a
+// captured graph that holds the old ones is dropped first).
+vne_status batch_table(vne_handle* h, size_t bytes) {
+    if (bytes <= h->btab_bytes) return VNE_OK;
+    cudaDeviceSynchronize();
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (h->btab_dev) cudaFree(h->btab_dev);
+    if (h->btab_host) cudaFreeHost(h->btab_host);
+    h->btab_dev = h->btab_host = nullptr;
+    h->btab_bytes = 0;
+    if (cudaMalloc((void**)&h->btab_dev, bytes) != cudaSuccess ||
+        cudaMallocHost((void**)&h->btab_host, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->btab_dev) cudaFree(h->btab_dev);
+        h->btab_dev = nullptr;
+        h->btab_host = nullptr;
+        return VNE_ERR_OOM;
+    }
+    h->btab_bytes = bytes;
+    return VNE_OK;
 }
 
 vne_status batch_resources(vne_handle* h, size_t ws_bytes, size_t count) {
@@ -1153,6 +1264,37 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     }
     vne_status vs = batch_resources(h, off[count], (size_t)count);
     if (vs != VNE_OK) return vs;
+    // the recurrence of the whole batch in one persistent launch
+    const int S_all = mode == MODE_BOTH ? 2 * p->s : p->s;
+    bool pers = batch_persistent_enabled() && p->precision == VNE_PREC_BF16 && S_all <= 64;
+    for (int i = 0; i < count && pers; ++i)
+        if (Rs[i].layout != VNE_DENSE || is_complex(Rs[i].dtype)) pers = false;
+    std::vector<TcBatchMat> bm;
+    std::vector<int> items;
+    int64_t n_items = 0;
+    const double l2_budget = batch_l2_budget();
+    const int min_tiles = batch_min_tiles(h->sm_count);
+    if (pers) {
+        bm.assign((size_t)count, TcBatchMat{});
+        for (int i = 0; i < count; ++i) {
+            TcBatchMat& b = bm[i];
+            b.n = Rs[i].n;
+            b.rows_pad = round_up(b.n, tc_tile_m());
+            b.ldk = round_up(b.n, tc_tile_k());
+            b.tiles = (int)(b.rows_pad / tc_tile_m());
+            b.S = S_all;
+            b.s = p->s;
+            b.m = p->m;
+            b.has_cheb = (mode & MODE_CHEB) ? 1 : 0;
+            b.has_tay = (mode & MODE_TAYLOR) ? 1 : 0;
+            b.T = b.has_tay ? p->m + 1 : p->m;
+        }
+        n_items = tc_batch_schedule(bm.data(), count, l2_budget, min_tiles, nullptr);
+        items.assign((size_t)n_items * 4, 0);
+        tc_batch_schedule(bm.data(), count, l2_budget, min_tiles, items.data());
+        vs = batch_table(h, tc_batch_table_bytes(bm.data(), count, n_items));
+        if (vs != VNE_OK) return vs;
+    }
     const int K = batch_streams();
     cudaStream_t user = (cudaStream_t)stream;
     cudaStream_t origin = h->bstreams[0];
@@ -1168,8 +1310,35 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
             Outputs o;
             o.ws = h->bws + off[i];
             o.host_slot = h->bhost + (size_t)i * SC_COUNT;
+            if (pers) {
+                o.phase = 1;
+                o.bmat = &bm[i];
+            }
             vne_status r = run(h, &Rs[i], p, mode, o, h->bstreams[i % K]);
             if (r != VNE_OK) return r;
+        }
+        if (pers) {
+            // join, one launch for every step of every matrix, fork again
+            for (int k = 1; k < K && e == cudaSuccess; ++k) {
+                e = cudaEventRecord(h->bevents[2 + k], h->bstreams[k]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, h->bevents[2 + k], 0);
+            }
+            if (e == cudaSuccess)
+                e = launch_tc_batch(bm.data(), count, items.data(), n_items, h->btab_host,
+                                    h->btab_dev, h->sm_count, origin);
+            if (e == cudaSuccess) ++h->launches;
+            if (e == cudaSuccess) e = cudaEventRecord(h->bevents[0], origin);
+            for (int k = 1; k < K && e == cudaSuccess; ++k)
+                e = cudaStreamWaitEvent(h->bstreams[k], h->bevents[0], 0);
+            if (e != cudaSuccess) return map_err(h, e);
+            for (int i = 0; i < count; ++i) {
+                Outputs o;
+                o.ws = h->bws + off[i];
+                o.host_slot = h->bhost + (size_t)i * SC_COUNT;
+                o.phase = 2;
+                vne_status r = run(h, &Rs[i], p, mode, o, h->bstreams[i % K]);
+                if (r != VNE_OK) return r;
+            }
         }
         for (int k = 1; k < K && e == cudaSuccess; ++k) {
             e = cudaEventRecord(h->bevents[2 + k], h->bstreams[k]);
@@ -1197,6 +1366,8 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         key = mix(key, (uint64_t)method);
         key = mix(key, (uint64_t)(uintptr_t)h->bws);
         key = mix(key, (uint64_t)(uintptr_t)h->bhost);
+        key = mix(key, pers ? (uint64_t)(uintptr_t)h->btab_dev ^ 0x70657273ull : 0ull);
+        key = mix(key, (uint64_t)(l2_budget / 1024.0) ^ ((uint64_t)min_tiles << 40));
         if (!h->graph || key != h->graph_key) {
             if (h->graph) {
                 cudaGraphExecDestroy(h->graph);

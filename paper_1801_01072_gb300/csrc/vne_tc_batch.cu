@@ -61,6 +61,19 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Named barrier `id` over `count` threads that also ANDs a flag over them, so
+// that the epilogue warps leave their loop together.
+__device__ __forceinline__ bool named_bar_and(uint32_t id, uint32_t count, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
+        " bar.red.and.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 // every matrix of the batch gets FLAG_TIMEOUT, and the queue stops
 __device__ void tb_abort(const TcBatchMat* mats, int count, int* abort_g) {
     atomicExch(abort_g, 1);
@@ -191,6 +204,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
             for (int q = 0;; ++q) {
                 const int s = q & 1, a = q & 1;
                 if (!mbar_wait(&slot_full[s], (uint32_t)(q >> 1) & 1u, abort_flag)) {
+                    tb_abort(mats, count, abort_g);
                     *abort_flag = 1;
                     break;
                 }
@@ -202,6 +216,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
                 const uint32_t idesc = idesc_bf16(TB_BM, npad);
                 const int nkb = (int)(M.ldk / TB_BK);
                 if (!mbar_wait(&acc_empty[a], ((uint32_t)(q >> 1) & 1u) ^ 1u, abort_flag)) {
+                    tb_abort(mats, count, abort_g);
                     *abort_flag = 1;
                     break;
                 }
@@ -224,6 +239,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
                     *kt_consumed = kt + 1;
                 }
                 if (!ok) {
+                    tb_abort(mats, count, abort_g);
                     *abort_flag = 1;
                     break;
                 }
@@ -236,10 +252,19 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
         const int et = threadIdx.x - 64;
         for (int q = 0;; ++q) {
             const int s = q & 1, a = q & 1;
-            if (!mbar_wait(&slot_full[s], (uint32_t)(q >> 1) & 1u, abort_flag)) break;
-            const TbSlot sl = slots[s];
+            bool ok = mbar_wait(&slot_full[s], (uint32_t)(q >> 1) & 1u, abort_flag);
+            TbSlot sl = slots[s];
+            if (!ok) sl.valid = 0;
             __syncwarp();
-            if (lane == 0) mbar_arrive_local(&slot_empty[s]);
+            if (lane == 0 && ok) mbar_arrive_local(&slot_empty[s]);
+            if (ok && sl.valid) ok = mbar_wait(&acc_full[a], (uint32_t)(q >> 1) & 1u, abort_flag);
+            // every epilogue thread leaves together: a wait that timed out in
+            // one warp stops all four
+            if (!named_bar_and(1, 128, ok)) {
+                if (et == 0) tb_abort(mats, count, abort_g);
+                *abort_flag = 1;
+                break;
+            }
             if (!sl.valid) break;
             const TcBatchMat& M = mats[sl.j];
             const int t = sl.t, S = M.S, sp = M.s;
@@ -254,7 +279,6 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
             const float* Yp2 = M.Y[(t + 1) % 3];
             float* Yn = M.Y[t % 3];
             __nv_bfloat16* sh_out = M.sh[t & 1];
-            if (!mbar_wait(&acc_full[a], (uint32_t)(q >> 1) & 1u, abort_flag)) break;
             tc_fence_after();
             const int npad = (S + 31) & ~31;
             uint32_t r0[32], r1[32];

@@ -1,5 +1,10 @@
 """Batched estimates of uneven matrices (one call, concurrent streams, CUDA
-graph replay) against the single calls and the oracle."""
+graph replay) against the single calls and the oracle.
+
+These tests pin the stream path (VNE_BATCH_PERSISTENT=0), whose per-matrix
+kernels are those of the single calls, so results agree bit for bit; the
+persistent recurrence of BF16 batches is tested in
+test_gpu_batched_persistent.py."""
 import numpy as np
 import pytest
 import torch
@@ -10,6 +15,11 @@ import synth
 pytestmark = pytest.mark.gpu
 
 vne = pytest.importorskip("paper_1801_01072_gb300")
+
+
+@pytest.fixture(autouse=True)
+def stream_path(monkeypatch):
+    monkeypatch.setenv("VNE_BATCH_PERSISTENT", "0")
 
 
 def mats(sizes, seed0=0):
