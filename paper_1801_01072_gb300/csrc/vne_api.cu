@@ -76,6 +76,7 @@ struct Outputs {
     // phase 2 enqueues the combine on the same workspace after the steps ran
     int phase = 0;
     TcBatchMat* bmat = nullptr;
+    int batch_power = 0;  // phase 1: leave the power products to the batch's launch
     size_t* measured = nullptr;
     char* ws = nullptr;
     double* host_slot = nullptr;
@@ -506,6 +507,14 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     if (pro && do_power) {
         if (pw_xdouble) c.launched(launch_power_init<double>((double*)x0, n, q, p->seed, sc, c.st));
         else c.launched(launch_power_init<float>((float*)x0, n, q, p->seed, sc, c.st));
+        // a batch's persistent power launch takes the products from here
+        const bool batch_pw = out.batch_power && out.phase == 1 && out.bmat && pw_rdt == 2 &&
+                              !pw_xdouble && q == 1 && dense && !cplx && pieces == 1;
+        if (batch_pw) {
+            out.bmat->x[0] = (float*)x0;
+            out.bmat->x[1] = (float*)x1;
+            out.bmat->ppart = ppart;
+        }
         void* xa = x0;
         void* xb = x1;
         const void* Rp = pw_rdt == 2 ? (const void*)Rpc[0] : Rk;
@@ -513,13 +522,13 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         // the products are timed as one span: an event between two of them
         // would stop the next one from starting early (programmatic launch)
         c.prof_begin();
-        if (use_sym) {
+        if (use_sym && !batch_pw) {
             c.launched(launch_power_sym(Rpc, sym_pieces, n, rows_pad, ldk, (const float*)x0,
                                         p->power_iters, sc, symws, u_scale, sym_grid, sym_phased,
                                         c.st));
             if (sym_phased) h->launches += 2 * p->power_iters + 2;
         }
-        for (int it = 0; it <= p->power_iters && c.ok() && !use_sym; ++it) {
+        for (int it = 0; it <= p->power_iters && c.ok() && !use_sym && !batch_pw; ++it) {
             const int fin = it == p->power_iters;
             if (dense)
                 c.launched(launch_power_step_dense(Rp, pw_rdt, n, ldp, xa, xb, pw_xdouble, q, sc,
@@ -1145,16 +1154,19 @@ int batch_streams() {
 
 // Batches run their recurrence in one persistent launch (BF16, dense real
 // matrices, at most 64 step columns) unless VNE_BATCH_PERSISTENT=0 (read at
-// each call).  VNE_BATCH_L2_MB (bf16 R kept active at a time, default 64) and
-// VNE_BATCH_MIN_TILES (default 2 per SM) shape its queue.
+// each call).  VNE_BATCH_L2_MB (bf16 R of the matrices active at a time;
+// default: no limit, every matrix in every round) and VNE_BATCH_MIN_TILES
+// (default 2 per SM) shape its queue.  Measured on 256 matrices of n in
+// [256, 4096]: 23.5 ms per batch with every matrix active, 28.1 ms with a
+// 16-128 MiB active set (fewer independent items per round).
 bool batch_persistent_enabled() {
     const char* e = getenv("VNE_BATCH_PERSISTENT");
     return !(e && e[0] == '0');
 }
 double batch_l2_budget() {
     const char* e = getenv("VNE_BATCH_L2_MB");
-    const double v = e ? atof(e) : 64.0;
-    return (v > 0.0 ? v : 64.0) * 1048576.0;
+    const double v = e ? atof(e) : 0.0;
+    return (v > 0.0 ? v * 1048576.0 : 1e300);
 }
 int batch_min_tiles(int sm_count) {
     const char* e = getenv("VNE_BATCH_MIN_TILES");
@@ -1270,8 +1282,10 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     for (int i = 0; i < count && pers; ++i)
         if (Rs[i].layout != VNE_DENSE || is_complex(Rs[i].dtype)) pers = false;
     std::vector<TcBatchMat> bm;
-    std::vector<int> items;
-    int64_t n_items = 0;
+    std::vector<int> items, pw_items;
+    int64_t n_items = 0, pw_items_n = 0;
+    bool pw_batch = false;
+    size_t pw_tab = 0;  // bytes of the power launch's table, before the recurrence's
     const double l2_budget = batch_l2_budget();
     const int min_tiles = batch_min_tiles(h->sm_count);
     if (pers) {
@@ -1292,7 +1306,18 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         n_items = tc_batch_schedule(bm.data(), count, l2_budget, min_tiles, nullptr);
         items.assign((size_t)n_items * 4, 0);
         tc_batch_schedule(bm.data(), count, l2_budget, min_tiles, items.data());
-        vs = batch_table(h, tc_batch_table_bytes(bm.data(), count, n_items));
+        // the power method in a persistent launch too (one trial, no given u):
+        // its own queue over t + 1 products
+        pw_batch = !(p->u_override > 0.0) && p->power_trials <= 1;
+        if (pw_batch) {
+            std::vector<TcBatchMat> pm(bm);
+            for (TcBatchMat& b : pm) b.T = p->power_iters + 1;
+            pw_items_n = tc_batch_schedule(pm.data(), count, 1e300, 0, nullptr);
+            pw_items.assign((size_t)pw_items_n * 4, 0);
+            tc_batch_schedule(pm.data(), count, 1e300, 0, pw_items.data());
+            pw_tab = (tc_batch_table_bytes(pm.data(), count, pw_items_n) + 255) & ~(size_t)255;
+        }
+        vs = batch_table(h, pw_tab + tc_batch_table_bytes(bm.data(), count, n_items));
         if (vs != VNE_OK) return vs;
     }
     const int K = batch_streams();
@@ -1313,6 +1338,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
             if (pers) {
                 o.phase = 1;
                 o.bmat = &bm[i];
+                o.batch_power = pw_batch ? 1 : 0;
             }
             vne_status r = run(h, &Rs[i], p, mode, o, h->bstreams[i % K]);
             if (r != VNE_OK) return r;
@@ -1323,9 +1349,19 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
                 e = cudaEventRecord(h->bevents[2 + k], h->bstreams[k]);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, h->bevents[2 + k], 0);
             }
+            if (e == cudaSuccess && pw_batch) {
+                std::vector<TcBatchMat> pm(bm);
+                for (TcBatchMat& b : pm) b.T = p->power_iters + 1;
+                const double u_scale = p->u_scale > 0.0 ? p->u_scale : 1.0;
+                e = launch_power_batch(pm.data(), count, pw_items.data(), pw_items_n,
+                                       p->power_iters, u_scale, h->btab_host, h->btab_dev,
+                                       h->sm_count, origin);
+                if (e == cudaSuccess) ++h->launches;
+            }
             if (e == cudaSuccess)
-                e = launch_tc_batch(bm.data(), count, items.data(), n_items, h->btab_host,
-                                    h->btab_dev, h->sm_count, origin);
+                e = launch_tc_batch(bm.data(), count, items.data(), n_items,
+                                    h->btab_host + pw_tab, h->btab_dev + pw_tab, h->sm_count,
+                                    origin);
             if (e == cudaSuccess) ++h->launches;
             if (e == cudaSuccess) e = cudaEventRecord(h->bevents[0], origin);
             for (int k = 1; k < K && e == cudaSuccess; ++k)
@@ -1367,7 +1403,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         key = mix(key, (uint64_t)(uintptr_t)h->bws);
         key = mix(key, (uint64_t)(uintptr_t)h->bhost);
         key = mix(key, pers ? (uint64_t)(uintptr_t)h->btab_dev ^ 0x70657273ull : 0ull);
-        key = mix(key, (uint64_t)(l2_budget / 1024.0) ^ ((uint64_t)min_tiles << 40));
+        key = mix(key, (uint64_t)std::min(l2_budget / 1024.0, 1e18) ^ ((uint64_t)min_tiles << 40));
         if (!h->graph || key != h->graph_key) {
             if (h->graph) {
                 cudaGraphExecDestroy(h->graph);

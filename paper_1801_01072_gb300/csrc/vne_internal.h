@@ -198,6 +198,9 @@ struct TcBatchMat {
     Partials P;               // moment partials, ntiles = rows_pad / 128
     int64_t n, rows_pad, ldk;
     int S, s, m, T, tiles, has_cheb, has_tay;
+    // power method in the batch's persistent launch (NULL x[0]: u is given)
+    float* x[2];              // iterates [n]; x_0 in x[0]
+    double* ppart;            // per-tile norm partials [2][tiles][3]
 };
 // Work items of the queue in launch order, (matrix, step, row tile), built so
 // that every item's dependencies (all tiles of the previous step of its
@@ -213,6 +216,15 @@ size_t tc_batch_table_bytes(const TcBatchMat* mats, int count, int64_t n_items);
 // on `st` (grid: 2 CTAs per SM).
 cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items, int64_t n_items,
                             void* host, void* dev, int sm_count, cudaStream_t st);
+// The power method (Algorithm alg:power, one trial, t + 1 products with the
+// bf16 R) of every matrix with x[0] set, in one persistent launch: items
+// (matrix, product k, 128-row tile) from `items` (the schedule of
+// tc_batch_schedule with T = t + 1); the last product writes p1~, u =
+// min(1, u_scale p1~) and the norm sums to each matrix's scalar block.  The
+// table (host, dev) is laid out as for launch_tc_batch.
+cudaError_t launch_power_batch(const TcBatchMat* mats, int count, const int* items,
+                               int64_t n_items, int power_iters, double u_scale, void* host,
+                               void* dev, int sm_count, cudaStream_t st);
 
 // autotuner: set (BN = 0 clears) the shape of n x ncols steps; candidates
 int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit);

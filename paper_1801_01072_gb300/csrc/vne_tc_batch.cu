@@ -363,6 +363,164 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
+// The power method of a batch (Appendix A, Algorithm alg:power, one trial) in
+// one persistent launch.  Items (matrix j, product k = 0..t, 128-row tile i)
+// come in dependency order from the same kind of queue; a CTA (256 threads)
+// takes one item at a time.  Product k forms y = R x_hat_k, x_hat_k =
+// x_k / ||x_k||, for its 128 rows with the bf16 R (FP32 accumulation, one warp
+// per row, 16-byte loads); ||x_k||^2 is n for the Rademacher start vector,
+// else the sum, in tile order, of the per-tile FP64 partials of product k-1.
+// The tile's partials of ||y||^2 (and, for the last product, x_hat.y and
+// x_hat.x_hat) go to ppart[k & 1][tile]; the CTA that completes the last
+// product of a matrix sums them in tile order into the scalar block and sets
+// p1~ = x_hat.y / x_hat.x_hat and u = min(1, u_scale p1~).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restrict__ mats,
+                                                     const int4* __restrict__ items, int n_items,
+                                                     int count, int* done, int tstride, int* head,
+                                                     int* abort_g, int power_iters,
+                                                     double u_scale) {
+    __shared__ int4 sh_item;
+    __shared__ float sh_inv;
+    __shared__ float wsum[8][3];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) {
+            int it = atomicAdd(head, 1);
+            if (it >= n_items || ld_acquire_gpu(abort_g)) it = -1;
+            int4 w = make_int4(-1, 0, 0, 0);
+            if (it >= 0) {
+                w = items[it];
+                if (w.y >= 2) {  // every tile of product k-1 of matrix j
+                    const int need = mats[w.x].tiles;
+                    const int* cnt = done + (size_t)w.x * tstride + (w.y - 1);
+                    const uint64_t t0 = globaltimer();
+                    for (uint32_t spin = 0; ld_acquire_gpu(cnt) < need; ++spin) {
+                        if ((spin & 63u) == 63u) {
+                            if (ld_acquire_gpu(abort_g)) {
+                                w.x = -1;
+                                break;
+                            }
+                            if (globaltimer() - t0 > kWaitNs) {
+                                tb_abort(mats, count, abort_g);
+                                w.x = -1;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+            if (w.x >= 0) {
+                const TcBatchMat& M = mats[w.x];
+                const int k = w.y - 1;
+                double nrm = (double)M.n;  // ||x_0||^2 of the +-1 start vector
+                if (k > 0) {
+                    nrm = 0.0;
+                    const volatile double* pp = M.ppart + (size_t)((k - 1) & 1) * M.tiles * 3;
+                    for (int i = 0; i < M.tiles; ++i) nrm += pp[3 * i];
+                }
+                sh_inv = (float)(1.0 / sqrt(nrm));
+            }
+            sh_item = w;
+        }
+        __syncthreads();
+        const int4 w = sh_item;
+        if (w.x < 0) break;
+        const TcBatchMat& M = mats[w.x];
+        const int k = w.y - 1, tile = w.z;
+        const bool fin = k == power_iters;
+        const float inv = sh_inv;
+        const float* __restrict__ x = M.x[k & 1];
+        float* __restrict__ y = M.x[(k + 1) & 1];
+        const int64_t n = M.n, ldk = M.ldk, n8 = n & ~(int64_t)7;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // this lane's share of the tile's sums
+        for (int rg = 0; rg < 16; rg += 4) {
+            const int64_t r0 = (int64_t)tile * 128 + warp * 16 + rg;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int64_t c = (int64_t)lane * 8; c < n8; c += 256) {
+                const float4 xa = __ldg(reinterpret_cast<const float4*>(x + c));
+                const float4 xb = __ldg(reinterpret_cast<const float4*>(x + c + 4));
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    const uint4 q = __ldcs(reinterpret_cast<const uint4*>(M.R + (r0 + rr) * ldk + c));
+                    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+                    const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+                    const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+                    float v = acc[rr];
+                    v = fmaf(f0.x, xa.x, v);
+                    v = fmaf(f0.y, xa.y, v);
+                    v = fmaf(f1.x, xa.z, v);
+                    v = fmaf(f1.y, xa.w, v);
+                    v = fmaf(f2.x, xb.x, v);
+                    v = fmaf(f2.y, xb.y, v);
+                    v = fmaf(f3.x, xb.z, v);
+                    v = fmaf(f3.y, xb.w, v);
+                    acc[rr] = v;
+                }
+            }
+            for (int64_t c = n8 + lane; c < n; c += 32) {  // ragged end of the rows
+                const float xv = x[c];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr)
+                    acc[rr] = fmaf(__bfloat162float(M.R[(r0 + rr) * ldk + c]), xv, acc[rr]);
+            }
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const float dot = warp_sum(acc[rr]);
+                const int64_t r = r0 + rr;
+                if (lane == rr && r < n) {
+                    const float yv = dot * inv;
+                    y[r] = yv;
+                    a0 = fmaf(yv, yv, a0);
+                    if (fin) {
+                        const float xh = x[r] * inv;
+                        a1 = fmaf(xh, yv, a1);
+                        a2 = fmaf(xh, xh, a2);
+                    }
+                }
+            }
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        if (lane == 0) {
+            wsum[warp][0] = a0;
+            wsum[warp][1] = a1;
+            wsum[warp][2] = a2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t3[3] = {0.0, 0.0, 0.0};
+            for (int ww = 0; ww < 8; ++ww)
+                for (int v = 0; v < 3; ++v) t3[v] += (double)wsum[ww][v];
+            double* pp = M.ppart + ((size_t)(k & 1) * M.tiles + tile) * 3;
+            pp[0] = t3[0];
+            pp[1] = t3[1];
+            pp[2] = t3[2];
+            __threadfence();
+            const int old = atomicAdd(done + (size_t)w.x * tstride + w.y, 1);
+            if (fin && old == M.tiles - 1) {  // the matrix's last tile: p1~ and u
+                __threadfence();
+                const volatile double* vp = M.ppart + (size_t)(k & 1) * M.tiles * 3;
+                double s3[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < M.tiles; ++i)
+                    for (int v = 0; v < 3; ++v) s3[v] += vp[3 * i + v];
+                double* sc = const_cast<double*>(M.sc);
+                for (int v = 0; v < 3; ++v) sc[SC_NORM + v] = s3[v];
+                const double lam = s3[1] / s3[2];
+                const double u = fmin(1.0, u_scale * lam);
+                sc[SC_LAM] = lam;
+                sc[SC_U] = u;
+                if (!isfinite(lam) || !(u > 0.0) || !isfinite(u))
+                    atomicOr(reinterpret_cast<unsigned long long*>(M.flags),
+                             (unsigned long long)FLAG_BAD_INTERVAL);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side: the queue order, the device table and the launch.
 // ---------------------------------------------------------------------------
 
@@ -465,6 +623,31 @@ cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items,
         reinterpret_cast<const TcBatchMat*>(db + L.mats), reinterpret_cast<const int4*>(db + L.items),
         (int)n_items, count, reinterpret_cast<int*>(db + L.done), L.tstride,
         reinterpret_cast<int*>(db + L.head), reinterpret_cast<int*>(db + L.head) + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_batch(const TcBatchMat* mats, int count, const int* items,
+                               int64_t n_items, int power_iters, double u_scale, void* host,
+                               void* dev, int sm_count, cudaStream_t st) {
+    if (!mats || count < 1 || !items || n_items < 1 || !host || !dev || power_iters < 0)
+        return cudaErrorInvalidValue;
+    const TbLayout L = tb_layout(mats, count, n_items);
+    char* hb = static_cast<char*>(host);
+    std::memset(hb, 0, L.total);
+    for (int j = 0; j < count; ++j)
+        if (!mats[j].x[0] || !mats[j].x[1] || !mats[j].ppart || mats[j].T != power_iters + 1)
+            return cudaErrorInvalidValue;
+    std::memcpy(hb + L.mats, mats, (size_t)count * sizeof(TcBatchMat));
+    std::memcpy(hb + L.items, items, (size_t)n_items * sizeof(int4));
+    cudaError_t e = cudaMemcpyAsync(dev, host, L.total, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    char* db = static_cast<char*>(dev);
+    const int grid = (int)std::min<int64_t>((int64_t)4 * sm_count, n_items);
+    k_power_batch<<<grid, 256, 0, st>>>(
+        reinterpret_cast<const TcBatchMat*>(db + L.mats), reinterpret_cast<const int4*>(db + L.items),
+        (int)n_items, count, reinterpret_cast<int*>(db + L.done), L.tstride,
+        reinterpret_cast<int*>(db + L.head), reinterpret_cast<int*>(db + L.head) + 1, power_iters,
+        u_scale);
     return cudaGetLastError();
 }
 

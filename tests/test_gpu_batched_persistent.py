@@ -4,7 +4,9 @@ every matrix, work items in dependency order) through vne_entropy_batched.
 Each estimate is checked against the oracle's same-probe estimate at the u
 the batch returns (BF16 tolerance 1e-3, matrices of order >= 64), against the
 stream path on the same batch (the same products in another FP32 summation
-order: 1e-4), and for replay determinism (bit-identical).  Sizes cover one
+order: 1e-4 on H, 1e-5 on u), and for replay determinism (bit-identical).  The
+power method of the batch (its own persistent launch) is checked against the
+oracle's FP64 power method at the BF16 path's 1e-3.  Sizes cover one
 tile (n <= 128), ragged last tiles and the largest batch matrices (4096);
 L2 budgets small enough to force many rounds and large enough for one."""
 import numpy as np
@@ -53,7 +55,9 @@ def test_persistent_batch_vs_oracle_and_stream_path(monkeypatch, method, s, l2_m
     monkeypatch.setenv("VNE_BATCH_PERSISTENT", "0")
     hc0, ht0, u0 = vne.entropy_batched(ts, m, s, seed=seed, probe="gaussian", precision="bf16",
                                        method=method)
-    assert np.array_equal(u, u0)
+    # the power method runs in the batch's own persistent launch: the same
+    # bf16 products in another FP32 summation order
+    np.testing.assert_allclose(u, u0, rtol=1e-5)
     for i, (t, R, p) in enumerate(ms):
         rc, rt = oracle_H(R, method, m, s, seed, u[i])
         if rc is not None:
@@ -90,3 +94,14 @@ def test_persistent_batch_many_small_matrices():
     for i in range(0, 256, 17):
         rc, _ = oracle_H(ms[i][1], "chebyshev", m, s, seed, u[i])
         assert abs(hc[i] - rc) <= 1e-3 * abs(rc), (i, sizes[i], hc[i], rc)
+
+
+def test_persistent_power_method_vs_oracle():
+    from oracle import rng as R_
+    sizes = [64, 129, 1000, 2048, 4096, 300]
+    ms = mats(sizes, seed0=500)
+    _, _, u = vne.entropy_batched([t for t, _, _ in ms], 4, 16, seed=7, probe="gaussian",
+                                  precision="bf16", power_iters=30)
+    for i, (t, R, p) in enumerate(ms):
+        lam, _ = O.power_method(R, R_.power_start(R.shape[0], 1, 7), 30)
+        assert abs(u[i] - min(1.0, lam)) <= 1e-3 * lam, (i, sizes[i], u[i], lam)
