@@ -1168,6 +1168,18 @@ double batch_l2_budget() {
     const double v = e ? atof(e) : 0.0;
     return (v > 0.0 ? v * 1048576.0 : 1e300);
 }
+// The power launch's queue: VNE_BATCH_POWER_L2_MB (default: no limit) and
+// VNE_BATCH_POWER_MIN_TILES (default 4 per SM).
+double batch_power_l2_budget() {
+    const char* e = getenv("VNE_BATCH_POWER_L2_MB");
+    const double v = e ? atof(e) : 0.0;
+    return (v > 0.0 ? v * 1048576.0 : 1e300);
+}
+int batch_power_min_tiles(int sm_count) {
+    const char* e = getenv("VNE_BATCH_POWER_MIN_TILES");
+    const int v = e ? atoi(e) : 4 * sm_count;
+    return v >= 0 ? v : 4 * sm_count;
+}
 int batch_min_tiles(int sm_count) {
     const char* e = getenv("VNE_BATCH_MIN_TILES");
     const int v = e ? atoi(e) : 2 * sm_count;
@@ -1288,6 +1300,8 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     size_t pw_tab = 0;  // bytes of the power launch's table, before the recurrence's
     const double l2_budget = batch_l2_budget();
     const int min_tiles = batch_min_tiles(h->sm_count);
+    const double pw_budget = batch_power_l2_budget();
+    const int pw_min_tiles = batch_power_min_tiles(h->sm_count);
     if (pers) {
         bm.assign((size_t)count, TcBatchMat{});
         for (int i = 0; i < count; ++i) {
@@ -1312,9 +1326,9 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         if (pw_batch) {
             std::vector<TcBatchMat> pm(bm);
             for (TcBatchMat& b : pm) b.T = p->power_iters + 1;
-            pw_items_n = tc_batch_schedule(pm.data(), count, 1e300, 0, nullptr);
+            pw_items_n = tc_batch_schedule(pm.data(), count, pw_budget, pw_min_tiles, nullptr);
             pw_items.assign((size_t)pw_items_n * 4, 0);
-            tc_batch_schedule(pm.data(), count, 1e300, 0, pw_items.data());
+            tc_batch_schedule(pm.data(), count, pw_budget, pw_min_tiles, pw_items.data());
             pw_tab = (tc_batch_table_bytes(pm.data(), count, pw_items_n) + 255) & ~(size_t)255;
         }
         vs = batch_table(h, pw_tab + tc_batch_table_bytes(bm.data(), count, n_items));
@@ -1404,6 +1418,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         key = mix(key, (uint64_t)(uintptr_t)h->bhost);
         key = mix(key, pers ? (uint64_t)(uintptr_t)h->btab_dev ^ 0x70657273ull : 0ull);
         key = mix(key, (uint64_t)std::min(l2_budget / 1024.0, 1e18) ^ ((uint64_t)min_tiles << 40));
+        key = mix(key, (uint64_t)std::min(pw_budget / 1024.0, 1e18) ^ ((uint64_t)pw_min_tiles << 40));
         if (!h->graph || key != h->graph_key) {
             if (h->graph) {
                 cudaGraphExecDestroy(h->graph);
