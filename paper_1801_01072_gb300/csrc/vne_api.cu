@@ -1168,6 +1168,15 @@ double batch_l2_budget() {
     const double v = e ? atof(e) : 0.0;
     return (v > 0.0 ? v * 1048576.0 : 1e300);
 }
+// Test hook of the persistent launches' bounded waits: VNE_BATCH_TEST_STALL=1
+// (recurrence) or 2 (power method) makes every dependency wait for one tile
+// more than the matrix has, so the waits expire and the call returns
+// VNE_ERR_TIMEOUT; the GPU is not faulted and the next call runs normally.
+int batch_test_stall() {
+    const char* e = getenv("VNE_BATCH_TEST_STALL");
+    return e ? atoi(e) : 0;
+}
+
 // The power launch's queue: VNE_BATCH_POWER_L2_MB (default: no limit) and
 // VNE_BATCH_POWER_MIN_TILES (default 4 per SM).
 double batch_power_l2_budget() {
@@ -1301,6 +1310,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     const double l2_budget = batch_l2_budget();
     const int min_tiles = batch_min_tiles(h->sm_count);
     const double pw_budget = batch_power_l2_budget();
+    const int stall = batch_test_stall();
     const int pw_min_tiles = batch_power_min_tiles(h->sm_count);
     if (pers) {
         bm.assign((size_t)count, TcBatchMat{});
@@ -1369,13 +1379,13 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
                 const double u_scale = p->u_scale > 0.0 ? p->u_scale : 1.0;
                 e = launch_power_batch(pm.data(), count, pw_items.data(), pw_items_n,
                                        p->power_iters, u_scale, h->btab_host, h->btab_dev,
-                                       h->sm_count, origin);
+                                       h->sm_count, origin, stall == 2 ? 1 : 0);
                 if (e == cudaSuccess) ++h->launches;
             }
             if (e == cudaSuccess)
                 e = launch_tc_batch(bm.data(), count, items.data(), n_items,
                                     h->btab_host + pw_tab, h->btab_dev + pw_tab, h->sm_count,
-                                    origin);
+                                    origin, stall == 1 ? 1 : 0);
             if (e == cudaSuccess) ++h->launches;
             if (e == cudaSuccess) e = cudaEventRecord(h->bevents[0], origin);
             for (int k = 1; k < K && e == cudaSuccess; ++k)
@@ -1419,6 +1429,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         key = mix(key, pers ? (uint64_t)(uintptr_t)h->btab_dev ^ 0x70657273ull : 0ull);
         key = mix(key, (uint64_t)std::min(l2_budget / 1024.0, 1e18) ^ ((uint64_t)min_tiles << 40));
         key = mix(key, (uint64_t)std::min(pw_budget / 1024.0, 1e18) ^ ((uint64_t)pw_min_tiles << 40));
+        key = mix(key, (uint64_t)stall);
         if (!h->graph || key != h->graph_key) {
             if (h->graph) {
                 cudaGraphExecDestroy(h->graph);

@@ -214,8 +214,11 @@ size_t tc_batch_table_bytes(const TcBatchMat* mats, int count, int64_t n_items);
 // Fills the table in host memory `host` (pinned, tc_batch_table_bytes) for the
 // device copy `dev`, copies it, clears the counters and launches the kernel
 // on `st` (grid: 2 CTAs per SM).
+// dep_extra > 0 raises every dependency's required count beyond what can
+// arrive (a test of the bounded waits: the launch times out, FLAG_TIMEOUT).
 cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items, int64_t n_items,
-                            void* host, void* dev, int sm_count, cudaStream_t st);
+                            void* host, void* dev, int sm_count, cudaStream_t st,
+                            int dep_extra = 0);
 // The power method (Algorithm alg:power, one trial, t + 1 products with the
 // bf16 R) of every matrix with x[0] set, in one persistent launch: items
 // (matrix, product k, 128-row tile) from `items` (the schedule of
@@ -224,7 +227,7 @@ cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items,
 // table (host, dev) is laid out as for launch_tc_batch.
 cudaError_t launch_power_batch(const TcBatchMat* mats, int count, const int* items,
                                int64_t n_items, int power_iters, double u_scale, void* host,
-                               void* dev, int sm_count, cudaStream_t st);
+                               void* dev, int sm_count, cudaStream_t st, int dep_extra = 0);
 
 // autotuner: set (BN = 0 clears) the shape of n x ncols steps; candidates
 int tc_set_tuned(int64_t n, int ncols, int BN, int CM, int CN, int ksplit);

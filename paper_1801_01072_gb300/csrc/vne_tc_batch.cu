@@ -85,7 +85,7 @@ __device__ void tb_abort(const TcBatchMat* mats, int count, int* abort_g) {
 __global__ void __launch_bounds__(TB_THREADS, 2)
     k_tc_batch(const CUtensorMap* __restrict__ maps, const TcBatchMat* __restrict__ mats,
                const int4* __restrict__ items, int n_items, int count, int* done, int tstride,
-               int* head, int* abort_g) {
+               int* head, int* abort_g, int dep_extra) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t* tail = smem + TB_STAGES * TB_STAGE;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
                 if (it < n_items) {
                     w = items[it];
                     if (w.y >= 2) {  // every tile of step t-1 of matrix j
-                        const int need = mats[w.x].tiles;
+                        const int need = mats[w.x].tiles + dep_extra;
                         const int* cnt = done + (size_t)w.x * tstride + (w.y - 1);
                         const uint64_t t0 = globaltimer();
                         for (uint32_t spin = 0; ld_acquire_gpu(cnt) < need; ++spin) {
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restric
                                                      const int4* __restrict__ items, int n_items,
                                                      int count, int* done, int tstride, int* head,
                                                      int* abort_g, int power_iters,
-                                                     double u_scale) {
+                                                     double u_scale, int dep_extra) {
     __shared__ int4 sh_item;
     __shared__ float sh_inv;
     __shared__ float wsum[8][3];
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restric
             if (it >= 0) {
                 w = items[it];
                 if (w.y >= 2) {  // every tile of product k-1 of matrix j
-                    const int need = mats[w.x].tiles;
+                    const int need = mats[w.x].tiles + dep_extra;
                     const int* cnt = done + (size_t)w.x * tstride + (w.y - 1);
                     const uint64_t t0 = globaltimer();
                     for (uint32_t spin = 0; ld_acquire_gpu(cnt) < need; ++spin) {
@@ -594,7 +594,7 @@ size_t tc_batch_table_bytes(const TcBatchMat* mats, int count, int64_t n_items) 
 }
 
 cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items, int64_t n_items,
-                            void* host, void* dev, int sm_count, cudaStream_t st) {
+                            void* host, void* dev, int sm_count, cudaStream_t st, int dep_extra) {
     if (!mats || count < 1 || !items || n_items < 1 || !host || !dev) return cudaErrorInvalidValue;
     const TbLayout L = tb_layout(mats, count, n_items);
     char* hb = static_cast<char*>(host);
@@ -622,13 +622,13 @@ cudaError_t launch_tc_batch(const TcBatchMat* mats, int count, const int* items,
         reinterpret_cast<const CUtensorMap*>(db + L.maps),
         reinterpret_cast<const TcBatchMat*>(db + L.mats), reinterpret_cast<const int4*>(db + L.items),
         (int)n_items, count, reinterpret_cast<int*>(db + L.done), L.tstride,
-        reinterpret_cast<int*>(db + L.head), reinterpret_cast<int*>(db + L.head) + 1);
+        reinterpret_cast<int*>(db + L.head), reinterpret_cast<int*>(db + L.head) + 1, dep_extra);
     return cudaGetLastError();
 }
 
 cudaError_t launch_power_batch(const TcBatchMat* mats, int count, const int* items,
                                int64_t n_items, int power_iters, double u_scale, void* host,
-                               void* dev, int sm_count, cudaStream_t st) {
+                               void* dev, int sm_count, cudaStream_t st, int dep_extra) {
     if (!mats || count < 1 || !items || n_items < 1 || !host || !dev || power_iters < 0)
         return cudaErrorInvalidValue;
     const TbLayout L = tb_layout(mats, count, n_items);
@@ -647,7 +647,7 @@ cudaError_t launch_power_batch(const TcBatchMat* mats, int count, const int* ite
         reinterpret_cast<const TcBatchMat*>(db + L.mats), reinterpret_cast<const int4*>(db + L.items),
         (int)n_items, count, reinterpret_cast<int*>(db + L.done), L.tstride,
         reinterpret_cast<int*>(db + L.head), reinterpret_cast<int*>(db + L.head) + 1, power_iters,
-        u_scale);
+        u_scale, dep_extra);
     return cudaGetLastError();
 }
 

@@ -105,3 +105,45 @@ def test_persistent_power_method_vs_oracle():
     for i, (t, R, p) in enumerate(ms):
         lam, _ = O.power_method(R, R_.power_start(R.shape[0], 1, 7), 30)
         assert abs(u[i] - min(1.0, lam)) <= 1e-3 * lam, (i, sizes[i], u[i], lam)
+
+
+@pytest.mark.parametrize("which", ["1", "2"])
+def test_stalled_dependency_times_out_and_context_survives(monkeypatch, which):
+    """A dependency that can never be met (VNE_BATCH_TEST_STALL: one tile more
+    than the matrix has; 1 = recurrence launch, 2 = power launch) ends each
+    bounded wait after its 2-s deadline: the batch returns VNE_ERR_TIMEOUT, and
+    the next batch on the same handle runs normally."""
+    import time
+    ms = mats([200, 333, 129], seed0=700)
+    ts = [t for t, _, _ in ms]
+    monkeypatch.setenv("VNE_BATCH_TEST_STALL", which)
+    t0 = time.perf_counter()
+    with pytest.raises(vne.VneError) as err:
+        vne.entropy_batched(ts, 6, 16, seed=3, probe="gaussian", precision="bf16")
+    dt = time.perf_counter() - t0
+    assert err.value.status == 6, err.value  # VNE_ERR_TIMEOUT
+    assert 1.5 < dt < 60.0
+    monkeypatch.delenv("VNE_BATCH_TEST_STALL")
+    hc, _, u = vne.entropy_batched(ts, 6, 16, seed=3, probe="gaussian", precision="bf16")
+    for i, (t, R, p) in enumerate(ms):
+        rc, _ = oracle_H(R, "chebyshev", 6, 16, 3, u[i])
+        assert abs(hc[i] - rc) <= 1e-3 * abs(rc), (i, hc[i], rc)
+
+
+@pytest.mark.parametrize("precision,method,s", [("bf16", "both", 48), ("bf16x3", "chebyshev", 16)])
+def test_batches_outside_the_persistent_path_equal_single_calls(precision, method, s):
+    """More than 64 step columns (both estimators, s = 48) or a split precision:
+    the batch runs the per-matrix kernels on the streams, bit-identical to the
+    single calls."""
+    ms = mats([200, 96, 333], seed0=800)
+    m, seed = 8, 4
+    hc, ht, u = vne.entropy_batched([t for t, _, _ in ms], m, s, seed=seed, probe="gaussian",
+                                    precision=precision, method=method)
+    kw = dict(seed=seed, probe="gaussian", precision=precision)
+    for i, (t, R, p) in enumerate(ms):
+        if method == "both":
+            one = vne.entropy_both(t, m, s, **kw)
+            assert (hc[i], ht[i], u[i]) == (one.H_chebyshev, one.H_taylor, one.u), i
+        else:
+            one = vne.entropy_chebyshev(t, m, s, **kw)
+            assert (hc[i], u[i]) == (one.H, one.u), i
