@@ -368,13 +368,15 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
 // come in dependency order from the same kind of queue; a CTA (256 threads)
 // takes one item at a time.  Product k forms y = R x_hat_k, x_hat_k =
 // x_k / ||x_k||, for its 128 rows with the bf16 R (FP32 accumulation, one warp
-// per row, 16-byte loads); ||x_k||^2 is n for the Rademacher start vector,
+// per row, a warp's 8 rows in flight together, 16-byte loads); ||x_k||^2 is n for the Rademacher start vector,
 // else the sum, in tile order, of the per-tile FP64 partials of product k-1.
 // The tile's partials of ||y||^2 (and, for the last product, x_hat.y and
 // x_hat.x_hat) go to ppart[k & 1][tile]; the CTA that completes the last
 // product of a matrix sums them in tile order into the scalar block and sets
 // p1~ = x_hat.y / x_hat.x_hat and u = min(1, u_scale p1~).
 // ---------------------------------------------------------------------------
+constexpr int TB_PW_ROWS = 8;  // rows of a warp in flight together (16-byte loads each)
+
 __global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restrict__ mats,
                                                      const int4* __restrict__ items, int n_items,
                                                      int count, int* done, int tstride, int* head,
@@ -434,14 +436,16 @@ __global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restric
         float* __restrict__ y = M.x[(k + 1) & 1];
         const int64_t n = M.n, ldk = M.ldk, n8 = n & ~(int64_t)7;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // this lane's share of the tile's sums
-        for (int rg = 0; rg < 16; rg += 4) {
+        for (int rg = 0; rg < 16; rg += TB_PW_ROWS) {
             const int64_t r0 = (int64_t)tile * 128 + warp * 16 + rg;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            float acc[TB_PW_ROWS];
+#pragma unroll
+            for (int rr = 0; rr < TB_PW_ROWS; ++rr) acc[rr] = 0.f;
             for (int64_t c = (int64_t)lane * 8; c < n8; c += 256) {
                 const float4 xa = __ldg(reinterpret_cast<const float4*>(x + c));
                 const float4 xb = __ldg(reinterpret_cast<const float4*>(x + c + 4));
 #pragma unroll
-                for (int rr = 0; rr < 4; ++rr) {
+                for (int rr = 0; rr < TB_PW_ROWS; ++rr) {
                     const uint4 q = __ldcs(reinterpret_cast<const uint4*>(M.R + (r0 + rr) * ldk + c));
                     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
                     const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
@@ -461,11 +465,11 @@ __global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restric
             for (int64_t c = n8 + lane; c < n; c += 32) {  // ragged end of the rows
                 const float xv = x[c];
 #pragma unroll
-                for (int rr = 0; rr < 4; ++rr)
+                for (int rr = 0; rr < TB_PW_ROWS; ++rr)
                     acc[rr] = fmaf(__bfloat162float(M.R[(r0 + rr) * ldk + c]), xv, acc[rr]);
             }
 #pragma unroll
-            for (int rr = 0; rr < 4; ++rr) {
+            for (int rr = 0; rr < TB_PW_ROWS; ++rr) {
                 const float dot = warp_sum(acc[rr]);
                 const int64_t r = r0 + rr;
                 if (lane == rr && r < n) {
