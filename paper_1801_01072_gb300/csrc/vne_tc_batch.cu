@@ -290,39 +290,39 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
             named_bar_sync(1, 128);
             if (et == 0) mbar_arrive_local(&acc_empty[a]);  // the accumulator is free
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh)
+            for (int hh = 0; hh < 2; ++hh) {
+                if (hh * 32 >= S) break;
+                // loads predicated per column (no branches), so that a chunk's
+                // operand loads can all be in flight together
+                float v[32];
 #pragma unroll
-            for (int qq = 0; qq < 32; ++qq) {
-                const int c = hh * 32 + qq;
-                if (c >= S) continue;
-                const float z = __uint_as_float(hh == 0 ? r0[qq] : r1[qq]);
-                const bool is_cheb = cheb_on && c < sp;
-                const bool is_tay = M.has_tay && c >= tay0 && c < tay0 + sp;
-                float v = 0.f;
-                if (is_cheb || is_tay) {
-                    const float g = row_ok ? M.G[(size_t)(c % sp) * n + row] : 0.f;
-                    float y;
+                for (int qq = 0; qq < 32; ++qq) {
+                    const int c = hh * 32 + qq;
+                    const bool is_cheb = c < S && cheb_on && c < sp;
+                    const bool is_tay = c < S && M.has_tay && c >= tay0 && c < tay0 + sp;
+                    const bool on = row_ok && (is_cheb || is_tay);
+                    const int gc = c >= sp ? c - sp : c;  // the column's probe
+                    const float z = __uint_as_float(hh == 0 ? r0[qq] : r1[qq]);
+                    const float g = on ? M.G[(size_t)gc * n + row] : 0.f;
+                    const bool need1 = on && (is_tay || t > 1);
+                    const float y1 = need1 ? Yp[(size_t)c * n + row] : 0.f;
+                    const float y2 = (on && is_cheb && t > 1) ? Yp2[(size_t)c * n + row] : 0.f;
+                    float y, vv;
                     if (is_cheb) {
-                        if (t == 1) {
-                            y = fmaf(fa, z, -g);
-                        } else {
-                            const float y1 = row_ok ? Yp[(size_t)c * n + row] : 0.f;
-                            const float y2 = row_ok ? Yp2[(size_t)c * n + row] : 0.f;
-                            y = 2.f * fmaf(fa, z, -y1) - y2;
-                        }
-                        v = g * y;
+                        y = t == 1 ? fmaf(fa, z, -g) : 2.f * fmaf(fa, z, -y1) - y2;
+                        vv = g * y;
                     } else {
-                        const float y1 = row_ok ? Yp[(size_t)c * n + row] : 0.f;
                         y = fmaf(-z, finvu, y1);
-                        v = g * z;
+                        vv = g * z;
                     }
-                    if (row_ok) {
+                    v[qq] = on ? vv : 0.f;
+                    if (on) {
                         Yn[(size_t)c * n + row] = y;
                         sh_out[(size_t)c * ldk + row] = __float2bfloat16_rn(y);
                     }
                 }
-                v = warp_sum(v);
-                if (lane == 0) red[quarter * TB_BNMAX + c] = v;
+                transpose_reduce32(v);  // lane l: the 32-row sum of column hh*32 + l
+                red[quarter * TB_BNMAX + hh * 32 + lane] = v[0];
             }
             // the shadows are read by later items through the async proxy
             fence_proxy_async_global();
@@ -375,7 +375,9 @@ __global__ void __launch_bounds__(TB_THREADS, 2)
 // product of a matrix sums them in tile order into the scalar block and sets
 // p1~ = x_hat.y / x_hat.x_hat and u = min(1, u_scale p1~).
 // ---------------------------------------------------------------------------
-constexpr int TB_PW_ROWS = 8;  // rows of a warp in flight together (16-byte loads each)
+// rows of a warp in flight together (the power method of the 256-matrix
+// benchmark batch: 8 rows 8.3 ms, 4 rows 9.3 ms, 16 rows 8.9 ms)
+constexpr int TB_PW_ROWS = 8;
 
 __global__ void __launch_bounds__(256) k_power_batch(const TcBatchMat* __restrict__ mats,
                                                      const int4* __restrict__ items, int n_items,
