@@ -1220,6 +1220,32 @@ vne_status batch_table(vne_handle* h, size_t bytes) {
     return VNE_OK;
 }
 
+// The identity of a captured batch graph: the matrices' sizes, addresses and
+// layouts, the parameters, the method, the handle's batch buffers and the
+// queue settings; a call with the same key replays the graph.
+uint64_t batch_key(const vne_handle* h, const vne_matrix* Rs, int count, const vne_params* p,
+                   int method, bool pers, double l2_budget, int min_tiles, double pw_budget,
+                   int pw_min_tiles, int stall) {
+    uint64_t key = mix(0x9E3779B97F4A7C15ull, (uint64_t)count);
+    for (int i = 0; i < count; ++i) {
+        key = mix(key, (uint64_t)Rs[i].n);
+        key = mix(key, (uint64_t)(uintptr_t)Rs[i].data);
+        key = mix(key, (uint64_t)Rs[i].ld);
+        key = mix(key, ((uint64_t)Rs[i].layout << 32) ^ ((uint64_t)Rs[i].dtype << 16) ^
+                           (uint64_t)Rs[i].n_diags);
+    }
+    const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
+    for (size_t b = 0; b < sizeof(vne_params); ++b) key = mix(key, pb[b] + (b << 8));
+    key = mix(key, (uint64_t)method);
+    key = mix(key, (uint64_t)(uintptr_t)h->bws);
+    key = mix(key, (uint64_t)(uintptr_t)h->bhost);
+    key = mix(key, pers ? (uint64_t)(uintptr_t)h->btab_dev ^ 0x70657273ull : 0ull);
+    key = mix(key, (uint64_t)std::min(l2_budget / 1024.0, 1e18) ^ ((uint64_t)min_tiles << 40));
+    key = mix(key, (uint64_t)std::min(pw_budget / 1024.0, 1e18) ^ ((uint64_t)pw_min_tiles << 40));
+    key = mix(key, (uint64_t)stall);
+    return key;
+}
+
 vne_status batch_resources(vne_handle* h, size_t ws_bytes, size_t count) {
     const int K = batch_streams();
     while ((int)h->bstreams.size() < K) {
@@ -1284,6 +1310,47 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     for (int i = 0; i < count; ++i)
         if (Rs[i].memory != VNE_MEM_DEVICE) return VNE_ERR_UNSUPPORTED;
     DeviceGuard guard(h->device);
+    // the recurrence (and power method) of the whole batch in persistent launches
+    const int S_all = mode == MODE_BOTH ? 2 * p->s : p->s;
+    bool pers = batch_persistent_enabled() && p->precision == VNE_PREC_BF16 && S_all <= 64;
+    for (int i = 0; i < count && pers; ++i)
+        if (Rs[i].layout != VNE_DENSE || is_complex(Rs[i].dtype)) pers = false;
+    const double l2_budget = batch_l2_budget();
+    const int min_tiles = batch_min_tiles(h->sm_count);
+    const double pw_budget = batch_power_l2_budget();
+    const int pw_min_tiles = batch_power_min_tiles(h->sm_count);
+    const int stall = batch_test_stall();
+    // results of the batch from the pinned host slots
+    auto collect = [&]() -> vne_status {
+        vne_status first = VNE_OK;
+        for (int i = 0; i < count; ++i) {
+            const double* hs = h->bhost + (size_t)i * SC_COUNT;
+            vne_status fs = slot_status(hs, p->check_trace);
+            if (fs != VNE_OK && first == VNE_OK) first = fs;
+            const double nan = std::nan("");
+            if (H_cheb && (mode & MODE_CHEB)) H_cheb[i] = fs == VNE_OK ? hs[SC_H_CHEB] : nan;
+            if (H_taylor && (mode & MODE_TAYLOR)) H_taylor[i] = fs == VNE_OK ? hs[SC_H_TAYLOR] : nan;
+            if (u_out) u_out[i] = hs[SC_U];
+        }
+        return first;
+    };
+    // replay: the same batch as the captured graph needs no planning at all
+    if (use_graph && h->graph && !h->bstreams.empty() &&
+        batch_key(h, Rs, count, p, method, pers, l2_budget, min_tiles, pw_budget, pw_min_tiles,
+                  stall) == h->graph_key) {
+        cudaStream_t user = (cudaStream_t)stream, origin = h->bstreams[0];
+        cudaError_t e = cudaEventRecord(h->bevents[1], user);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, h->bevents[1], 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(h->graph, origin);
+        if (e == cudaSuccess) e = cudaEventRecord(h->bevents[1], origin);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->bevents[1], 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(user);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return map_err(h, e);
+        }
+        return collect();
+    }
     // workspace of every matrix (the same plan as a single call)
     std::vector<size_t> off((size_t)count + 1, 0);
     for (int i = 0; i < count; ++i) {
@@ -1297,21 +1364,11 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
     }
     vne_status vs = batch_resources(h, off[count], (size_t)count);
     if (vs != VNE_OK) return vs;
-    // the recurrence of the whole batch in one persistent launch
-    const int S_all = mode == MODE_BOTH ? 2 * p->s : p->s;
-    bool pers = batch_persistent_enabled() && p->precision == VNE_PREC_BF16 && S_all <= 64;
-    for (int i = 0; i < count && pers; ++i)
-        if (Rs[i].layout != VNE_DENSE || is_complex(Rs[i].dtype)) pers = false;
     std::vector<TcBatchMat> bm;
     std::vector<int> items, pw_items;
     int64_t n_items = 0, pw_items_n = 0;
     bool pw_batch = false;
     size_t pw_tab = 0;  // bytes of the power launch's table, before the recurrence's
-    const double l2_budget = batch_l2_budget();
-    const int min_tiles = batch_min_tiles(h->sm_count);
-    const double pw_budget = batch_power_l2_budget();
-    const int stall = batch_test_stall();
-    const int pw_min_tiles = batch_power_min_tiles(h->sm_count);
     if (pers) {
         bm.assign((size_t)count, TcBatchMat{});
         for (int i = 0; i < count; ++i) {
@@ -1413,23 +1470,8 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         return map_err(h, e);
     }
     if (use_graph) {
-        uint64_t key = mix(0x9E3779B97F4A7C15ull, (uint64_t)count);
-        for (int i = 0; i < count; ++i) {
-            key = mix(key, (uint64_t)Rs[i].n);
-            key = mix(key, (uint64_t)(uintptr_t)Rs[i].data);
-            key = mix(key, (uint64_t)Rs[i].ld);
-            key = mix(key, ((uint64_t)Rs[i].layout << 32) ^ ((uint64_t)Rs[i].dtype << 16) ^
-                               (uint64_t)Rs[i].n_diags);
-        }
-        const unsigned char* pb = reinterpret_cast<const unsigned char*>(p);
-        for (size_t b = 0; b < sizeof(vne_params); ++b) key = mix(key, pb[b] + (b << 8));
-        key = mix(key, (uint64_t)method);
-        key = mix(key, (uint64_t)(uintptr_t)h->bws);
-        key = mix(key, (uint64_t)(uintptr_t)h->bhost);
-        key = mix(key, pers ? (uint64_t)(uintptr_t)h->btab_dev ^ 0x70657273ull : 0ull);
-        key = mix(key, (uint64_t)std::min(l2_budget / 1024.0, 1e18) ^ ((uint64_t)min_tiles << 40));
-        key = mix(key, (uint64_t)std::min(pw_budget / 1024.0, 1e18) ^ ((uint64_t)pw_min_tiles << 40));
-        key = mix(key, (uint64_t)stall);
+        const uint64_t key = batch_key(h, Rs, count, p, method, pers, l2_budget, min_tiles,
+                                       pw_budget, pw_min_tiles, stall);
         if (!h->graph || key != h->graph_key) {
             if (h->graph) {
                 cudaGraphExecDestroy(h->graph);
@@ -1479,17 +1521,7 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         cudaGetLastError();
         return map_err(h, e);
     }
-    vne_status first = VNE_OK;
-    for (int i = 0; i < count; ++i) {
-        const double* hs = h->bhost + (size_t)i * SC_COUNT;
-        vne_status fs = slot_status(hs, p->check_trace);
-        if (fs != VNE_OK && first == VNE_OK) first = fs;
-        const double nan = std::nan("");
-        if (H_cheb && (mode & MODE_CHEB)) H_cheb[i] = fs == VNE_OK ? hs[SC_H_CHEB] : nan;
-        if (H_taylor && (mode & MODE_TAYLOR)) H_taylor[i] = fs == VNE_OK ? hs[SC_H_TAYLOR] : nan;
-        if (u_out) u_out[i] = hs[SC_U];
-    }
-    return first;
+    return collect();
 }
 
 vne_status vne_tc_shape(int64_t n, int32_t ncols, int32_t sm_count, int32_t* shape_out) {
