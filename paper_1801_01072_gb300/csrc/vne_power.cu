@@ -546,7 +546,8 @@ __global__ void __launch_bounds__(kSymThreads, 1) k_power_sym(const __grid_const
     const uint32_t stage_bytes = (uint32_t)NP * kSymTileBytes;  // the pieces' tiles, one after the other
     float* xsm = reinterpret_cast<float*>(ring + (size_t)NS * stage_bytes);  // nb*128
     __shared__ uint64_t full[kSymMaxStages];
-    __shared__ float colsm[2][kSymWarps][kSymT];  // per-warp column partials (two tiles); group sums
+    // 16-byte aligned for its float4 accesses, whatever precedes it
+    __shared__ __align__(16) float colsm[2][kSymWarps][kSymT];  // per-warp column partials (two tiles); group sums
     __shared__ int flag_sh;
     __shared__ double red_sh[kSymWarps];
     __shared__ uint32_t tl[kSymMaxTiles];  // this CTA's tiles: (I << 16) | K
