@@ -1089,6 +1089,7 @@ def run_gpu(args):
     ms_max = float(t.item())
 
     # ---- end to end: host-resident R, copies inside the call ----
+    # (a) one single call per matrix: its copy, then its estimate
     Rpin = torch.as_tensor(Rh).pin_memory()
     step(Rpin)
     torch.cuda.synchronize()
@@ -1101,9 +1102,31 @@ def run_gpu(args):
         step(Rpin)
     ev3.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = ev2.elapsed_time(ev3) / e2e_steps
-    e2e_wall = (time.perf_counter() - e0) / e2e_steps * 1e3
-    e2e_ms = max(e2e_ms, e2e_wall)
+    e2e_single_ms = max(ev2.elapsed_time(ev3) / e2e_steps,
+                        (time.perf_counter() - e0) / e2e_steps * 1e3)
+    # (b) the sequence call over host matrices (two pinned buffers,
+    # alternating): each matrix's transfer runs while the previous one is
+    # estimated; the first transfer is not hidden and is counted
+    Rpin2 = Rpin.clone().pin_memory()
+    seq_len = max(8, args.steps // 4)
+    seq = [Rpin if i % 2 == 0 else Rpin2 for i in range(seq_len)]
+    meth = "both" if dense else "chebyshev"
+
+    def run_seq():
+        return vne.entropy_sequence(seq, m, s, seed=seed, probe=w["probe"], precision=prec,
+                                    power_iters=w["power_iters"], method=meth,
+                                    layouts=[layout] * seq_len)
+    seq_out = run_seq()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    ev2.record(stream)
+    seq_out = run_seq()
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max(ev2.elapsed_time(ev3), (time.perf_counter() - e0) * 1e3) / seq_len
+    # the sequence's estimates are the single call's
+    one = step(Rpin)
+    same = bool(np.all(seq_out[0] == (one.H_chebyshev if dense else one.H)))
 
     # ---- accuracy of this precision against the FP64 path on the GPU ----
     rel_err = None
@@ -1214,7 +1237,13 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (R is %.0f MB)" % (Rh.nbytes / 1e6),
                    "parallelism": f"independent matrices, {world} GPU(s)"},
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
-                "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": 200 * 8},
+                "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": 200 * 8,
+                "api": f"entropy_sequence over {seq_len} pinned host matrices (two buffers, "
+                       "alternating): each transfer overlaps the previous estimate",
+                "equals_single_calls": same,
+                "single_call": {"value": world * 1e3 / e2e_single_ms, "unit": "entropies/s",
+                                "api": "entropy_both / entropy_chebyshev on one pinned host "
+                                       "matrix: copy, then estimate"}},
         "gpu_launches": int(n_launch),
         "phases_ms_per_step": {"recurrence": k_ms / args.steps, "power_method": p_ms / args.steps,
                                "other": ms_max / args.steps - (k_ms + p_ms) / args.steps},

@@ -251,6 +251,28 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
                                const vne_params* p, int32_t method, int32_t use_graph,
                                double* H_cheb, double* H_taylor, double* u_out, void* stream);
 
+/* A sequence of density matrices estimated one after another (Algorithms
+ * 1a/1b with alg:power, applied to each), with the transfers of HOST-resident
+ * matrices hidden behind the estimates.  Rs[i] (HOST or DEVICE memory, any
+ * layout and dtype a single call accepts) is estimated on `stream` by the
+ * single call's kernels with the same parameters p; method is
+ * VNE_METHOD_CHEBYSHEV, VNE_METHOD_TAYLOR or VNE_METHOD_BOTH.  Each host
+ * matrix is copied into one of two device slots held by the handle (each the
+ * size of the largest host matrix of the call) on the handle's own copy
+ * stream, one matrix ahead: the copy of host matrix j + 1 runs while matrix j
+ * is estimated.  Host memory that is pinned (cudaHostAlloc,
+ * cudaHostRegister) overlaps; pageable memory is copied correctly but the
+ * runtime stages it without overlap.
+ * H_cheb / H_taylor / u_out: host arrays of count doubles (those of the
+ * estimators not run may be NULL; u_out may be NULL).  Every matrix is
+ * validated before the first transfer.  Returns the first failing status;
+ * the matrix that failed and the ones after it get NaN.  Results equal the
+ * single calls' exactly.  No transfer from the caller's memory is in flight
+ * when the call returns.  Synchronises `stream`. */
+vne_status vne_entropy_sequence(vne_handle* h, const vne_matrix* Rs, int32_t count,
+                                const vne_params* p, int32_t method, double* H_cheb,
+                                double* H_taylor, double* u_out, void* stream);
+
 /* Autotuner of the tensor-core step (BF16 / BF16X3 dense paths; not in the
  * paper).  Times every candidate tile shape -- BN probe columns per CTA (the
  * widest MMA, half of it, 128), each with and without the K split over a CTA

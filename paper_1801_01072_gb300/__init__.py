@@ -329,6 +329,42 @@ def entropy_batched(Rs, m: int, s: int, seed: int = 0, probe: str = "rademacher"
     return hc, ht, uo
 
 
+def entropy_sequence(Rs, m: int, s: int, seed: int = 0, probe: str = "rademacher",
+                     precision: str = "f64", method: str = "chebyshev", power_iters: int = 30,
+                     power_trials: int = 1, u_scale: float = 1.0, u: float | None = None,
+                     layouts=None, stream=None):
+    """Density matrices (host or device tensors) estimated one after another
+    with the single call's kernels; a host matrix's transfer (pinned memory)
+    runs while the previous matrix is estimated.  Returns (H_chebyshev,
+    H_taylor, u) as float64 arrays (None for an estimator not run)."""
+    layouts = layouts or ["dense"] * len(Rs)
+    mats, keep, dev, host_dev = [], [], None, None
+    for R, lay in zip(Rs, layouts):
+        mat, k, d = _matrix(R, lay)
+        mats.append(mat)
+        keep.append(k)
+        if k.is_cuda:
+            if dev is not None and d != dev:
+                raise ValueError("entropy_sequence takes tensors of one device")
+            dev = d
+        else:
+            host_dev = d
+    dev = host_dev if dev is None else dev
+    arr = (_lib.VneMatrix * len(mats))(*mats)
+    h = _handle(dev)
+    p = _params(m, s, seed, probe, precision, power_iters, power_trials, u_scale, u, False)
+    meth = {"taylor": 0, "chebyshev": 1, "both": 2}[method]
+    n = len(mats)
+    hc = np.full(n, np.nan) if meth in (1, 2) else None
+    ht = np.full(n, np.nan) if meth in (0, 2) else None
+    uo = np.full(n, np.nan)
+    st = h.lib.vne_entropy_sequence(h.h, C.cast(arr, C.c_void_p), n, C.byref(p), meth,
+                                    _dptr(hc), _dptr(ht), _dptr(uo), _stream(dev, stream))
+    h.check(st, "vne_entropy_sequence")
+    del keep
+    return hc, ht, uo
+
+
 def autotune(R, m: int, s: int, precision: str = "bf16", method: str = "chebyshev",
              seed: int = 0, probe: str = "gaussian", power_iters: int = 30, stream=None):
     """Time the tensor-core tile shapes on R and keep the fastest for R's size

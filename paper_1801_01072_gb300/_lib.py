@@ -67,6 +67,8 @@ SIGNATURES = [
     ("vne_entropy_batched", C.c_int,
      [_H, C.c_void_p, C.c_int32, C.POINTER(VneParams), C.c_int32, C.c_int32, _D, _D, _D,
       C.c_void_p]),
+    ("vne_entropy_sequence", C.c_int,
+     [_H, C.c_void_p, C.c_int32, C.POINTER(VneParams), C.c_int32, _D, _D, _D, C.c_void_p]),
     ("vne_tc_autotune", C.c_int,
      [_H, C.POINTER(VneMatrix), C.POINTER(VneParams), C.c_int32, C.c_void_p, _D, C.c_void_p]),
     ("vne_tc_shape", C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p]),

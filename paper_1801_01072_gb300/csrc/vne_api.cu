@@ -53,6 +53,12 @@ struct vne_handle {
     char* btab_dev = nullptr;
     char* btab_host = nullptr;
     size_t btab_bytes = 0;
+    // sequences of host-resident matrices: two device slots, one filled by
+    // the copy stream while the matrix in the other is estimated
+    char* stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t cev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1051,6 +1057,11 @@ void vne_destroy(vne_handle* h) {
     if (h->btab_dev) cudaFree(h->btab_dev);
     if (h->btab_host) cudaFreeHost(h->btab_host);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        if (h->stage[k]) cudaFree(h->stage[k]);
+        if (h->cev[k]) cudaEventDestroy(h->cev[k]);
+    }
+    if (h->cstream) cudaStreamDestroy(h->cstream);
     delete h;
 }
 
@@ -1295,6 +1306,39 @@ vne_status batch_resources(vne_handle* h, size_t ws_bytes, size_t count) {
     }
     return VNE_OK;
 }
+
+// The copy stream, its two events and `slots` device slots of `bytes` each
+// for a sequence call (grown as needed; freed with the handle).
+vne_status stage_resources(vne_handle* h, size_t bytes, int slots) {
+    cudaError_t e = cudaSuccess;
+    if (!h->cstream) e = cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        if (!h->cev[k]) e = cudaEventCreateWithFlags(&h->cev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return map_err(h, e);
+    }
+    if (bytes > h->stage_bytes) {
+        cudaDeviceSynchronize();
+        for (int k = 0; k < 2; ++k) {
+            if (h->stage[k]) cudaFree(h->stage[k]);
+            h->stage[k] = nullptr;
+        }
+        h->stage_bytes = 0;
+    }
+    for (int k = 0; k < slots; ++k) {
+        if (h->stage[k]) continue;
+        const size_t want = bytes > h->stage_bytes ? bytes : h->stage_bytes;
+        if (cudaMalloc((void**)&h->stage[k], want) != cudaSuccess) {
+            cudaGetLastError();
+            h->stage[k] = nullptr;
+            return VNE_ERR_OOM;
+        }
+    }
+    if (bytes > h->stage_bytes) h->stage_bytes = bytes;
+    return VNE_OK;
+}
+
 }  // namespace
 
 vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t count,
@@ -1522,6 +1566,94 @@ vne_status vne_entropy_batched(vne_handle* h, const vne_matrix* Rs, int32_t coun
         return map_err(h, e);
     }
     return collect();
+}
+
+vne_status vne_entropy_sequence(vne_handle* h, const vne_matrix* Rs, int32_t count,
+                                const vne_params* p, int32_t method, double* H_cheb,
+                                double* H_taylor, double* u_out, void* stream) {
+    if (!h || !Rs || !p || count < 1) return VNE_ERR_INVALID_ARG;
+    if (method != VNE_METHOD_TAYLOR && method != VNE_METHOD_CHEBYSHEV && method != VNE_METHOD_BOTH)
+        return VNE_ERR_INVALID_ARG;
+    const int mode = method == VNE_METHOD_TAYLOR ? MODE_TAYLOR
+                     : method == VNE_METHOD_CHEBYSHEV ? MODE_CHEB : MODE_BOTH;
+    if ((mode & MODE_CHEB) && !H_cheb) return VNE_ERR_INVALID_ARG;
+    if ((mode & MODE_TAYLOR) && !H_taylor) return VNE_ERR_INVALID_ARG;
+    // every matrix is checked before any transfer starts
+    size_t stage = 0;
+    int nhost = 0;
+    for (int i = 0; i < count; ++i) {
+        vne_status vs = validate(&Rs[i], p, mode);
+        if (vs != VNE_OK) return vs;
+        if (Rs[i].memory == VNE_MEM_HOST) {
+            const size_t b = (size_t)(Rs[i].layout == VNE_DENSE ? Rs[i].n : Rs[i].n_diags) *
+                             (size_t)Rs[i].ld * elt_size(Rs[i].dtype);
+            if (b > stage) stage = b;
+            ++nhost;
+        }
+    }
+    const double nan = std::nan("");
+    for (int i = 0; i < count; ++i) {
+        if (H_cheb && (mode & MODE_CHEB)) H_cheb[i] = nan;
+        if (H_taylor && (mode & MODE_TAYLOR)) H_taylor[i] = nan;
+        if (u_out) u_out[i] = nan;
+    }
+    DeviceGuard guard(h->device);
+    if (nhost > 0) {
+        vne_status vs = stage_resources(h, stage, nhost < 2 ? 1 : 2);
+        if (vs != VNE_OK) return vs;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    std::vector<int> host_idx;
+    for (int i = 0; i < count; ++i)
+        if (Rs[i].memory == VNE_MEM_HOST) host_idx.push_back(i);
+    // host matrix number j goes to slot j & 1; it is requested once matrix
+    // j - 1 has been estimated (the single call returns synchronised), so the
+    // slot's previous matrix, j - 2, is no longer read
+    int issued = 0, ord = 0;
+    auto request = [&](int j) -> cudaError_t {
+        const vne_matrix& R = Rs[host_idx[j]];
+        const size_t b = (size_t)(R.layout == VNE_DENSE ? R.n : R.n_diags) * (size_t)R.ld *
+                         elt_size(R.dtype);
+        cudaError_t e = cudaMemcpyAsync(h->stage[j & 1], R.data, b, cudaMemcpyHostToDevice,
+                                        h->cstream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->cev[j & 1], h->cstream);
+        return e;
+    };
+    vne_status first = VNE_OK;
+    for (int i = 0; i < count; ++i) {
+        vne_matrix M = Rs[i];
+        if (M.memory == VNE_MEM_HOST) {
+            cudaError_t e = cudaSuccess;
+            while (e == cudaSuccess && issued < nhost && issued <= ord + 1) e = request(issued++);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->cev[ord & 1], 0);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                first = map_err(h, e);
+                break;
+            }
+            M.data = h->stage[ord & 1];
+            M.memory = VNE_MEM_DEVICE;
+            ++ord;
+        }
+        Outputs o;
+        if (mode & MODE_CHEB) o.H_cheb = &H_cheb[i];
+        if (mode & MODE_TAYLOR) o.H_taylor = &H_taylor[i];
+        o.u = u_out ? &u_out[i] : nullptr;
+        vne_status r = run(h, &M, p, mode, o, stream);
+        if (r != VNE_OK) {
+            first = r;
+            break;
+        }
+    }
+    // no copy from the caller's memory is in flight once this returns
+    if (h->cstream) {
+        cudaError_t e = cudaStreamSynchronize(h->cstream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (first == VNE_OK) first = map_err(h, e);
+        }
+    }
+    return first;
 }
 
 vne_status vne_tc_shape(int64_t n, int32_t ncols, int32_t sm_count, int32_t* shape_out) {

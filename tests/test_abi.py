@@ -75,6 +75,7 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.vne_entropy_taylor_probes(None, None, None, None, C.byref(H), None, None,
                                          None) == 1
     assert lib.vne_create(None, 0) == 1
+    assert lib.vne_entropy_sequence(None, None, 1, None, 1, None, None, None, None) == 1
 
 
 def tc_shape(lib, n, ncols, sms=152):
