@@ -50,7 +50,7 @@ typedef enum vne_status {
 } vne_status;
 
 /* vne_matrix.layout */
-enum { VNE_DENSE = 0, VNE_DIA = 1 };
+enum { VNE_DENSE = 0, VNE_DIA = 1, VNE_DENSE_UPPER = 2 };
 /* vne_matrix.dtype: storage type of the matrix entries.  The complex types
  * hold a Hermitian R (Section 4) as interleaved (real, imaginary) pairs, dense
  * layout only; ld counts complex entries. */
@@ -87,6 +87,18 @@ enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1, VNE_METHOD_BOTH = 2 };
  *   n        : order of R (n >= 1).
  *   layout   : VNE_DENSE -- row-major, entry (i, k) at data[i*ld + k], ld >= n.
  *                           Only symmetric R is meaningful; the full square is read.
+ *              VNE_DENSE_UPPER -- the same storage, but only the upper triangle
+ *                           (k >= i) is read; the strictly lower entries may hold
+ *                           anything.  R is taken as exactly symmetric: the call
+ *                           mirrors the upper triangle into a full copy on the
+ *                           device first.  A HOST matrix moves only its upper
+ *                           triangle, plus the lower halves of diagonal blocks of
+ *                           at most 256 rows, as rectangular copies: about half
+ *                           the bytes of VNE_DENSE.  Real dtypes only; the
+ *                           estimators, vne_lambda_max and the sequence and
+ *                           batched calls accept it, the projection, learned and
+ *                           allocation-free calls do not (VNE_ERR_UNSUPPORTED or
+ *                           VNE_ERR_INVALID_ARG).
  *              VNE_DIA   -- symmetric banded: n_diags stored diagonals with offsets
  *                           0..n_diags-1, entry R[i, i+d] at data[d*ld + i] for
  *                           i < n-d (the rest of each row is ignored); the lower

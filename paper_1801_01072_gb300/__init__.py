@@ -15,6 +15,8 @@ is no CPU fallback.
 ``R`` is a dense (n, n) tensor (row-major; complex128/complex64 for a
 Hermitian R, Section 4) or, with ``layout="dia"``, the
 (D, n) band storage ``vals[d, i] = R[i, i + d]`` of a symmetric banded R.
+With ``layout="upper"`` only the upper triangle of a dense real R is read
+(a host R then moves about half the bytes).
 It may live on the GPU (device pointer) or in host memory (the call then
 copies it itself).
 """
@@ -128,11 +130,12 @@ def _matrix(R, layout: str):
     if R.stride(1) != 1:
         R = R.contiguous()
     mat = _lib.VneMatrix()
-    if layout == "dense":
+    if layout in ("dense", "upper"):
+        # "upper": only the upper triangle is read (R taken as exactly symmetric)
         if R.shape[0] != R.shape[1]:
             raise ValueError("dense R must be square")
         mat.n = R.shape[0]
-        mat.layout = _lib.DENSE
+        mat.layout = _lib.DENSE if layout == "dense" else _lib.DENSE_UPPER
         mat.n_diags = 0
     elif layout == "dia":
         mat.n = R.shape[1]

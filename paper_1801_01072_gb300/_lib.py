@@ -12,7 +12,7 @@ STATUS = {
     3: "VNE_ERR_BAD_INTERVAL", 4: "VNE_ERR_OOM", 5: "VNE_ERR_CUDA", 6: "VNE_ERR_TIMEOUT",
     7: "VNE_ERR_NONFINITE", 8: "VNE_ERR_UNSUPPORTED",
 }
-DENSE, DIA = 0, 1
+DENSE, DIA, DENSE_UPPER = 0, 1, 2
 F64, F32, C128, C64 = 0, 1, 2, 3
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "bf16x3": 3, "bf16x6": 4}
 PROBE = {"rademacher": 0, "gaussian": 1}

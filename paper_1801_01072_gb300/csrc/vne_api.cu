@@ -261,7 +261,8 @@ bool coop_launch_ok(const vne_handle* h) {
 vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
     if (!R || !p) return VNE_ERR_INVALID_ARG;
     if (R->n < 1 || !R->data) return VNE_ERR_INVALID_ARG;
-    if (R->layout != VNE_DENSE && R->layout != VNE_DIA) return VNE_ERR_INVALID_ARG;
+    if (R->layout != VNE_DENSE && R->layout != VNE_DIA && R->layout != VNE_DENSE_UPPER)
+        return VNE_ERR_INVALID_ARG;
     if (R->dtype != VNE_F64 && R->dtype != VNE_F32 && !is_complex(R->dtype))
         return VNE_ERR_INVALID_ARG;
     if (R->memory != VNE_MEM_DEVICE && R->memory != VNE_MEM_HOST) return VNE_ERR_INVALID_ARG;
@@ -303,6 +304,40 @@ vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
 }
 
 // ---------------------------------------------------------------------------
+// The upper triangle of a row-major n x n matrix (plus the lower halves of
+// diagonal blocks of at most 256 rows) as rectangular copies: the triangle on
+// rows [r0, r1) is the block of rows [r0, mid) and columns [mid, r1), plus the
+// triangles on [r0, mid) and [mid, r1).  About 2 log2(n / 256) + n / 256
+// copies; no stored value of the lower triangle is needed afterwards.
+cudaError_t copy_upper_async(void* dst, int64_t ldd, const void* src, int64_t lds, int64_t n,
+                             size_t elt, cudaMemcpyKind kind, cudaStream_t st) {
+    struct Span { int64_t r0, r1; };
+    std::vector<Span> todo{{0, n}};
+    char* d = static_cast<char*>(dst);
+    const char* sp = static_cast<const char*>(src);
+    while (!todo.empty()) {
+        const Span t = todo.back();
+        todo.pop_back();
+        const int64_t w = t.r1 - t.r0;
+        if (w <= 0) continue;
+        cudaError_t e;
+        if (w <= 256) {
+            e = cudaMemcpy2DAsync(d + (size_t)(t.r0 * ldd + t.r0) * elt, (size_t)ldd * elt,
+                                  sp + (size_t)(t.r0 * lds + t.r0) * elt, (size_t)lds * elt,
+                                  (size_t)w * elt, (size_t)w, kind, st);
+        } else {
+            const int64_t mid = t.r0 + w / 2;
+            e = cudaMemcpy2DAsync(d + (size_t)(t.r0 * ldd + mid) * elt, (size_t)ldd * elt,
+                                  sp + (size_t)(t.r0 * lds + mid) * elt, (size_t)lds * elt,
+                                  (size_t)(t.r1 - mid) * elt, (size_t)(mid - t.r0), kind, st);
+            todo.push_back({mid, t.r1});
+            todo.push_back({t.r0, mid});
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // One estimator call.
 // ---------------------------------------------------------------------------
 vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mode, Outputs out,
@@ -318,7 +353,9 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     // embedding [[B, -C], [C, B]] with probes [g; 0] and u = 1 unless given.
     const bool cplx = is_complex(R.dtype);
     const int64_t n = cplx ? 2 * R.n : R.n;
-    const bool dense = R.layout == VNE_DENSE;
+    // VNE_DENSE_UPPER runs as VNE_DENSE on a full copy mirrored from its upper triangle
+    const bool upper = R.layout == VNE_DENSE_UPPER;
+    const bool dense = R.layout != VNE_DIA;
     const int prec = p->precision;
     const bool tc = dense && prec >= VNE_PREC_BF16;
     // bf16 pieces of R and Y on the tensor-core path: 1 (BF16), 2 (bf16x3), 3 (bf16x6)
@@ -405,7 +442,7 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
         *counter = b.take<unsigned int>(64);
         *ppart = b.take<double>((size_t)std::max(power_blocks, 256) * 3 * q);
         *Rcopy = nullptr;
-        if (R.memory == VNE_MEM_HOST)
+        if (R.memory == VNE_MEM_HOST || upper)
             *Rcopy = b.take<char>((size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype));
         *Rop = nullptr;
         for (int k = 0; k < kMaxPieces; ++k) Rpc[k] = nullptr;
@@ -478,11 +515,20 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     const void* Rdata = R.data;
     if (R.memory == VNE_MEM_HOST) {
         const size_t bytes = (size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype);
-        if (pro) c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
+        if (pro && upper)
+            c.chk(copy_upper_async(Rcopy, R.ld, R.data, R.ld, R.n, elt_size(R.dtype),
+                                   cudaMemcpyHostToDevice, c.st));
+        else if (pro)
+            c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
+        Rdata = Rcopy;
+    }
+    if (upper) {  // in place on the host copy, else from the caller's matrix
+        if (pro) c.launched(launch_dense_symmetrize(Rdata, R.ld, Rcopy, R.ld, R.n, R.dtype, c.st));
         Rdata = Rcopy;
     }
     if (pro && p->check_trace)
-        c.launched(launch_trace(Rdata, R.layout, R.dtype, R.n, R.ld, ppart, counter, sc, c.st));
+        c.launched(launch_trace(Rdata, dense ? VNE_DENSE : VNE_DIA, R.dtype, R.n, R.ld, ppart,
+                                counter, sc, c.st));
 
     // ---- operands ----
     const void* Rk = Rdata;  // operand of the SIMT / DIA / power kernels
@@ -1585,7 +1631,7 @@ vne_status vne_entropy_sequence(vne_handle* h, const vne_matrix* Rs, int32_t cou
         vne_status vs = validate(&Rs[i], p, mode);
         if (vs != VNE_OK) return vs;
         if (Rs[i].memory == VNE_MEM_HOST) {
-            const size_t b = (size_t)(Rs[i].layout == VNE_DENSE ? Rs[i].n : Rs[i].n_diags) *
+            const size_t b = (size_t)(Rs[i].layout != VNE_DIA ? Rs[i].n : Rs[i].n_diags) *
                              (size_t)Rs[i].ld * elt_size(Rs[i].dtype);
             if (b > stage) stage = b;
             ++nhost;
@@ -1612,10 +1658,14 @@ vne_status vne_entropy_sequence(vne_handle* h, const vne_matrix* Rs, int32_t cou
     int issued = 0, ord = 0;
     auto request = [&](int j) -> cudaError_t {
         const vne_matrix& R = Rs[host_idx[j]];
-        const size_t b = (size_t)(R.layout == VNE_DENSE ? R.n : R.n_diags) * (size_t)R.ld *
+        const size_t b = (size_t)(R.layout != VNE_DIA ? R.n : R.n_diags) * (size_t)R.ld *
                          elt_size(R.dtype);
-        cudaError_t e = cudaMemcpyAsync(h->stage[j & 1], R.data, b, cudaMemcpyHostToDevice,
-                                        h->cstream);
+        cudaError_t e = R.layout == VNE_DENSE_UPPER
+                            ? copy_upper_async(h->stage[j & 1], R.ld, R.data, R.ld, R.n,
+                                               elt_size(R.dtype), cudaMemcpyHostToDevice,
+                                               h->cstream)
+                            : cudaMemcpyAsync(h->stage[j & 1], R.data, b, cudaMemcpyHostToDevice,
+                                              h->cstream);
         if (e == cudaSuccess) e = cudaEventRecord(h->cev[j & 1], h->cstream);
         return e;
     };
@@ -1633,6 +1683,17 @@ vne_status vne_entropy_sequence(vne_handle* h, const vne_matrix* Rs, int32_t cou
             }
             M.data = h->stage[ord & 1];
             M.memory = VNE_MEM_DEVICE;
+            if (M.layout == VNE_DENSE_UPPER) {  // the slot is the handle's: mirror in place
+                e = launch_dense_symmetrize(M.data, M.ld, h->stage[ord & 1], M.ld, M.n, M.dtype,
+                                            user);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    first = map_err(h, e);
+                    break;
+                }
+                ++h->launches;
+                M.layout = VNE_DENSE;
+            }
             ++ord;
         }
         Outputs o;

@@ -77,6 +77,10 @@ cudaError_t launch_dia_convert(const void* src, int src_dtype, int64_t n, int64_
 // ld complex elements) into dst (2n x 2n, ld 2n, FP64 if dst_dtype 0 else FP32)
 cudaError_t launch_hermitian_embed(const void* src, int cdtype, int64_t n, int64_t ld, void* dst,
                                    int dst_dtype, cudaStream_t st);
+// A full symmetric copy of a dense R whose upper triangle is authoritative
+// (dtype 0 = FP64, 1 = FP32; in place when dst == src, then lds == ldd).
+cudaError_t launch_dense_symmetrize(const void* src, int64_t lds, void* dst, int64_t ldd,
+                                    int64_t n, int dtype, cudaStream_t st);
 cudaError_t launch_trace(const void* R, int layout, int dtype, int64_t n, int64_t ld,
                          double* partial, unsigned int* counter, double* sc, cudaStream_t st);
 cudaError_t launch_set_u(double* sc, double u, cudaStream_t st);

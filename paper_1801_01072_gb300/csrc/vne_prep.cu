@@ -148,6 +148,65 @@ cudaError_t launch_dense_convert_bf16(const void* src, int src_dtype, int64_t n,
     return launch_convert_bf16_rect(src, src_dtype, n, n, ld, out, pieces, rows_pad, ldk, st);
 }
 
+// A full symmetric copy of R from its upper triangle (layout VNE_DENSE_UPPER),
+// in the storage type T.  Output tile (I, J) of 32 x 32: strictly upper tiles
+// are copied (skipped when dst == src: they are already there), strictly
+// lower ones are the transposes of the upper tiles (J, I), staged through
+// shared memory so that both the reads and the writes are row-contiguous, and
+// diagonal tiles take every entry (i, k) from (min(i, k), max(i, k)).  In place,
+// no tile is both read by one block and written by another: lower tiles read
+// only strictly upper tiles, which nobody writes, and a diagonal tile is read
+// and rewritten by its own block alone.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_symmetrize(const T* src, int64_t lds, T* dst,
+                                                          int64_t ldd, int64_t n, int in_place) {
+    __shared__ T sm[32][33];
+    const int64_t I = blockIdx.y, J = blockIdx.x;
+    if (I < J && in_place) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    if (I < J) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t r = I * 32 + ty + 8 * k, c = J * 32 + tx;
+            if (r < n && c < n) dst[r * ldd + c] = src[r * lds + c];
+        }
+        return;
+    }
+    // the source tile: (J, I) for a lower tile, (I, I) for a diagonal one
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t r = J * 32 + ty + 8 * k, c = I * 32 + tx;
+        if (r < n && c < n) sm[ty + 8 * k][tx] = src[r * lds + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int y = ty + 8 * k;
+        const int64_t r = I * 32 + y, c = J * 32 + tx;
+        if (r >= n || c >= n) continue;
+        // lower tile: dst(r, c) = src(c, r) = sm[tx][y]; diagonal: upper
+        // entries (tx >= y) from sm[y][tx], lower ones mirrored
+        dst[r * ldd + c] = (I > J || tx < y) ? sm[tx][y] : sm[y][tx];
+    }
+}
+
+cudaError_t launch_dense_symmetrize(const void* src, int64_t lds, void* dst, int64_t ldd,
+                                    int64_t n, int dtype, cudaStream_t st) {
+    if (n < 1 || lds < n || ldd < n || (dtype != 0 && dtype != 1)) return cudaErrorInvalidValue;
+    const int64_t tiles = (n + 31) / 32;
+    if (tiles > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)tiles, (unsigned)tiles), block(32, 8);
+    const int in_place = src == dst ? 1 : 0;
+    if (in_place && lds != ldd) return cudaErrorInvalidValue;
+    if (dtype == 0)
+        k_dense_symmetrize<double><<<grid, block, 0, st>>>((const double*)src, lds, (double*)dst,
+                                                           ldd, n, in_place);
+    else
+        k_dense_symmetrize<float><<<grid, block, 0, st>>>((const float*)src, lds, (float*)dst, ldd,
+                                                          n, in_place);
+    return cudaGetLastError();
+}
+
 __global__ void k_dia_convert(const void* src, int sdt, int64_t n, int64_t ld, int D, void* dst,
                               int ddt) {
     const int64_t total = (int64_t)D * n;

@@ -120,3 +120,65 @@ def test_failing_matrix_stops_the_sequence():
                                        C.byref(u), None) == 0
     assert hc[0] == H.value and uo[0] == u.value
     assert np.isnan(hc[1:]).all() and np.isnan(uo[1:]).all()
+
+
+def poisoned(R):
+    """R with NaN below the diagonal: a call that read the lower triangle of
+    an upper-layout matrix would return NaN."""
+    P = R.copy()
+    P[np.tril_indices(R.shape[0], -1)] = np.nan
+    return P
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("where", ["device", "pinned", "pageable"])
+def test_upper_layout_equals_dense(precision, where):
+    """layout "upper" reads only the upper triangle; on an exactly symmetric
+    R the result is the dense layout's, bit for bit (n spans several 32-row
+    tiles with a ragged edge, and several 256-row copy blocks)."""
+    for n, dt in ((1000, np.float64), (700, np.float32), (2600, np.float64)):
+        R = dense([n], seed0=n)[0].astype(dt)
+        P = torch.tensor(poisoned(R))
+        P = P.cuda() if where == "device" else (P.pin_memory() if where == "pinned" else P)
+        kw = dict(seed=3, probe="gaussian", precision=precision)
+        got = single(P, 10, 8, "both", layout="upper", **kw)
+        want = single(torch.tensor(R).cuda(), 10, 8, "both", **kw)
+        assert got == want, (n, got, want)
+        lam = vne.lambda_max(P, precision=precision if precision in ("f64", "f32") else "f64",
+                             layout="upper")
+        assert lam == vne.lambda_max(torch.tensor(R).cuda(),
+                                     precision=precision if precision in ("f64", "f32")
+                                     else "f64")
+
+
+def test_upper_layout_sequence_and_batch():
+    Rs = dense([1500, 300, 2049], seed0=90)
+    host = [torch.tensor(poisoned(R)).pin_memory() for R in Rs]
+    kw = dict(seed=5, probe="gaussian", precision="bf16", method="both")
+    hc, ht, u = vne.entropy_sequence(host, 12, 16, layouts=["upper"] * 3, **kw)
+    bc, bt, bu = vne.entropy_batched([t.cuda() for t in host], 12, 16, layouts=["upper"] * 3,
+                                     **kw)
+    for i, R in enumerate(Rs):
+        c, t, uu = single(torch.tensor(R).cuda(), 12, 16, "both", seed=5, probe="gaussian",
+                          precision="bf16")
+        assert (hc[i], ht[i], u[i]) == (c, t, uu), i
+    # the batch runs its matrices on the per-matrix path: the same bits
+    assert np.array_equal(bc, hc) and np.array_equal(bt, ht)
+
+
+def test_upper_layout_refused_where_unsupported():
+    """The projection and allocation-free calls take no upper layout, nor does
+    a complex (Hermitian) R: refused before any work."""
+    from paper_1801_01072_gb300 import _lib
+    R = torch.tensor(dense([256], seed0=3)[0]).cuda()
+    mat = vne._matrix(R, "upper")[0]
+    h = vne._handle(torch.cuda.current_device())
+    H = C.c_double()
+    st = h.lib.vne_entropy_projection(h.h, C.byref(mat), 8, 16, 0, 0, 0, 1, C.byref(H), None, None)
+    assert _lib.STATUS[st] == "VNE_ERR_INVALID_ARG"  # a layout the projection does not know
+    p = vne._params(1, 1, 0, "rademacher", "f64", 30, 1, 1.0, None, False)
+    assert _lib.STATUS[h.lib.vne_lambda_max_static(C.byref(mat), C.byref(p), C.byref(H), None)] \
+        == "VNE_ERR_INVALID_ARG"
+    Cx = torch.tensor(dense([64], seed0=4)[0]).to(torch.complex128).cuda()
+    with pytest.raises(vne.VneError):
+        vne.entropy_chebyshev(Cx, 4, 4, layout="upper")
