@@ -50,25 +50,6 @@ def peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
-def upper_copy_bytes(n, elt):
-    """Bytes the upper-layout host transfer moves for an n x n matrix: the
-    rectangles of the split triangle, and whole diagonal blocks of <= 256 rows
-    (the same split as the library's copy)."""
-    todo, total = [(0, n)], 0
-    while todo:
-        r0, r1 = todo.pop()
-        w = r1 - r0
-        if w <= 0:
-            continue
-        if w <= 256:
-            total += w * w
-        else:
-            mid = r0 + w // 2
-            total += (mid - r0) * (r1 - mid)
-            todo += [(mid, r1), (r0, mid)]
-    return total * elt
-
-
 def profiled_traffic(profile_name, source):
     """DRAM bytes per launch recorded in profiles/<profile_name> by an ncu
     capture, or None when the kernel source changed since that capture."""
@@ -1126,20 +1107,15 @@ def run_gpu(args):
     # (b) the sequence call over host matrices (two pinned buffers,
     # alternating): each matrix's transfer runs while the previous one is
     # estimated; the first transfer is not hidden and is counted
-    # A dense R is symmetric, so the sequence passes it with layout "upper":
-    # only the upper triangle (and the lower halves of the diagonal blocks)
-    # crosses the host link
     Rpin2 = Rpin.clone().pin_memory()
     seq_len = max(8, args.steps // 4)
     seq = [Rpin if i % 2 == 0 else Rpin2 for i in range(seq_len)]
     meth = "both" if dense else "chebyshev"
-    seq_layout = "upper" if dense else layout
-    h2d_seq = upper_copy_bytes(n, Rh.itemsize) if dense else int(Rh.nbytes)
 
     def run_seq():
         return vne.entropy_sequence(seq, m, s, seed=seed, probe=w["probe"], precision=prec,
                                     power_iters=w["power_iters"], method=meth,
-                                    layouts=[seq_layout] * seq_len)
+                                    layouts=[layout] * seq_len)
     seq_out = run_seq()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
@@ -1261,16 +1237,13 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (R is %.0f MB)" % (Rh.nbytes / 1e6),
                    "parallelism": f"independent matrices, {world} GPU(s)"},
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": "entropies/s",
-                "h2d_bytes_per_step": h2d_seq, "d2h_bytes_per_step": 200 * 8,
+                "h2d_bytes_per_step": int(Rh.nbytes), "d2h_bytes_per_step": 200 * 8,
                 "api": f"entropy_sequence over {seq_len} pinned host matrices (two buffers, "
-                       f"alternating), layout {seq_layout}: each transfer overlaps the previous "
-                       "estimate" + ("; the upper triangle of the symmetric R crosses the link "
-                                     "and is mirrored on the device" if dense else ""),
+                       "alternating): each transfer overlaps the previous estimate",
                 "equals_single_calls": same,
                 "single_call": {"value": world * 1e3 / e2e_single_ms, "unit": "entropies/s",
-                                "h2d_bytes_per_step": int(Rh.nbytes),
                                 "api": "entropy_both / entropy_chebyshev on one pinned host "
-                                       "matrix, full square: copy, then estimate"}},
+                                       "matrix: copy, then estimate"}},
         "gpu_launches": int(n_launch),
         "phases_ms_per_step": {"recurrence": k_ms / args.steps, "power_method": p_ms / args.steps,
                                "other": ms_max / args.steps - (k_ms + p_ms) / args.steps},

@@ -88,13 +88,11 @@ enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1, VNE_METHOD_BOTH = 2 };
  *   layout   : VNE_DENSE -- row-major, entry (i, k) at data[i*ld + k], ld >= n.
  *                           Only symmetric R is meaningful; the full square is read.
  *              VNE_DENSE_UPPER -- the same storage, but only the upper triangle
- *                           (k >= i) is read; the strictly lower entries may hold
+ *                           (k >= i) is used; the strictly lower entries may hold
  *                           anything.  R is taken as exactly symmetric: the call
  *                           mirrors the upper triangle into a full copy on the
- *                           device first.  A HOST matrix moves only its upper
- *                           triangle, plus the lower halves of diagonal blocks of
- *                           at most 256 rows, as rectangular copies: about half
- *                           the bytes of VNE_DENSE.  Real dtypes only; the
+ *                           device first (a HOST matrix is copied whole, then
+ *                           mirrored in place).  Real dtypes only; the
  *                           estimators, vne_lambda_max and the sequence and
  *                           batched calls accept it, the projection, learned and
  *                           allocation-free calls do not (VNE_ERR_UNSUPPORTED or

@@ -15,8 +15,8 @@ is no CPU fallback.
 ``R`` is a dense (n, n) tensor (row-major; complex128/complex64 for a
 Hermitian R, Section 4) or, with ``layout="dia"``, the
 (D, n) band storage ``vals[d, i] = R[i, i + d]`` of a symmetric banded R.
-With ``layout="upper"`` only the upper triangle of a dense real R is read
-(a host R then moves about half the bytes).
+With ``layout="upper"`` only the upper triangle of a dense real R is used
+(mirrored on the device).
 It may live on the GPU (device pointer) or in host memory (the call then
 copies it itself).
 """

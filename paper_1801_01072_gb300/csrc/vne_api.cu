@@ -304,40 +304,6 @@ vne_status validate(const vne_matrix* R, const vne_params* p, int mode) {
 }
 
 // ---------------------------------------------------------------------------
-// The upper triangle of a row-major n x n matrix (plus the lower halves of
-// diagonal blocks of at most 256 rows) as rectangular copies: the triangle on
-// rows [r0, r1) is the block of rows [r0, mid) and columns [mid, r1), plus the
-// triangles on [r0, mid) and [mid, r1).  About 2 log2(n / 256) + n / 256
-// copies; no stored value of the lower triangle is needed afterwards.
-cudaError_t copy_upper_async(void* dst, int64_t ldd, const void* src, int64_t lds, int64_t n,
-                             size_t elt, cudaMemcpyKind kind, cudaStream_t st) {
-    struct Span { int64_t r0, r1; };
-    std::vector<Span> todo{{0, n}};
-    char* d = static_cast<char*>(dst);
-    const char* sp = static_cast<const char*>(src);
-    while (!todo.empty()) {
-        const Span t = todo.back();
-        todo.pop_back();
-        const int64_t w = t.r1 - t.r0;
-        if (w <= 0) continue;
-        cudaError_t e;
-        if (w <= 256) {
-            e = cudaMemcpy2DAsync(d + (size_t)(t.r0 * ldd + t.r0) * elt, (size_t)ldd * elt,
-                                  sp + (size_t)(t.r0 * lds + t.r0) * elt, (size_t)lds * elt,
-                                  (size_t)w * elt, (size_t)w, kind, st);
-        } else {
-            const int64_t mid = t.r0 + w / 2;
-            e = cudaMemcpy2DAsync(d + (size_t)(t.r0 * ldd + mid) * elt, (size_t)ldd * elt,
-                                  sp + (size_t)(t.r0 * lds + mid) * elt, (size_t)lds * elt,
-                                  (size_t)(t.r1 - mid) * elt, (size_t)(mid - t.r0), kind, st);
-            todo.push_back({mid, t.r1});
-            todo.push_back({t.r0, mid});
-        }
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 // One estimator call.
 // ---------------------------------------------------------------------------
 vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mode, Outputs out,
@@ -515,11 +481,9 @@ vne_status run(vne_handle* h, const vne_matrix* Rin, const vne_params* p, int mo
     const void* Rdata = R.data;
     if (R.memory == VNE_MEM_HOST) {
         const size_t bytes = (size_t)(dense ? R.n : D) * R.ld * elt_size(R.dtype);
-        if (pro && upper)
-            c.chk(copy_upper_async(Rcopy, R.ld, R.data, R.ld, R.n, elt_size(R.dtype),
-                                   cudaMemcpyHostToDevice, c.st));
-        else if (pro)
-            c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
+        // whole (an upper-layout matrix too: strided copies of its triangle
+        // from host memory ran far below the link's rate)
+        if (pro) c.chk(cudaMemcpyAsync(Rcopy, R.data, bytes, cudaMemcpyHostToDevice, c.st));
         Rdata = Rcopy;
     }
     if (upper) {  // in place on the host copy, else from the caller's matrix
@@ -1660,12 +1624,8 @@ vne_status vne_entropy_sequence(vne_handle* h, const vne_matrix* Rs, int32_t cou
         const vne_matrix& R = Rs[host_idx[j]];
         const size_t b = (size_t)(R.layout != VNE_DIA ? R.n : R.n_diags) * (size_t)R.ld *
                          elt_size(R.dtype);
-        cudaError_t e = R.layout == VNE_DENSE_UPPER
-                            ? copy_upper_async(h->stage[j & 1], R.ld, R.data, R.ld, R.n,
-                                               elt_size(R.dtype), cudaMemcpyHostToDevice,
-                                               h->cstream)
-                            : cudaMemcpyAsync(h->stage[j & 1], R.data, b, cudaMemcpyHostToDevice,
-                                              h->cstream);
+        cudaError_t e = cudaMemcpyAsync(h->stage[j & 1], R.data, b, cudaMemcpyHostToDevice,
+                                        h->cstream);
         if (e == cudaSuccess) e = cudaEventRecord(h->cev[j & 1], h->cstream);
         return e;
     };

@@ -133,9 +133,9 @@ def poisoned(R):
 @pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("where", ["device", "pinned", "pageable"])
 def test_upper_layout_equals_dense(precision, where):
-    """layout "upper" reads only the upper triangle; on an exactly symmetric
-    R the result is the dense layout's, bit for bit (n spans several 32-row
-    tiles with a ragged edge, and several 256-row copy blocks)."""
+    """layout "upper" uses only the upper triangle; on an exactly symmetric
+    R the result is the dense layout's, bit for bit (n spans many 32-row
+    mirror tiles with a ragged edge)."""
     for n, dt in ((1000, np.float64), (700, np.float32), (2600, np.float64)):
         R = dense([n], seed0=n)[0].astype(dt)
         P = torch.tensor(poisoned(R))
