@@ -94,9 +94,9 @@ enum { VNE_METHOD_TAYLOR = 0, VNE_METHOD_CHEBYSHEV = 1, VNE_METHOD_BOTH = 2 };
  *                           device first (a HOST matrix is copied whole, then
  *                           mirrored in place).  Real dtypes only; the
  *                           estimators, vne_lambda_max and the sequence and
- *                           batched calls accept it, the projection, learned and
- *                           allocation-free calls do not (VNE_ERR_UNSUPPORTED or
- *                           VNE_ERR_INVALID_ARG).
+ *                           batched calls accept it; the projection, learned,
+ *                           autotuner and allocation-free calls do not
+ *                           (VNE_ERR_UNSUPPORTED or VNE_ERR_INVALID_ARG).
  *              VNE_DIA   -- symmetric banded: n_diags stored diagonals with offsets
  *                           0..n_diags-1, entry R[i, i+d] at data[d*ld + i] for
  *                           i < n-d (the rest of each row is ignored); the lower
